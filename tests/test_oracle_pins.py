@@ -1,0 +1,273 @@
+"""Pins for the CPU oracle: closed forms, invariants, brute force and convergence.
+
+Every check here is fixed by the mathematics of the method (the paper prints no
+worked example for this path), and each is chosen so that a plausible mistake in
+the oracle (a dropped term, a transposed Jacobian, a wrong index) fails one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import fem_inputs as FI
+import oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms_1d.json")))
+
+
+def _num(s):
+    return float(eval(s, {"sqrt": math.sqrt}))
+
+
+def perturbed(nx, ny, nz, seed=0):
+    return O.HexGridMesh(nx, ny, nz, FI.perturbed_cube_vertices(nx, ny, nz, seed=seed))
+
+
+def unperturbed(nx, ny, nz):
+    return O.HexGridMesh(nx, ny, nz, FI.perturbed_cube_vertices(nx, ny, nz, seed=0, amp=0.0))
+
+
+# ---------------------------------------------------------------- 1D rules
+
+@pytest.mark.parametrize("q", [2, 3])
+def test_gauss_closed_form(q):
+    pts, wts = O.gauss_legendre(q)
+    g = GOLD["gauss_legendre_on_m1_1"][str(q)]
+    np.testing.assert_allclose(2 * pts - 1, [_num(s) for s in g["points"]], atol=1e-15)
+    np.testing.assert_allclose(2 * wts, [_num(s) for s in g["weights"]], atol=1e-15)
+
+
+@pytest.mark.parametrize("q", range(1, 12))
+def test_gauss_exactness(q):
+    pts, wts = O.gauss_legendre(q)
+    assert abs(wts.sum() - 1) < 1e-14
+    for k in range(2 * q):
+        assert abs(wts @ pts ** k - 1.0 / (k + 1)) < 1e-14, k
+    # degree 2q is no longer exact: the remainder of the q-point rule on [0,1] for t^(2q) is
+    # (q!)^4 / ((2q+1) ((2q)!)^2) (standard Gauss error term with f^(2q) = (2q)!)
+    if q <= 7:
+        err = 1.0 / (2 * q + 1) - wts @ pts ** (2 * q)
+        expect = math.factorial(q) ** 4 / ((2 * q + 1) * math.factorial(2 * q) ** 2)
+        assert abs(err / expect - 1) < 1e-3
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_gll_closed_form(p):
+    t = O.gll_points(p)
+    assert t[0] == 0.0 and t[-1] == 1.0
+    np.testing.assert_allclose(2 * t[1:-1] - 1, [_num(s) for s in GOLD["gll_interior_on_m1_1"][str(p)]], atol=1e-15)
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_gll_lobatto_rule_exact(p):
+    # With weights 2/(p(p+1) P_p(t)^2) the GLL nodes integrate degree 2p-1 exactly on [-1,1];
+    # P_p is evaluated by numpy's Legendre series, independent of the oracle's recurrence.
+    t = 2 * O.gll_points(p) - 1
+    Pp = np.polynomial.legendre.legval(t, [0] * p + [1])
+    w = 2.0 / (p * (p + 1) * Pp ** 2)
+    assert np.all(np.diff(t) > 0)
+    np.testing.assert_allclose(t, -t[::-1], atol=1e-15)
+    for k in range(2 * p):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(w @ t ** k - exact) < 1e-13, (p, k)
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_lagrange_identities(p):
+    nodes = O.gll_points(p)
+    V, dV = O.lagrange(nodes, nodes)
+    np.testing.assert_allclose(V, np.eye(p + 1), atol=1e-14)
+    t = np.linspace(-0.2, 1.3, 17)
+    V, dV = O.lagrange(nodes, t)
+    for k in range(p + 1):   # reproduces t^k and its derivative exactly
+        np.testing.assert_allclose(V @ nodes ** k, t ** k, atol=1e-11)
+        np.testing.assert_allclose(dV @ nodes ** k, k * t ** max(k - 1, 0) if k else 0 * t, atol=1e-10)
+
+
+# ---------------------------------------------------------------- closed forms in 3D
+
+def _closed_1d(p, n, h):
+    g = GOLD["element_matrices_unit_interval"]["p%d" % p]
+    Ke = np.array(g["stiffness"], float) * _num(g["stiffness_scale"]) / h
+    Me = np.array(g["mass"], float) * _num(g["mass_scale"]) * h
+    N = p * n + 1
+    K, M = np.zeros((N, N)), np.zeros((N, N))
+    for e in range(n):
+        s = slice(p * e, p * e + p + 1)
+        K[s, s] += Ke
+        M[s, s] += Me
+    return K, M
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_unperturbed_kronecker_closed_form(p):
+    nx, ny, nz = 3, 2, 2
+    mesh = unperturbed(nx, ny, nz)
+    Kx, Mx = _closed_1d(p, nx, 1.0 / nx)
+    Ky, My = _closed_1d(p, ny, 1.0 / ny)
+    Kz, Mz = _closed_1d(p, nz, 1.0 / nz)
+    # global index x fastest -> kron(z, kron(y, x))
+    M3 = np.kron(Mz, np.kron(My, Mx))
+    K3 = np.kron(Mz, np.kron(My, Kx)) + np.kron(Mz, np.kron(Ky, Mx)) + np.kron(Kz, np.kron(My, Mx))
+    np.testing.assert_allclose(O.assemble_csr(mesh, p, p + 2, O.MASS).toarray(), M3, atol=1e-15)
+    np.testing.assert_allclose(O.assemble_csr(mesh, p, p + 2, O.DIFFUSION).toarray(), K3, atol=1e-13)
+
+
+# ---------------------------------------------------------------- invariants on perturbed meshes
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_volume_and_constant_nullspace(p):
+    mesh = perturbed(2, 3, 2, seed=p)
+    M = O.assemble_csr(mesh, p, p + 2, O.MASS)
+    K = O.assemble_csr(mesh, p, p + 2, O.DIFFUSION)
+    one = np.ones(M.shape[0])
+    assert abs(one @ (M @ one) - 1.0) < 1e-14           # 1^T M 1 = |Omega| = 1
+    assert np.abs(K @ one).max() < 1e-12                 # K 1 = 0
+    assert abs((M - M.T)).max() < 1e-16 and abs((K - K.T)).max() < 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_stiffness_psd_one_dim_nullspace(p):
+    mesh = perturbed(2, 2, 2, seed=7)
+    K = O.assemble_csr(mesh, p, p + 2, O.DIFFUSION).toarray()
+    ev = np.linalg.eigvalsh(K)
+    assert ev[0] > -1e-12 and abs(ev[0]) < 1e-12
+    assert ev[1] > 1e-3
+    M = O.assemble_csr(mesh, p, p + 2, O.MASS).toarray()
+    assert np.linalg.eigvalsh(M)[0] > 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_mass_quadrature_exact(p):
+    # phi_a phi_b detJ has degree <= 2p+2 per variable: q = p+2 is exact, so more points change nothing
+    mesh = perturbed(2, 1, 2, seed=3)
+    A = O.assemble_csr(mesh, p, p + 2, O.MASS).toarray()
+    B = O.assemble_csr(mesh, p, p + 6, O.MASS).toarray()
+    np.testing.assert_allclose(A, B, atol=1e-14 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_patch_test_linear(p):
+    # For a linear field u, adj(J)^T grad-hat(phi) . a has degree <= p+2 per variable, so the
+    # quadrature is exact and interior rows of K u_I vanish.
+    mesh = perturbed(3, 2, 2, seed=11)
+    K = O.assemble_csr(mesh, p, p + 2, O.DIFFUSION)
+    xyz = O.node_coords(mesh, p)
+    u = 0.3 + 1.1 * xyz[:, 0] - 0.7 * xyz[:, 1] + 2.3 * xyz[:, 2]
+    interior = np.setdiff1d(np.arange(len(u)), O.boundary_dofs(mesh, p))
+    assert np.abs((K @ u)[interior]).max() < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dirichlet_solve_reproduces_linear(p):
+    mesh = perturbed(2, 3, 2, seed=5)
+    prob = O.Problem(mesh, p, None, O.DIFFUSION)
+    xyz = O.node_coords(mesh, p)
+    u = 0.3 + 1.1 * xyz[:, 0] - 0.7 * xyz[:, 1] + 2.3 * xyz[:, 2]
+    ess = prob.ess
+    b = -(prob.A @ np.where(np.isin(np.arange(len(u)), ess), u, 0.0))   # lift of the boundary data
+    b[ess] = u[ess]
+    x, it, res = prob.solve(b, rtol=1e-14)
+    np.testing.assert_allclose(x, u, atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_mass_projection_reproduces_polynomials(p):
+    # u of total degree <= p in physical coordinates is in Q_p after the trilinear map, and
+    # the load-vector quadrature is exact, so M c = b(u) returns the nodal values of u.
+    mesh = perturbed(2, 2, 3, seed=13)
+    M = O.assemble_csr(mesh, p, p + 2, O.MASS).toarray()
+    def u(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return (0.5 + X - 2 * Y + 0.25 * Z) ** p + (X * Y if p >= 2 else 0.0)
+    b = O.rhs_from_qp(mesh, p, p + 2, u(O.qp_coords(mesh, p, p + 2)))
+    c = sla.solve(M, b, assume_a="pos")
+    np.testing.assert_allclose(c, u(O.node_coords(mesh, p)), atol=1e-10)
+
+
+# ---------------------------------------------------------------- brute force and internal consistency
+
+@pytest.mark.parametrize("form", [O.MASS, O.DIFFUSION])
+@pytest.mark.parametrize("p,shape", [(1, (2, 2, 2)), (2, (2, 1, 2)), (3, (1, 2, 1))])
+def test_bruteforce_equals_csr(form, p, shape):
+    mesh = perturbed(*shape, seed=17)
+    A = O.assemble_csr(mesh, p, p + 2, form).toarray()
+    B = O.dense_bruteforce(mesh, p, p + 2, form)
+    np.testing.assert_allclose(A, B, atol=1e-13 * np.abs(B).max())
+
+
+@pytest.mark.parametrize("form", [O.MASS, O.DIFFUSION])
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_elementwise_action_rows_diag_match_csr(form, p):
+    mesh = perturbed(3, 2, 2, seed=19)
+    prob = O.Problem(mesh, p, None, form)
+    x = FI.uniform_vector(prob.N, seed=1)
+    for constrained in (False, True):
+        ess = prob.ess if constrained else None
+        y = (prob.Ac if constrained else prob.A) @ x
+        y2 = O.action_elementwise(mesh, p, p + 2, form, x, ess=ess)
+        np.testing.assert_allclose(y2, y, atol=1e-13 * np.abs(y).max())
+        rows = np.random.default_rng(0).choice(prob.N, 25, replace=False)
+        np.testing.assert_allclose(O.action_rows(mesh, p, p + 2, form, x, rows, ess=ess), y[rows],
+                                   atol=1e-13 * np.abs(y).max())
+        d = O.diagonal_elementwise(mesh, p, p + 2, form, ess=ess)
+        np.testing.assert_allclose(d, (prob.Ac if constrained else prob.A).diagonal(), rtol=1e-13)
+
+
+def test_rhs_of_one_is_mass_times_one():
+    mesh = perturbed(2, 2, 2, seed=23)
+    for p in (1, 2, 4):
+        b = O.rhs_from_qp(mesh, p, p + 2, np.ones((mesh.num_elements, (p + 2) ** 3)))
+        M = O.assemble_csr(mesh, p, p + 2, O.MASS)
+        np.testing.assert_allclose(b, M @ np.ones(M.shape[0]), atol=1e-15)
+        assert abs(b.sum() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("form", [O.MASS, O.DIFFUSION])
+def test_cg_matches_dense_solve(form):
+    mesh = perturbed(3, 3, 2, seed=29)
+    prob = O.Problem(mesh, 2, None, form)
+    b = prob.sine_rhs()
+    x, it, res = prob.solve(b, rtol=1e-13)
+    xd = sla.solve(prob.Ac.toarray(), b, assume_a="pos")
+    assert res <= 1e-13
+    assert np.linalg.norm(x - xd) <= 1e-11 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_convergence_rate(p):
+    errs = []
+    ns = (2, 4, 8) if p < 3 else (2, 4, 6)
+    for n in ns:
+        mesh = perturbed(n, n, n, seed=31)
+        prob = O.Problem(mesh, p, None, O.DIFFUSION)
+        x, it, res = prob.solve(prob.sine_rhs(), rtol=1e-12)
+        errs.append(O.l2_error(mesh, p, x, O.sine_solution))
+    rate = math.log(errs[-2] / errs[-1]) / math.log(ns[-1] / ns[-2])
+    assert rate > p + 1 - 0.35, (errs, rate)
+
+
+def test_planted_transpose_mistake_is_caught(monkeypatch):
+    # Using J^{-T} J^{-1} in place of J^{-1} J^{-T} (a transposed Jacobian) must fail the
+    # linear patch test on a perturbed mesh: the pins are sensitive to it.
+    orig = O.fem_oracle.qp_factors
+
+    def wrong(X, R, form):
+        F = orig(X, R, form)
+        if form != O.DIFFUSION:
+            return F
+        _, J = O.trilinear(X, R.xi)
+        Jinv = np.linalg.inv(J)
+        wdet = R.w[None, :] * np.linalg.det(J)
+        return wdet[..., None, None] * np.einsum("emdr,emds->emrs", Jinv, Jinv)
+
+    monkeypatch.setattr(O.fem_oracle, "qp_factors", wrong)
+    mesh = perturbed(3, 2, 2, seed=11)
+    K = O.fem_oracle.assemble_csr(mesh, 2, 4, O.DIFFUSION)
+    xyz = O.node_coords(mesh, 2)
+    u = 0.3 + 1.1 * xyz[:, 0] - 0.7 * xyz[:, 1] + 2.3 * xyz[:, 2]
+    interior = np.setdiff1d(np.arange(len(u)), O.boundary_dofs(mesh, 2))
+    assert np.abs((K @ u)[interior]).max() > 1e-6
