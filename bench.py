@@ -1,0 +1,342 @@
+"""Benchmark: BP3 (H1 diffusion) Jacobi-PCG throughput, GDOF/s per CG iteration.
+
+One step = one pass of the whole hot path over one synthetic problem:
+geometry setup D from the (device-resident) vertices, load vector of the sine
+manufactured solution, matrix-free diagonal, and the Jacobi-PCG solve to a relative
+residual of 1e-10 (every iteration applies the fused G^T B^T D B G kernel).
+value = N * (CG iterations) / step time, summed over ranks (independent replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import fem_inputs as FI  # noqa: E402
+
+METRIC = "BP3 GDOF/s per CG iter (FP64 vs mixed+refine)"
+UNIT = "GDOF/s"
+
+
+def workload_name(p, n, q):
+    N = (p * n + 1) ** 3
+    return (f"BP3 diffusion, p={p}, q={q}, {n}^3 perturbed trilinear hexes (+-0.1h), N={N} DOFs, "
+            f"sine manufactured RHS, homogeneous Dirichlet, Jacobi PCG to 1e-10")
+
+
+def flops_per_elem(n, q, form):
+    """Algorithmic flops of one element's sum-factorised action (standard 3-stage
+    contractions forward and transposed, plus the pointwise D)."""
+    if form == "mass":
+        return 4 * n * q * (n * n + n * q + q * q) + q ** 3
+    return 2 * (4 * n ** 3 * q + 6 * n * n * q * q + 6 * n * q ** 3) + 15 * q ** 3
+
+
+def bytes_per_elem(n, q, form, p, nelem_per_dim):
+    """Algorithmic HBM bytes of one action per element: D, the element->DOF map and
+    x/y once per global DOF."""
+    ncomp = 6 if form == "diffusion" else 1
+    N = (p * nelem_per_dim + 1) ** 3
+    E = nelem_per_dim ** 3
+    return 8 * ncomp * q ** 3 + 4 * n ** 3 + 16.0 * N / E
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smmax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+# nominal FP64 rate of the B300 (no FP64 tensor-core path); the FP64 pipe bounds this kernel
+FP64_PEAK_GFLOPS = 1250.0
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(p, n_sample, seed=0):
+    """One bounded sample of the workload on the CPU oracle: same p, form, mesh recipe
+    and solver, on n_sample^3 elements.  Returns (DOF-iterations, seconds, iterations)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    mesh = O.HexGridMesh(n_sample, n_sample, n_sample, FI.perturbed_cube_vertices(n_sample, n_sample, n_sample,
+                                                                                   seed=seed))
+    prob = O.Problem(mesh, p, None, O.DIFFUSION)
+    b = prob.sine_rhs()
+    x, it, res = prob.solve(b, rtol=1e-10)
+    dt = time.perf_counter() - t0
+    return prob.N * it, dt, it
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    p, n_s = args.p, args.oracle_n
+    for _ in range(args.warmup):
+        oracle_sample(p, n_s)
+    tot_dofit, tot_t, its = 0, 0.0, []
+    for _ in range(args.steps):
+        d, t, it = oracle_sample(p, n_s)
+        tot_dofit += d
+        tot_t += t
+        its.append(it)
+    value = tot_dofit / tot_t / 1e9
+    sample = (f"oracle (CSR assembly by quadrature + Jacobi PCG to 1e-10, numpy/scipy) on {n_s}^3 elements, "
+              f"p={p}, N={(p * n_s + 1) ** 3}; timed: assembly, load vector, solve")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(p, args.n, p + 2), "sample": sample},
+            "iterations": its,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import paper_2402_15940_b300 as F
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    p, n = args.p, args.n
+    verts_np = FI.perturbed_cube_vertices(n, n, n, seed=rank)
+    op = F.Operator(n, n, n, verts_np, p, form="diffusion")
+    q, N, E = op.q, op.N, op.E
+    op.set_essential(op.boundary_dofs())
+    verts = torch.from_numpy(verts_np).cuda()
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    scale = 3 * math.pi ** 2
+
+    def step():
+        op.set_vertices(verts)          # D from the trilinear map
+        op.rhs_sine(scale, out=b)       # load vector
+        x.zero_()
+        _, st = op.solve(b, x, rtol=args.rtol, maxit=args.maxit)   # diagonal + Jacobi PCG
+        return st
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = F.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            iters.append(step()["iterations"])
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = F.launch_count() - l0
+    t = ev0.elapsed_time(ev1) / 1e3
+    dofit = N * sum(iters)
+    if dist is not None:
+        tt = torch.tensor([t, float(dofit)], dtype=torch.float64, device="cuda")
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_all, dofit_all = float(tmax[0]), float(tt[1])
+    else:
+        t_all, dofit_all = t, float(dofit)
+    value = dofit_all / t_all / 1e9
+
+    # dominant kernel: the fused action, timed alone on the same stream with CUDA events
+    xr = torch.from_numpy(FI.uniform_vector(N, seed=1)).cuda()
+    yr = torch.empty_like(xr)
+    for _ in range(3):
+        op.apply(xr, out=yr)
+    reps = 20
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    k0.record()
+    for _ in range(reps):
+        op.apply(xr, out=yr)
+    k1.record()
+    torch.cuda.synchronize()
+    t_apply = k0.elapsed_time(k1) / 1e3 / reps
+    fl = flops_per_elem(p + 1, q, "diffusion") * E
+    achieved = fl / t_apply / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": args.traffic,
+            "kernel": f"pa_apply_f64<{p},{q},diffusion>", "apply_ms": t_apply * 1e3,
+            "apply_gdofs": N / t_apply / 1e9,
+            "peak_note": "FP64 pipe, nominal 1.25 TFLOP/s (B300); a DFMA microbenchmark measured 0.95 TFLOP/s",
+            "algorithmic_bytes_per_launch": bytes_per_elem(p + 1, q, "diffusion", p, n) * E}
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.from_numpy(verts_np).pin_memory().numpy()
+        bh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        bh[:] = b.cpu().numpy()
+        xh = torch.zeros(N, dtype=torch.float64).pin_memory().numpy()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e_its = 0
+        for _ in range(args.steps):
+            op.set_vertices(vh)
+            xh[:] = 0.0
+            _, st = op.solve_host(bh, xh, rtol=args.rtol, maxit=args.maxit)
+            e_its += st["iterations"]
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([te, float(N * e_its)], dtype=torch.float64, device="cuda")
+            tm = tt[:1].clone()
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+            te, e_dofit = float(tm[0]), float(tt[1])
+        else:
+            e_dofit = float(N * e_its)
+        e2e = {"value": e_dofit / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(vh.nbytes + 2 * bh.nbytes),
+               "d2h_bytes_per_step": int(xh.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d, tcpu, it = oracle_sample(p, args.oracle_n)
+        cpu = {"value": d / tcpu / 1e9, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"oracle CSR assembly + Jacobi PCG to 1e-10 on {args.oracle_n}^3 elements, p={p}, "
+                         f"N={(p * args.oracle_n + 1) ** 3}, {it} iterations, {tcpu:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name(p, n, q), "precision": "fp64",
+                           "l2": "inputs larger than L2 (D alone is %.2f GB)" % (E * 6 * q ** 3 * 8 / 1e9),
+                           "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
+                "iterations_per_step": iters, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--oracle-n", type=int, default=12)
+    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per apply launch from ncu")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        return run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * fepa.h -- matrix-free partial-assembly (PA) finite element operators and their
+ * Jacobi-preconditioned CG solve, for H1 mass and diffusion on hexahedral meshes,
+ * on one NVIDIA B300 (sm_103a).
+ *
+ * What the calls compute (arXiv 2402.15940):
+ *   The operator is the decomposition A = P^T G^T B^T D B G P of Fig. "fig_feod"
+ *   (Sec. 3.5).  On one GPU with a conforming mesh P = I.  G maps the global
+ *   (L-vector) DOFs to element DOFs (E-vector) and G^T sums them back; B evaluates
+ *   values or reference gradients at the quadrature points (Q-vector) by sum
+ *   factorisation of the tensor-product basis (Sec. 2.1); D is the pointwise
+ *   quadrature-point factor, the only data partial assembly stores (Sec. 2.2,
+ *   "Partial Assembly").  Forms: the CEED bake-off operators BP1 (mass) and BP3
+ *   (diffusion) named in Sec. 2.2.  The solver is CG with the matrix-free
+ *   diagonal as preconditioner (Sec. 2.1), run as fused device kernels with
+ *   warp-level dot products (Sec. 2.3).
+ *
+ * Discretisation (choices the paper leaves open; the same choices as the CPU
+ * oracle's readings):
+ *   - reference element [0,1]^3; Lagrange basis of order p on the Gauss-Lobatto-
+ *     Legendre nodes; Gauss-Legendre quadrature with q points per direction;
+ *   - mesh: structured grid of (nx+1)(ny+1)(nz+1) vertices at arbitrary positions
+ *     (x index fastest), element (ex,ey,ez) = ex + nx*(ey + ny*ez), trilinear map;
+ *   - global DOFs: the (p*nx+1)(p*ny+1)(p*nz+1) node grid, x fastest; element-local
+ *     DOF a + (p+1)*(b + (p+1)*c);
+ *   - mass: D = w*det(J); diffusion: D = w*adj(J)adj(J)^T/det(J) (symmetric 3x3,
+ *     6 stored components xx, xy, xz, yy, yz, zz);
+ *   - Dirichlet (essential) DOFs: the constrained operator (I-E) A (I-E) + E.
+ *
+ * Conventions:
+ *   - Every int-returning call returns FEPA_OK (0) or a negative FEPA_ERR_* code and
+ *     then fepa_last_error() holds a message (thread-local).  Nothing aborts or traps.
+ *   - "device" pointers are CUDA global-memory pointers of the op's device; "host"
+ *     pointers are ordinary CPU memory.  The caller owns every buffer it passes in;
+ *     the library owns the fepa_op handle and the device arrays inside it.
+ *   - All device work is enqueued on the op's stream (given at creation, may be 0 for
+ *     the legacy default stream) and is asynchronous with respect to the host unless
+ *     a call says otherwise.
+ *   - Floating point is IEEE binary64 unless a call says otherwise.
+ */
+#ifndef FEPA_H
+#define FEPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FEPA_OK 0
+#define FEPA_ERR_ARG (-1)         /* invalid argument (null pointer, size, order ...) */
+#define FEPA_ERR_OOM (-2)         /* device allocation failed */
+#define FEPA_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define FEPA_ERR_MESH (-4)        /* non-positive Jacobian determinant at a quadrature point */
+#define FEPA_ERR_NOCONV (-5)      /* CG reached maxit before the tolerance */
+#define FEPA_ERR_UNSUPPORTED (-7) /* order / quadrature outside the compiled range */
+
+/* bilinear forms */
+#define FEPA_MASS 0       /* BP1: (u, v) */
+#define FEPA_DIFFUSION 1  /* BP3: (grad u, grad v) */
+
+/* preconditioners */
+#define FEPA_PRECOND_NONE 0
+#define FEPA_PRECOND_JACOBI 1
+
+/* compiled range: 1 <= p <= FEPA_MAX_ORDER, q = p+1 .. p+2 (q1d > p) */
+#define FEPA_MAX_ORDER 8
+
+typedef struct fepa_op fepa_op; /* opaque: mesh + H1 space + form + stored D */
+
+typedef struct fepa_cg_stats {
+  int32_t iterations;     /* operator applications inside the loop */
+  int32_t status;         /* FEPA_OK or FEPA_ERR_NOCONV */
+  double rel_residual;    /* ||r_k||_2 / ||b||_2 at exit */
+  double precond_norm;    /* sqrt(z_k . r_k) at exit (preconditioned residual norm) */
+  double b_norm;          /* ||b||_2 */
+} fepa_cg_stats;
+
+/* Version string of the library build. */
+const char* fepa_version(void);
+
+/* Thread-local message describing the last error returned on this thread. */
+const char* fepa_last_error(void);
+
+/* Number of this library's kernel launches so far in this process (graph-launched
+ * kernels included, counted by executed iterations).  Used to attribute GPU work. */
+int64_t fepa_launch_count(void);
+
+/*
+ * Create an operator on the current CUDA device.
+ *   nx, ny, nz    elements per direction (>= 1)
+ *   vertices      host, ((nx+1)*(ny+1)*(nz+1)) x 3 doubles, row-major, x index fastest
+ *   p             polynomial order, 1..FEPA_MAX_ORDER
+ *   q1d           Gauss points per direction; 0 selects p+2; allowed p+1 or p+2
+ *   form          FEPA_MASS or FEPA_DIFFUSION
+ *   stream        cudaStream_t (as void*) on which all work of this op is enqueued
+ * Builds G (element->DOF map), the 1D tables of B, and D (Sec. 2.2, partial
+ * assembly: the quadrature-point data is computed once and stored).  Blocks until D
+ * is built and returns FEPA_ERR_MESH if any det(J) <= 0.  No essential DOFs are set.
+ */
+int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, int32_t p, int32_t q1d,
+                   int32_t form, void* stream, fepa_op** out);
+
+/*
+ * Move the mesh: replace the vertex coordinates (same nx, ny, nz) and rebuild D.
+ *   vertices     ((nx+1)*(ny+1)*(nz+1)) x 3 doubles, host or device memory
+ *   on_device    0: vertices is a host pointer; 1: a device pointer
+ * Blocks until D is rebuilt; returns FEPA_ERR_MESH (D then undefined) if any
+ * det(J) <= 0.  Invalidates the cached diagonal.
+ */
+int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device);
+
+/* Release the op and every device array it owns (synchronises its stream). */
+void fepa_op_destroy(fepa_op* op);
+
+/* Sizes: global DOFs N, elements E, q1d, number of stored D components per
+ * quadrature point (1 mass, 6 diffusion). */
+int64_t fepa_op_ndofs(const fepa_op* op);
+int64_t fepa_op_nelems(const fepa_op* op);
+int32_t fepa_op_q1d(const fepa_op* op);
+int32_t fepa_op_dcomps(const fepa_op* op);
+
+/* Change the stream subsequent work of this op is enqueued on. */
+int fepa_op_set_stream(fepa_op* op, void* stream);
+
+/* Boundary DOFs of the node grid, ascending, written to dofs (host, capacity
+ * entries); *count receives the total (which may exceed capacity: then nothing
+ * is written and FEPA_ERR_ARG is returned). dofs may be null to query the count. */
+int fepa_op_boundary_dofs(const fepa_op* op, int32_t* dofs, int64_t capacity, int64_t* count);
+
+/* Set the essential (Dirichlet) DOF list (host, count entries, each in [0,N)).
+ * Replaces any previous list; count = 0 clears it.  Synchronous. */
+int fepa_op_set_essential(fepa_op* op, const int32_t* dofs, int64_t count);
+
+/* Copy of G: element-local to global DOF map, device int32 [E][(p+1)^3]
+ * (essential DOFs appear unflagged). */
+int fepa_op_elem_dofs(const fepa_op* op, int32_t* out);
+
+/* Copy of D: device double [E][dcomps][q^3], quadrature point i + q*(j + q*k). */
+int fepa_op_qdata(const fepa_op* op, double* out);
+
+/* Physical coordinates of the quadrature points: device double [E][q^3][3]. */
+int fepa_op_qp_coords(const fepa_op* op, double* out);
+
+/*
+ * y = A x (Fig. fig_feod: G^T B^T D B G), with the constrained form
+ * y = (I-E) A (I-E) x + E x when essential DOFs are set.
+ *   x, y   device, N doubles each; must not overlap.
+ */
+int fepa_op_apply(fepa_op* op, const double* x, double* y);
+
+/* diag(A) (of the constrained operator: 1 on essential rows), computed without
+ * assembling A by sum factorisation (Sec. 2.1).  diag: device, N doubles. */
+int fepa_op_diagonal(fepa_op* op, double* diag);
+
+/* b = G^T B^T (w det(J) f): load vector of f given at the quadrature points.
+ *   f_qp  device double [E][q^3]; b device, N doubles (overwritten).
+ * Essential rows are left as computed (the caller sets boundary values). */
+int fepa_op_rhs(fepa_op* op, const double* f_qp, double* b);
+
+/* As fepa_op_rhs with f = scale * sin(pi x) sin(pi y) sin(pi z) evaluated in-kernel
+ * at the physical quadrature points, and essential rows of b set to 0
+ * (homogeneous Dirichlet data, the manufactured problem). */
+int fepa_op_rhs_sine(fepa_op* op, double scale, double* b);
+
+/*
+ * Solve A x = b by CG, preconditioned with diag(A) (FEPA_PRECOND_JACOBI) or not.
+ *   b      device, N doubles
+ *   x      device, N doubles: initial guess on entry, solution on exit
+ *   rtol   stop when ||r_k||_2 <= rtol * ||b||_2
+ *   maxit  iteration limit (>= 1)
+ *   stats  host, may be null
+ * Iterations run on the device inside one CUDA graph with a device-side loop
+ * condition; the call blocks until the solve ends.  Returns FEPA_ERR_NOCONV (with
+ * stats filled and x holding the last iterate) if maxit is reached first.
+ */
+int fepa_cg_solve(fepa_op* op, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
+                  fepa_cg_stats* stats);
+
+/* As fepa_cg_solve with HOST b and x (N doubles each): copies b and x to the device,
+ * solves, copies x back; blocks until done. */
+int fepa_cg_solve_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t maxit,
+                       int32_t precond, fepa_cg_stats* stats);
+
+/*
+ * Fixed-count CG iterations (no stopping test) for timing the per-iteration cost:
+ * runs exactly `iters` iterations from x (device), preconditioned like fepa_cg_solve.
+ * stats->rel_residual holds the residual after them.  Blocks until done.
+ */
+int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, int32_t precond,
+                       fepa_cg_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEPA_H */

@@ -270,8 +270,12 @@ def element_matrices(X: np.ndarray, p: int, q: int, form: str) -> np.ndarray:
     R = rule(p, q)
     F = qp_factors(X, R, form)
     if form == MASS:
-        return np.einsum("ma,em,mb->eab", R.Phi, F, R.Phi, optimize=True)
-    return np.einsum("mar,emrs,mbs->eab", R.dPhi, F, R.dPhi, optimize=True)
+        return np.matmul(R.Phi.T[None, :, :] * F[:, None, :], R.Phi[None, :, :])
+    # Ke[a,b] = sum_{pt,r} dPhi[pt,a,r] V[pt,r,b] with V[pt,r,b] = sum_s F[pt,r,s] dPhi[pt,b,s]
+    m, n3 = R.dPhi.shape[0], R.dPhi.shape[1]
+    V = np.einsum("emrs,mbs->emrb", F, R.dPhi, optimize=True).reshape(X.shape[0], m * 3, n3)
+    Pt = R.dPhi.transpose(1, 0, 2).reshape(n3, m * 3)
+    return np.matmul(Pt[None, :, :], V)
 
 
 def assemble_csr(mesh: HexGridMesh, p: int, q: int, form: str) -> sp.csr_matrix:

@@ -1,0 +1,10 @@
+"""B300-native matrix-free partial-assembly finite elements (arXiv 2402.15940, hot path).
+
+The compute path is libfepa.so (hand-written sm_103a CUDA behind a C ABI, see
+include/fepa.h); this package is its thin Python binding.
+"""
+from .fepa import (DIFFUSION, MASS, PRECOND_JACOBI, PRECOND_NONE, CgStats, FepaError, Operator, launch_count,
+                   load_library, LIB_PATH)
+
+__all__ = ["Operator", "FepaError", "CgStats", "MASS", "DIFFUSION", "PRECOND_NONE", "PRECOND_JACOBI",
+           "launch_count", "load_library", "LIB_PATH"]

@@ -1,0 +1,205 @@
+// Conjugate-gradient vector kernels with device-resident scalars (arXiv 2402.15940,
+// Sec. 2.3: CG built from 1D vector kernels, the 3D operator kernel, warp-level dot
+// products and a synchronisation mechanism).  Here each dot product is reduced with
+// warp shuffles, then per block, then by the last block to finish (a ticket counter,
+// no spinning), which also computes the CG scalars on the device.  The iteration loop
+// itself runs inside a CUDA graph whose while-condition the last kernel sets, so the
+// host never waits per iteration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fepa {
+
+struct CgState {
+  double rho;       // (z, r)
+  double alpha;     // rho / (d, h)
+  double beta;      // rho_new / rho
+  double bb;        // ||b||^2
+  double rr;        // ||r||^2
+  double tol2;      // rtol^2 ||b||^2
+  int iter;         // iterations done
+  int maxit;
+  int done;         // set when converged or maxit reached
+  int converged;
+  unsigned int ticket;
+  int pad;
+};
+
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce NV values; thread 0 returns the sums in out[].
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (&out)[NV]) {
+  __shared__ double red[NV][RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) red[k][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) s += red[k][w];
+      out[k] = s;
+    }
+  }
+}
+
+// Publish this block's partial sums; returns true (in thread 0) for the last block to
+// arrive, after which partials[] of every block are visible to it.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(double (&blk)[NV], double* partials, unsigned int* ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * gridDim.x + blockIdx.x] = blk[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// Fixed-order final sum over block partials (deterministic for a fixed grid).
+template <int NV>
+__device__ __forceinline__ void final_sums(const double* partials, double (&out)[NV]) {
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    v[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v[k] += __ldcg(partials + k * gridDim.x + b);
+  }
+  block_sum<NV>(v, out);
+}
+
+// r = b - h; z = r * inv_diag (or r); d = z; h = 0; rho = (z,r), rr = (r,r), bb = (b,b)
+__global__ void __launch_bounds__(RED_THREADS)
+cg_init(int64_t N, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ d,
+        double* __restrict__ h, const double* __restrict__ inv_diag, CgState* st, double rtol2, int maxit,
+        double* partials) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - h[i];
+    const double zi = inv_diag ? ri * inv_diag[i] : ri;
+    r[i] = ri;
+    d[i] = zi;
+    h[i] = 0.0;
+    v[0] += zi * ri;
+    v[1] += ri * ri;
+    v[2] += bi * bi;
+  }
+  double blk[3];
+  block_sum<3>(v, blk);
+  if (publish_partials<3>(blk, partials, &st->ticket)) {
+    double tot[3];
+    final_sums<3>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->rho = tot[0];
+      st->rr = tot[1];
+      st->bb = tot[2];
+      st->tol2 = rtol2 * tot[2];
+      st->iter = 0;
+      st->maxit = maxit;
+      st->converged = (tot[1] <= st->tol2) ? 1 : 0;
+      st->done = st->converged;
+      st->alpha = st->beta = 0.0;
+      st->ticket = 0;
+    }
+  }
+}
+
+// alpha = rho / (d, h)
+__global__ void __launch_bounds__(RED_THREADS)
+cg_dot_dh(int64_t N, const double* __restrict__ d, const double* __restrict__ h, CgState* st, double* partials) {
+  if (st->done) return;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += d[i] * h[i];
+  double blk[1];
+  block_sum<1>(v, blk);
+  if (publish_partials<1>(blk, partials, &st->ticket)) {
+    double tot[1];
+    final_sums<1>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->alpha = st->rho / tot[0];
+      st->ticket = 0;
+    }
+  }
+}
+
+// x += alpha d; r -= alpha h; rho_new = (z, r) with z = r * inv_diag; rr = (r, r);
+// then the stopping test and beta.
+__global__ void __launch_bounds__(RED_THREADS)
+cg_update(int64_t N, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
+          const double* __restrict__ h, const double* __restrict__ inv_diag, CgState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * d[i];
+    const double ri = r[i] - alpha * h[i];
+    r[i] = ri;
+    const double zi = inv_diag ? ri * inv_diag[i] : ri;
+    v[0] += zi * ri;
+    v[1] += ri * ri;
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      st->rr = tot[1];
+      if (tot[1] <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (st->iter >= st->maxit) {
+        st->done = 1;
+      }
+      st->beta = tot[0] / st->rho;
+      st->rho = tot[0];
+      st->ticket = 0;
+    }
+  }
+}
+
+// d = z + beta d; h = 0.  Block 0 sets the graph's while-condition to !done.
+__global__ void __launch_bounds__(RED_THREADS)
+cg_direction(int64_t N, const double* __restrict__ r, double* __restrict__ d, double* __restrict__ h,
+             const double* __restrict__ inv_diag, const CgState* st, cudaGraphConditionalHandle cond,
+             int use_cond) {
+  const int done = st->done;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (done) return;
+  const double beta = st->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+    d[i] = zi + beta * d[i];
+    h[i] = 0.0;
+  }
+}
+
+__global__ void reciprocal(int64_t N, const double* __restrict__ a, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 1.0 / a[i];
+}
+
+__global__ void set_rows(int64_t count, const int* __restrict__ rows, double value, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    v[rows[i]] = value;
+}
+
+}  // namespace fepa

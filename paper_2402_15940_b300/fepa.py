@@ -1,0 +1,279 @@
+"""Python binding of the C-ABI library (include/fepa.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libfepa.so; torch provides device
+memory and the current stream.  There is no CPU fallback: if the library is
+missing, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfepa.so")
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_MESH, ERR_NOCONV, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
+MASS, DIFFUSION = 0, 1
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+MAX_ORDER = 8
+
+_FORMS = {"mass": MASS, "diffusion": DIFFUSION, MASS: MASS, DIFFUSION: DIFFUSION}
+_PRECONDS = {"none": PRECOND_NONE, "jacobi": PRECOND_JACOBI, None: PRECOND_NONE,
+             PRECOND_NONE: PRECOND_NONE, PRECOND_JACOBI: PRECOND_JACOBI}
+
+# (name, restype, argtypes) of every exported symbol; the CPU test checks them against the header.
+_P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("precond_norm", ctypes.c_double), ("b_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SIGNATURES = [
+    ("fepa_version", ctypes.c_char_p, []),
+    ("fepa_last_error", ctypes.c_char_p, []),
+    ("fepa_launch_count", _I64, []),
+    ("fepa_op_create", ctypes.c_int, [_I32, _I32, _I32, _P, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    ("fepa_op_set_vertices", ctypes.c_int, [_P, _P, _I32]),
+    ("fepa_op_destroy", None, [_P]),
+    ("fepa_op_ndofs", _I64, [_P]),
+    ("fepa_op_nelems", _I64, [_P]),
+    ("fepa_op_q1d", _I32, [_P]),
+    ("fepa_op_dcomps", _I32, [_P]),
+    ("fepa_op_set_stream", ctypes.c_int, [_P, _P]),
+    ("fepa_op_boundary_dofs", ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
+    ("fepa_op_set_essential", ctypes.c_int, [_P, _P, _I64]),
+    ("fepa_op_elem_dofs", ctypes.c_int, [_P, _P]),
+    ("fepa_op_qdata", ctypes.c_int, [_P, _P]),
+    ("fepa_op_qp_coords", ctypes.c_int, [_P, _P]),
+    ("fepa_op_apply", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_op_diagonal", ctypes.c_int, [_P, _P]),
+    ("fepa_op_rhs", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_op_rhs_sine", ctypes.c_int, [_P, _D, _P]),
+    ("fepa_cg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_cg_solve_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_cg_iterations", ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.POINTER(CgStats)]),
+]
+
+
+class FepaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fepa error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfepa.so (built by paper_2402_15940_b300.build) and declare its symbols."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2402_15940_b300.build`")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise FepaError(rc, load_library().fepa_last_error().decode())
+
+
+def launch_count() -> int:
+    return int(load_library().fepa_launch_count())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("fepa needs a CUDA device; no CPU fallback exists")
+    return torch
+
+
+def _dev_ptr(t, dtype, numel, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """A partial-assembly operator: structured hex mesh + H1 space of order p + form + D."""
+
+    def __init__(self, nx, ny, nz, vertices, p, form="diffusion", q=0):
+        torch = _torch()
+        lib = load_library()
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        if v.shape != ((nx + 1) * (ny + 1) * (nz + 1), 3):
+            raise ValueError("vertices must have shape ((nx+1)(ny+1)(nz+1), 3)")
+        self._lib = lib
+        self.nx, self.ny, self.nz, self.p = int(nx), int(ny), int(nz), int(p)
+        self.form = _FORMS[form]
+        h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream
+        _check(lib.fepa_op_create(self.nx, self.ny, self.nz, v.ctypes.data_as(ctypes.c_void_p), self.p, int(q),
+                                  self.form, ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._h = h
+        self.N = int(lib.fepa_op_ndofs(h))
+        self.E = int(lib.fepa_op_nelems(h))
+        self.q = int(lib.fepa_op_q1d(h))
+        self.dcomps = int(lib.fepa_op_dcomps(h))
+        self.n = self.p + 1
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fepa_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        torch = _torch()
+        _check(self._lib.fepa_op_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def _vec(self, out):
+        torch = _torch()
+        return torch.empty(self.N, dtype=torch.float64, device="cuda") if out is None else out
+
+    def set_vertices(self, vertices):
+        """New vertex positions (numpy host array or CUDA float64 tensor); rebuilds D."""
+        torch = _torch()
+        nv = (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+        self._sync_stream()
+        if isinstance(vertices, torch.Tensor):
+            ptr = _dev_ptr(vertices, torch.float64, 3 * nv, "vertices")
+            _check(self._lib.fepa_op_set_vertices(self._h, ptr, 1))
+        else:
+            v = np.ascontiguousarray(vertices, dtype=np.float64)
+            if v.size != 3 * nv:
+                raise ValueError("vertices has the wrong size")
+            _check(self._lib.fepa_op_set_vertices(self._h, v.ctypes.data_as(ctypes.c_void_p), 0))
+
+    # -- space and data
+    def boundary_dofs(self) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        _check(self._lib.fepa_op_boundary_dofs(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.int32)
+        _check(self._lib.fepa_op_boundary_dofs(self._h, out.ctypes.data_as(ctypes.c_void_p), cnt.value,
+                                               ctypes.byref(cnt)))
+        return out
+
+    def set_essential(self, dofs):
+        d = np.ascontiguousarray(dofs, dtype=np.int32)
+        self._sync_stream()
+        _check(self._lib.fepa_op_set_essential(self._h, d.ctypes.data_as(ctypes.c_void_p), len(d)))
+
+    def elem_dofs(self):
+        torch = _torch()
+        out = torch.empty((self.E, self.n ** 3), dtype=torch.int32, device="cuda")
+        self._sync_stream()
+        _check(self._lib.fepa_op_elem_dofs(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def qdata(self):
+        torch = _torch()
+        out = torch.empty((self.E, self.dcomps, self.q ** 3), dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        _check(self._lib.fepa_op_qdata(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def qp_coords(self):
+        torch = _torch()
+        out = torch.empty((self.E, self.q ** 3, 3), dtype=torch.float64, device="cuda")
+        self._sync_stream()
+        _check(self._lib.fepa_op_qp_coords(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    # -- operator
+    def apply(self, x, out=None):
+        torch = _torch()
+        y = self._vec(out)
+        px = _dev_ptr(x, torch.float64, self.N, "x")
+        py = _dev_ptr(y, torch.float64, self.N, "y")
+        self._sync_stream()
+        _check(self._lib.fepa_op_apply(self._h, px, py))
+        return y
+
+    def diagonal(self, out=None):
+        torch = _torch()
+        y = self._vec(out)
+        self._sync_stream()
+        _check(self._lib.fepa_op_diagonal(self._h, _dev_ptr(y, torch.float64, self.N, "diag")))
+        return y
+
+    def rhs(self, f_qp, out=None):
+        torch = _torch()
+        b = self._vec(out)
+        pf = _dev_ptr(f_qp, torch.float64, self.E * self.q ** 3, "f_qp")
+        self._sync_stream()
+        _check(self._lib.fepa_op_rhs(self._h, pf, _dev_ptr(b, torch.float64, self.N, "b")))
+        return b
+
+    def rhs_sine(self, scale=1.0, out=None):
+        torch = _torch()
+        b = self._vec(out)
+        self._sync_stream()
+        _check(self._lib.fepa_op_rhs_sine(self._h, float(scale), _dev_ptr(b, torch.float64, self.N, "b")))
+        return b
+
+    # -- solver
+    def solve(self, b, x=None, rtol=1e-10, maxit=10000, precond="jacobi", raise_on_noconv=True):
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = CgStats()
+        self._sync_stream()
+        rc = self._lib.fepa_cg_solve(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                     _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(maxit),
+                                     _PRECONDS[precond], ctypes.byref(st))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        return x, st.as_dict()
+
+    def solve_host(self, b, x=None, rtol=1e-10, maxit=10000, precond="jacobi", raise_on_noconv=True):
+        """Solve with host (numpy) buffers; copies happen inside the library call."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.N) if x is None else x
+        if b.shape != (self.N,) or x.shape != (self.N,) or x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("b and x must be contiguous float64 arrays of length N")
+        st = CgStats()
+        self._sync_stream()
+        rc = self._lib.fepa_cg_solve_host(self._h, b.ctypes.data_as(ctypes.c_void_p),
+                                          x.ctypes.data_as(ctypes.c_void_p), float(rtol), int(maxit),
+                                          _PRECONDS[precond], ctypes.byref(st))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        return x, st.as_dict()
+
+    def iterations(self, b, x, iters, precond="jacobi"):
+        torch = _torch()
+        st = CgStats()
+        self._sync_stream()
+        _check(self._lib.fepa_cg_iterations(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                            _dev_ptr(x, torch.float64, self.N, "x"), int(iters),
+                                            _PRECONDS[precond], ctypes.byref(st)))
+        return st.as_dict()
