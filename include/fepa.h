@@ -191,6 +191,31 @@ int fepa_cg_solve_host(fepa_op* op, const double* b_host, double* x_host, double
 int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, int32_t precond,
                        fepa_cg_stats* stats);
 
+/*
+ * CG solve that allocates nothing.  The paper has no counterpart: this call exists
+ * for callers that cannot allocate device memory once they are running -- for
+ * instance a host program whose framework has already reserved the whole GPU for its
+ * own caching pool (a cudaMalloc would fail), or a latency-bound loop that must not
+ * call cudaMalloc/cudaFree because they can synchronise the device and stall other
+ * streams.  fepa_cg_solve, by contrast, allocates its work vectors on first use.
+ *
+ * Same arguments, result and status codes as fepa_cg_solve; x is iterated in place.
+ * The work vectors live in one static device array of this library, sized for at
+ * most FEPA_NOALLOC_MAX_DOFS global DOFs (about 4.2 MB, held on every GPU that loads
+ * the library until the process exits).  Larger operators are rejected with
+ * FEPA_ERR_ARG before any device work.  The iteration loop is driven from the host
+ * in short chunks of stream launches (no CUDA graph is built).
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call shares the array and finds it holding the previous call's
+ *     contents; the call clears what must start at zero itself.  Calls that overlap
+ *     on the GPU (other streams, other threads, other ops) race on the array: run
+ *     them one after another.
+ */
+#define FEPA_NOALLOC_MAX_DOFS 131072
+int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
+                          fepa_cg_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -557,3 +558,109 @@ int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CG solve without allocation (fepa_cg_solve_noalloc).  Its work vectors live in
+// one file-scope device array instead of cudaMalloc'ed buffers, for callers that
+// cannot allocate device memory after start-up.  Layout, in doubles, each piece
+// starting on a 256-byte boundary:
+//   [0, 32)                     CgState (device scalars and the reduction ticket)
+//   [32, 32 + 3584)             block partial sums of the dot products
+//   then r, d, h, 1/diag        FEPA_NOALLOC_MAX_DOFS doubles each
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_STATE = 0;
+constexpr int64_t NA_PARTIALS = 32;
+constexpr int64_t NA_PARTIALS_CAP = 3584;  // >= 3 * (148 * 8) block partials
+constexpr int64_t NA_VEC0 = NA_PARTIALS + NA_PARTIALS_CAP;
+constexpr int64_t NA_TOTAL = NA_VEC0 + 4 * (int64_t)FEPA_NOALLOC_MAX_DOFS;
+static_assert(sizeof(CgState) <= 32 * sizeof(double), "state does not fit its slot");
+static_assert(NA_VEC0 % 32 == 0 && FEPA_NOALLOC_MAX_DOFS % 32 == 0, "pieces must stay 256-byte aligned");
+
+static __device__ __align__(256) double g_noalloc_scratch[NA_TOTAL];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[NA_MAX_DEVICES] = {nullptr};
+
+// Device address of the array on the current device, looked up once per device.
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= NA_MAX_DEVICES) return fail(FEPA_ERR_ARG, "device ordinal %d unsupported", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != device) return fail(FEPA_ERR_ARG, "the op's device %d is not the current device %d", device, cur);
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[device] = (double*)p;
+  }
+  *out = g_noalloc_ptr[device];
+  return FEPA_OK;
+}
+
+}  // namespace
+
+extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, double rtol, int32_t maxit,
+                                     int32_t precond, fepa_cg_stats* stats) {
+  if (!op || !b || !x) return fail(FEPA_ERR_ARG, "null argument");
+  if (maxit < 1) return fail(FEPA_ERR_ARG, "maxit must be >= 1");
+  if (!(rtol >= 0.0)) return fail(FEPA_ERR_ARG, "rtol must be >= 0");
+  if (precond != FEPA_PRECOND_NONE && precond != FEPA_PRECOND_JACOBI) return fail(FEPA_ERR_ARG, "bad precond");
+  if (op->N > FEPA_NOALLOC_MAX_DOFS)
+    return fail(FEPA_ERR_ARG, "fepa_cg_solve_noalloc handles at most %d DOFs; this operator has %lld",
+                FEPA_NOALLOC_MAX_DOFS, (long long)op->N);
+  double* base = nullptr;
+  TRY(noalloc_scratch(op->device, &base));
+  CgState* st = (CgState*)(base + NA_STATE);
+  double* partials = base + NA_PARTIALS;
+  double* r = base + NA_VEC0;
+  double* d = r + FEPA_NOALLOC_MAX_DOFS;
+  double* h = d + FEPA_NOALLOC_MAX_DOFS;
+  double* invd = h + FEPA_NOALLOC_MAX_DOFS;
+  const int64_t N = op->N;
+  const int rb = grid_for(N, RED_THREADS, 148 * 8);
+  cudaStream_t s = op->stream;
+
+  // the array holds whatever the previous call left: reset the scalars and ticket
+  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(CgState), s));
+  if (precond) {
+    TRY(compute_diagonal(op, invd, s));  // zeroes invd, then sums the element diagonals
+    reciprocal<<<grid_for(N, 256, 148 * 16), 256, 0, s>>>(N, invd, invd);
+    LAUNCH_CHECK();
+  }
+  const double* pinv = precond ? invd : nullptr;
+  CUDA_TRY(cudaMemsetAsync(h, 0, N * sizeof(double), s));
+  TRY(launch_apply(op, x, h, nullptr, s));
+  cg_init<<<rb, RED_THREADS, 0, s>>>(N, b, r, d, h, pinv, st, rtol * rtol, maxit, partials);
+  LAUNCH_CHECK();
+  // host-driven loop in chunks; every kernel returns at once after the device sets done
+  constexpr int CHUNK = 8;
+  CgState hs;
+  for (;;) {
+    for (int k = 0; k < CHUNK; ++k) {
+      TRY(launch_apply(op, d, h, &st->done, s));
+      cg_dot_dh<<<rb, RED_THREADS, 0, s>>>(N, d, h, st, partials);
+      LAUNCH_CHECK();
+      cg_update<<<rb, RED_THREADS, 0, s>>>(N, x, r, d, h, pinv, st, partials);
+      LAUNCH_CHECK();
+      cg_direction<<<rb, RED_THREADS, 0, s>>>(N, r, d, h, pinv, st, 0, 0);
+      LAUNCH_CHECK();
+    }
+    CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.done) break;
+  }
+  if (stats) {
+    stats->iterations = hs.iter;
+    stats->status = hs.converged ? FEPA_OK : FEPA_ERR_NOCONV;
+    stats->b_norm = sqrt(hs.bb);
+    stats->rel_residual = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
+    stats->precond_norm = sqrt(fabs(hs.rho));
+  }
+  if (!hs.converged && rtol > 0.0)
+    return fail(FEPA_ERR_NOCONV, "CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)", rtol, hs.iter,
+                hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0);
+  return FEPA_OK;
+}

@@ -60,7 +60,9 @@ SIGNATURES = [
     ("fepa_cg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_solve_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_iterations", ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
 ]
+NOALLOC_MAX_DOFS = 131072
 
 
 class FepaError(RuntimeError):
