@@ -2,8 +2,11 @@
 
 One step = one pass of the whole hot path over one synthetic problem:
 geometry setup D from the (device-resident) vertices, load vector of the sine
-manufactured solution, matrix-free diagonal, and the Jacobi-PCG solve to a relative
-residual of 1e-10 (every iteration applies the fused G^T B^T D B G kernel).
+manufactured solution, matrix-free diagonal, and the solve to a relative FP64
+residual of 1e-10 (every CG iteration applies the fused G^T B^T D B G kernel).
+Two forms of the solve are timed on the same problem: the mixed-precision one (FP64
+iterative refinement around an FP32 Jacobi-PCG; the headline `value`) and the plain
+FP64 Jacobi-PCG (`fp64_plain`).
 value = N * (CG iterations) / step time, summed over ranks (independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -47,13 +50,13 @@ def flops_per_elem(n, q, form):
     return 2 * (4 * n ** 3 * q + 6 * n * n * q * q + 6 * n * q ** 3) + 15 * q ** 3
 
 
-def bytes_per_elem(n, q, form, p, nelem_per_dim):
+def bytes_per_elem(n, q, form, p, nelem_per_dim, word=8):
     """Algorithmic HBM bytes of one action per element: D, the element->DOF map and
-    x/y once per global DOF."""
+    x/y once per global DOF (word = 8 for FP64, 4 for FP32 data)."""
     ncomp = 6 if form == "diffusion" else 1
     N = (p * nelem_per_dim + 1) ** 3
     E = nelem_per_dim ** 3
-    return 8 * ncomp * q ** 3 + 4 * n ** 3 + 16.0 * N / E
+    return word * ncomp * q ** 3 + 4 * n ** 3 + 2.0 * word * N / E
 
 
 class ClockSampler:
@@ -187,102 +190,133 @@ def run_ours(args, rank, world, dist):
     op = F.Operator(n, n, n, verts_np, p, form="diffusion")
     q, N, E = op.q, op.N, op.E
     op.set_essential(op.boundary_dofs())
+    op.set_cg_mode(args.cg_mode)
     verts = torch.from_numpy(verts_np).cuda()
     b = torch.empty(N, dtype=torch.float64, device="cuda")
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
     scale = 3 * math.pi ** 2
 
-    def step():
-        op.set_vertices(verts)          # D from the trilinear map
-        op.rhs_sine(scale, out=b)       # load vector
-        x.zero_()
-        _, st = op.solve(b, x, rtol=args.rtol, maxit=args.maxit)   # diagonal + Jacobi PCG
-        return st
-
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    l0 = F.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters = []
-    with ClockSampler(local) as clk:
-        ev0.record()
-        for _ in range(args.steps):
-            iters.append(step()["iterations"])
-        ev1.record()
-        torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    launches = F.launch_count() - l0
-    t = ev0.elapsed_time(ev1) / 1e3
-    dofit = N * sum(iters)
-    if dist is not None:
-        tt = torch.tensor([t, float(dofit)], dtype=torch.float64, device="cuda")
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    def reduce_max_sum(t, work):
+        if dist is None:
+            return t, float(work)
+        tt = torch.tensor([t, float(work)], dtype=torch.float64, device="cuda")
+        tm = tt[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_all, dofit_all = float(tmax[0]), float(tt[1])
-    else:
-        t_all, dofit_all = t, float(dofit)
-    value = dofit_all / t_all / 1e9
+        return float(tm[0]), float(tt[1])
 
-    # dominant kernel: the fused action, timed alone on the same stream with CUDA events
-    xr = torch.from_numpy(FI.uniform_vector(N, seed=1)).cuda()
-    yr = torch.empty_like(xr)
-    for _ in range(3):
-        op.apply(xr, out=yr)
-    reps = 20
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    k0.record()
-    for _ in range(reps):
-        op.apply(xr, out=yr)
-    k1.record()
-    torch.cuda.synchronize()
-    t_apply = k0.elapsed_time(k1) / 1e3 / reps
-    fl = flops_per_elem(p + 1, q, "diffusion") * E
-    achieved = fl / t_apply / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": args.traffic,
-            "kernel": f"pa_apply_f64<{p},{q},diffusion>", "apply_ms": t_apply * 1e3,
-            "apply_gdofs": N / t_apply / 1e9,
-            "peak_note": "FP64 pipe, nominal 1.25 TFLOP/s (B300); a DFMA microbenchmark measured 0.95 TFLOP/s",
-            "algorithmic_bytes_per_launch": bytes_per_elem(p + 1, q, "diffusion", p, n) * E}
+    def solve(prec):
+        if prec == "fp64":
+            _, st = op.solve(b, x, rtol=args.rtol, maxit=args.maxit)
+            return st["iterations"], st
+        _, st = op.solve_refined(b, x, rtol=args.rtol, inner_rtol=args.inner_rtol)
+        return st["inner_iterations"], st
 
-    # end to end through the public API with host buffers (pinned)
-    e2e = None
-    if not args.no_e2e:
+    def step(prec):
+        op.set_vertices(verts)          # D from the trilinear map (a1)
+        op.rhs_sine(scale, out=b)       # load vector (a11)
+        x.zero_()
+        return solve(prec)              # diagonal (a10) + PCG (a9; a2-a8 in every iteration)
+
+    def timed(prec):
+        for _ in range(args.warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        l0 = F.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its, stats = [], []
+        with ClockSampler(local) as clk:
+            ev0.record()
+            for _ in range(args.steps):
+                it, st = step(prec)
+                its.append(it)
+                stats.append(st)
+            ev1.record()
+            torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        launches = F.launch_count() - l0
+        t, work = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, N * sum(its))
+        return {"value": work / t / 1e9, "ms_per_step": 1e3 * t / args.steps, "iterations_per_step": its,
+                "gpu_launches": launches, "clocks": clk.summary(), "stats": stats[-1]}
+
+    def kernel_time(prec, reps=20):
+        if prec == "fp64":
+            xr = torch.from_numpy(FI.uniform_vector(N, seed=1)).cuda()
+            fn = lambda out: op.apply(xr, out=out)  # noqa: E731
+            yr = torch.empty_like(xr)
+        else:
+            xr = torch.from_numpy(FI.uniform_vector(N, seed=1).astype(np.float32)).cuda()
+            fn = lambda out: op.apply_f32(xr, out=out)  # noqa: E731
+            yr = torch.empty_like(xr)
+        for _ in range(3):
+            fn(yr)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        k0.record()
+        for _ in range(reps):
+            fn(yr)
+        k1.record()
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / 1e3 / reps
+
+    def e2e(prec):
         vh = torch.from_numpy(verts_np).pin_memory().numpy()
         bh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+        op.set_vertices(verts)
+        op.rhs_sine(scale, out=b)
         bh[:] = b.cpu().numpy()
         xh = torch.zeros(N, dtype=torch.float64).pin_memory().numpy()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        e_its = 0
+        its = 0
         for _ in range(args.steps):
             op.set_vertices(vh)
             xh[:] = 0.0
-            _, st = op.solve_host(bh, xh, rtol=args.rtol, maxit=args.maxit)
-            e_its += st["iterations"]
+            if prec == "fp64":
+                _, st = op.solve_host(bh, xh, rtol=args.rtol, maxit=args.maxit)
+                its += st["iterations"]
+            else:
+                _, st = op.solve_refined_host(bh, xh, rtol=args.rtol, inner_rtol=args.inner_rtol)
+                its += st["inner_iterations"]
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([te, float(N * e_its)], dtype=torch.float64, device="cuda")
-            tm = tt[:1].clone()
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-            te, e_dofit = float(tm[0]), float(tt[1])
+        te, work = reduce_max_sum(time.perf_counter() - t0, N * its)
+        return {"value": work / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(vh.nbytes + 2 * bh.nbytes),
+                "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": 1e3 * te / args.steps}
+
+    hbm_peak, hbm_src = peaks()
+    results = {}
+    for prec in ("mixed", "fp64"):
+        if args.precision not in (prec, "both"):
+            continue
+        r = timed(prec)
+        t_apply = kernel_time(prec)
+        if prec == "fp64":
+            fl = flops_per_elem(p + 1, q, "diffusion") * E
+            ach = fl / t_apply / 1e9
+            r["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                             "frac": ach / FP64_PEAK_GFLOPS, "traffic": args.traffic_fp64,
+                             "kernel": f"pa_apply<double,{p},{q},diffusion>", "apply_ms": 1e3 * t_apply,
+                             "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s (2 DFMA/clk/SM x 148 SMs)"}
         else:
-            e_dofit = float(N * e_its)
-        e2e = {"value": e_dofit / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(vh.nbytes + 2 * bh.nbytes),
-               "d2h_bytes_per_step": int(xh.nbytes)}
+            by = bytes_per_elem(p + 1, q, "diffusion", p, n, word=4) * E
+            ach = by / t_apply / 1e9
+            fl = flops_per_elem(p + 1, q, "diffusion") * E
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "traffic": args.traffic_fp32,
+                             "kernel": f"pa_apply<float,{p},{q},diffusion>", "apply_ms": 1e3 * t_apply,
+                             "peak_note": f"HBM copy bandwidth ({hbm_src})",
+                             "fp32_tflops": fl / t_apply / 1e12}
+        r["apply_gdofs"] = N / t_apply / 1e9
+        r["e2e"] = None if args.no_e2e else e2e(prec)
+        results[prec] = r
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -292,14 +326,32 @@ def run_ours(args, rank, world, dist):
                          f"N={(p * args.oracle_n + 1) ** 3}, {it} iterations, {tcpu:.1f} s"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(p, n, q), "precision": "fp64",
+        head = results.get("mixed") or results["fp64"]
+        mixed = "mixed" in results
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64 (FP32 operator and inner CG, FP64 refinement residual/dots/scalars/setup)"
+                         if mixed else "f64",
+                "data": "synthetic",
+                "config": {"workload": workload_name(p, n, q),
+                           "precision": "mixed+refine" if mixed else "fp64",
+                           "solver": (f"FP64 iterative refinement to rtol {args.rtol} around FP32 Jacobi-PCG "
+                                      f"(inner rtol {args.inner_rtol})") if mixed else
+                                     f"FP64 Jacobi-PCG to rtol {args.rtol}",
+                           "cg_loop": args.cg_mode,
                            "l2": "inputs larger than L2 (D alone is %.2f GB)" % (E * 6 * q ** 3 * 8 / 1e9),
                            "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
-                "iterations_per_step": iters, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk.summary()}
+                "iterations_per_step": head["iterations_per_step"], "roofline": head["roofline"],
+                "cpu_baseline": cpu, "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+                "clocks": head["clocks"]}
+        if mixed:
+            line["refine_stats"] = head["stats"]
+        if mixed and "fp64" in results:
+            f64 = results["fp64"]
+            line["fp64_plain"] = {k: f64[k] for k in ("value", "ms_per_step", "iterations_per_step", "roofline",
+                                                       "e2e", "apply_gdofs", "gpu_launches", "clocks")}
+            line["time_to_solution_speedup_vs_fp64"] = f64["ms_per_step"] / head["ms_per_step"]
         print(json.dumps(line), flush=True)
     return 0
 
@@ -315,7 +367,12 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--oracle-n", type=int, default=12)
-    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per apply launch from ncu")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "both"], default="both")
+    ap.add_argument("--cg-mode", choices=["graph", "stream"], default="graph",
+                    help="graph: CG loop in one CUDA graph (default); stream: plain launches (for profiling)")
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--traffic-fp64", type=float, default=None, help="DRAM bytes per FP64 apply launch (ncu)")
+    ap.add_argument("--traffic-fp32", type=float, default=None, help="DRAM bytes per FP32 apply launch (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -54,6 +54,7 @@ extern "C" {
 #define FEPA_ERR_CUDA (-3)        /* a CUDA runtime call failed */
 #define FEPA_ERR_MESH (-4)        /* non-positive Jacobian determinant at a quadrature point */
 #define FEPA_ERR_NOCONV (-5)      /* CG reached maxit before the tolerance */
+#define FEPA_ERR_TIMEOUT (-6)     /* a kernel's bounded wait for staged data expired (no fault) */
 #define FEPA_ERR_UNSUPPORTED (-7) /* order / quadrature outside the compiled range */
 
 /* bilinear forms */
@@ -63,6 +64,10 @@ extern "C" {
 /* preconditioners */
 #define FEPA_PRECOND_NONE 0
 #define FEPA_PRECOND_JACOBI 1
+
+/* how CG iterations are driven (fepa_op_set_cg_mode) */
+#define FEPA_CG_GRAPH 0   /* one CUDA graph with a device-side while-condition (default) */
+#define FEPA_CG_STREAM 1  /* host-driven chunks of stream launches, state checked per chunk */
 
 /* compiled range: 1 <= p <= FEPA_MAX_ORDER, q = p+1 .. p+2 (q1d > p) */
 #define FEPA_MAX_ORDER 8
@@ -76,6 +81,14 @@ typedef struct fepa_cg_stats {
   double precond_norm;    /* sqrt(z_k . r_k) at exit (preconditioned residual norm) */
   double b_norm;          /* ||b||_2 */
 } fepa_cg_stats;
+
+typedef struct fepa_refine_stats {
+  int32_t outer_iterations;  /* FP64 residual corrections applied */
+  int32_t inner_iterations;  /* FP32 CG iterations, summed over the corrections */
+  int32_t status;            /* FEPA_OK or FEPA_ERR_NOCONV */
+  double rel_residual;       /* ||b - A x||_2 / ||b||_2 with the FP64 operator, at exit */
+  double b_norm;             /* ||b||_2 */
+} fepa_refine_stats;
 
 /* Version string of the library build. */
 const char* fepa_version(void);
@@ -124,6 +137,11 @@ int32_t fepa_op_dcomps(const fepa_op* op);
 /* Change the stream subsequent work of this op is enqueued on. */
 int fepa_op_set_stream(fepa_op* op, void* stream);
 
+/* Select how CG iterations are driven: FEPA_CG_GRAPH (default; no host wait per
+ * iteration) or FEPA_CG_STREAM (plain stream launches, e.g. for per-kernel profiling).
+ * Both run the same kernels and give the same iterates. */
+int fepa_op_set_cg_mode(fepa_op* op, int32_t mode);
+
 /* Boundary DOFs of the node grid, ascending, written to dofs (host, capacity
  * entries); *count receives the total (which may exceed capacity: then nothing
  * is written and FEPA_ERR_ARG is returned). dofs may be null to query the count. */
@@ -149,6 +167,17 @@ int fepa_op_qp_coords(const fepa_op* op, double* out);
  *   x, y   device, N doubles each; must not overlap.
  */
 int fepa_op_apply(fepa_op* op, const double* x, double* y);
+
+/*
+ * The same action in FP32: D, the 1D tables, the contractions, x and y are single
+ * precision (the operator of the mixed-precision solve).  x, y: device, N floats each.
+ * The first call builds an FP32 copy of D (4 bytes per stored value, each component
+ * padded to a multiple of 4 values).  The kernel stages each block's D with one TMA
+ * bulk copy; if that copy's bounded wait expires the block skips its work and sets an
+ * error word that the next blocking call on this op (fepa_solve_refined) reports as
+ * FEPA_ERR_TIMEOUT.
+ */
+int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
 
 /* diag(A) (of the constrained operator: 1 on essential rows), computed without
  * assembling A by sum factorisation (Sec. 2.1).  diag: device, N doubles. */
@@ -190,6 +219,24 @@ int fepa_cg_solve_host(fepa_op* op, const double* b_host, double* x_host, double
  */
 int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, int32_t precond,
                        fepa_cg_stats* stats);
+
+/*
+ * Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG.
+ * Each outer step forms r = b - A x with the FP64 operator and FP64 reductions; when
+ * ||r||_2 > rtol ||b||_2 it solves A e = r with the FP32 operator (fepa_op_apply_f32)
+ * to relative residual inner_rtol (at most inner_maxit iterations; FP32 vectors, dot
+ * products accumulated to FP64 accuracy, FP64 scalars) and updates x += e in FP64.
+ *   b, x        device, N doubles (x: initial guess in, solution out)
+ *   rtol        outer stopping rule on the FP64 residual
+ *   max_outer   limit on corrections; FEPA_ERR_NOCONV (stats filled) if reached
+ * Blocks until done.  The essential set and preconditioner are those of fepa_cg_solve.
+ */
+int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int32_t max_outer, double inner_rtol,
+                       int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats);
+
+/* As fepa_solve_refined with HOST b and x (copies inside the call). */
+int fepa_solve_refined_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t max_outer,
+                            double inner_rtol, int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats);
 
 /*
  * CG solve that allocates nothing.  The paper has no counterpart: this call exists

@@ -203,3 +203,171 @@ __global__ void set_rows(int64_t count, const int* __restrict__ rows, double val
 }
 
 }  // namespace fepa
+
+namespace fepa {
+
+// ---------------------------------------------------------------------------
+// Mixed precision: inner CG on FP32 vectors with the FP32 operator, inside FP64
+// iterative refinement.  On this GPU the FP64 pipe is ~75x slower than FP32, so the
+// inner loop keeps it idle: vector updates are FP32, and the dot products are
+// accumulated per thread as an unevaluated sum of two floats (exact products by FMA,
+// exact sums by TwoSum), i.e. to about 48 significant bits on the FP32 pipe, then
+// combined across threads and blocks in FP64.  Scalars (alpha, beta, rho) stay FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void f2_add_prod(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);   // a*b - p exactly
+  const float s = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));  // hi + p - s exactly
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ double f2_value(float hi, float lo) { return (double)hi + (double)lo; }
+
+// x = 0; r = b; z = r * inv_diag; d = z; h = 0; rho = (z,r), rr = (r,r), bb = (b,b)
+__global__ void __launch_bounds__(RED_THREADS)
+cg32_init(int64_t N, const float* __restrict__ b, float* __restrict__ x, float* __restrict__ r,
+          float* __restrict__ d, float* __restrict__ h, const float* __restrict__ inv_diag, CgState* st,
+          double rtol2, int maxit, double* partials) {
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f, bb_h = 0.f, bb_l = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = b[i];
+    const float zi = inv_diag ? ri * inv_diag[i] : ri;
+    x[i] = 0.f;
+    r[i] = ri;
+    d[i] = zi;
+    h[i] = 0.f;
+    f2_add_prod(zr_h, zr_l, zi, ri);
+    f2_add_prod(rr_h, rr_l, ri, ri);
+    f2_add_prod(bb_h, bb_l, ri, ri);
+  }
+  double v[3] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l), f2_value(bb_h, bb_l)};
+  double blk[3];
+  block_sum<3>(v, blk);
+  if (publish_partials<3>(blk, partials, &st->ticket)) {
+    double tot[3];
+    final_sums<3>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->rho = tot[0];
+      st->rr = tot[1];
+      st->bb = tot[2];
+      st->tol2 = rtol2 * tot[2];
+      st->iter = 0;
+      st->maxit = maxit;
+      st->converged = (tot[1] <= st->tol2) ? 1 : 0;
+      st->done = st->converged;
+      st->alpha = st->beta = 0.0;
+      st->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+cg32_dot_dh(int64_t N, const float* __restrict__ d, const float* __restrict__ h, CgState* st, double* partials) {
+  if (st->done) return;
+  float s_h = 0.f, s_l = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    f2_add_prod(s_h, s_l, d[i], h[i]);
+  double v[1] = {f2_value(s_h, s_l)};
+  double blk[1];
+  block_sum<1>(v, blk);
+  if (publish_partials<1>(blk, partials, &st->ticket)) {
+    double tot[1];
+    final_sums<1>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->alpha = st->rho / tot[0];
+      st->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+cg32_update(int64_t N, float* __restrict__ x, float* __restrict__ r, const float* __restrict__ d,
+            const float* __restrict__ h, const float* __restrict__ inv_diag, CgState* st, double* partials) {
+  if (st->done) return;
+  const float alpha = (float)st->alpha;
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fmaf(alpha, d[i], x[i]);
+    const float ri = fmaf(-alpha, h[i], r[i]);
+    r[i] = ri;
+    const float zi = inv_diag ? ri * inv_diag[i] : ri;
+    f2_add_prod(zr_h, zr_l, zi, ri);
+    f2_add_prod(rr_h, rr_l, ri, ri);
+  }
+  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      st->rr = tot[1];
+      if (tot[1] <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (st->iter >= st->maxit) {
+        st->done = 1;
+      }
+      st->beta = tot[0] / st->rho;
+      st->rho = tot[0];
+      st->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, float* __restrict__ h,
+               const float* __restrict__ inv_diag, const CgState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  const int done = st->done;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (done) return;
+  const float beta = (float)st->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+    d[i] = fmaf(beta, d[i], zi);
+    h[i] = 0.f;
+  }
+}
+
+// Outer step of the refinement: r = b - h in FP64 (h = A x from the FP64 operator),
+// handed to the inner solve as r32; ||r||^2 and ||b||^2 in FP64 into st->rr, st->bb.
+__global__ void __launch_bounds__(RED_THREADS)
+refine_residual(int64_t N, const double* __restrict__ b, const double* __restrict__ h, float* __restrict__ r32,
+                CgState* st, double* partials) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - h[i];
+    r32[i] = (float)ri;
+    v[0] += ri * ri;
+    v[1] += bi * bi;
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->rr = tot[0];
+      st->bb = tot[1];
+      st->ticket = 0;
+    }
+  }
+}
+
+// x += e (FP64 accumulation of the FP32 correction)
+__global__ void refine_correct(int64_t N, double* __restrict__ x, const float* __restrict__ e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)e[i];
+}
+
+__global__ void to_f32(int64_t N, const double* __restrict__ a, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)a[i];
+}
+
+}  // namespace fepa

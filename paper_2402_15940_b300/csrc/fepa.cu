@@ -1,15 +1,18 @@
 // C-ABI of the partial-assembly library (declarations and conventions: include/fepa.h).
 //
 // Host side: validates arguments, builds the 1D tables, owns device arrays, dispatches
-// the compiled (p, q, form) kernel instances, and drives CG through a CUDA graph whose
-// while-node repeats one CG iteration until a device-side flag says stop.
+// the compiled (p, q, form) kernel instances, and drives CG either through a CUDA graph
+// whose while-node repeats one iteration until a device-side flag says stop, or (stream
+// mode) through short host-driven chunks of the same kernels.
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
-#include <mutex>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -17,6 +20,7 @@
 #include "basis1d.hpp"
 #include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
+#include "pa_tma_f32.cuh"
 
 using namespace fepa;
 
@@ -42,12 +46,27 @@ int fail(int code, const char* fmt, ...) {
                                        __FILE__, __LINE__);                                          \
   } while (0)
 
+// counts the launch, then checks it
 #define LAUNCH_CHECK()                                                                               \
   do {                                                                                               \
     g_launches.fetch_add(1);                                                                         \
     cudaError_t e_ = cudaGetLastError();                                                             \
     if (e_ != cudaSuccess) return fail(FEPA_ERR_CUDA, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
                                        __FILE__, __LINE__);                                          \
+  } while (0)
+
+// checks a launch without counting it (loop bodies, counted by iterations run)
+#define BODY_CHECK()                                                                                 \
+  do {                                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                                             \
+    if (e_ != cudaSuccess) return fail(FEPA_ERR_CUDA, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                          \
+  } while (0)
+
+#define TRY(call)                   \
+  do {                              \
+    int rc_ = (call);               \
+    if (rc_ != FEPA_OK) return rc_; \
   } while (0)
 
 inline int grid_for(int64_t work, int threads, int cap) {
@@ -60,24 +79,34 @@ inline int grid_for(int64_t work, int threads, int cap) {
 // ---------------------------------------------------------------------------
 // compiled kernel instances, indexed by p (1..8), q - p - 1 (0, 1), form (0, 1)
 // ---------------------------------------------------------------------------
+template <typename R>
+using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*);
+using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
+
 struct KernelSet {
-  void (*apply)(int, const int*, const double*, const double*, const double*, const double*, double*, const int*);
+  ApplyFn<double> apply;
+  Apply32Fn apply32;
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   void (*rhs)(int, int, const double*, const int*, const double*, const double*, const double*, const double*,
               double, double*);
   int apply_smem, apply_tpe, apply_ne;
+  int apply32_smem, apply32_ne, d32_stride;
   int diag_smem, rhs_smem;
 };
 
 template <int P, int Q, bool DIFF>
 KernelSet make_set() {
   KernelSet k;
-  k.apply = pa_apply_f64<P, Q, DIFF>;
+  k.apply = pa_apply<double, P, Q, DIFF>;
+  k.apply32 = pa_apply_f32_tma<P, Q, DIFF>;
   k.diag = pa_diag_f64<P, Q, DIFF>;
   k.rhs = pa_rhs_f64<P, Q>;
-  k.apply_smem = PaShape<P, Q, DIFF>::SMEM;
-  k.apply_tpe = PaShape<P, Q, DIFF>::TPE;
-  k.apply_ne = PaShape<P, Q, DIFF>::NE;
+  k.apply_smem = PaShape<double, P, Q, DIFF>::SMEM;
+  k.apply_tpe = PaShape<double, P, Q, DIFF>::TPE;
+  k.apply_ne = PaShape<double, P, Q, DIFF>::NE;
+  k.apply32_smem = TmaShape<P, Q, DIFF>::SMEM;
+  k.apply32_ne = TmaShape<P, Q, DIFF>::NE;
+  k.d32_stride = TmaShape<P, Q, DIFF>::DSTRIDE;
   k.diag_smem = DiagShape<P, Q, DIFF>::SMEM;
   k.rhs_smem = RhsShape<P, Q>::SMEM;
   return k;
@@ -115,15 +144,30 @@ int allow_smem(const void* fn, int bytes) {
   return FEPA_OK;
 }
 
+// One CG loop (FP64 or FP32 inner): work vectors, device scalars, and its cached graph.
+struct CgLoop {
+  void* x = nullptr;  // iterate (FP32 loops own it; the FP64 loop iterates in a copy)
+  void *r = nullptr, *d = nullptr, *h = nullptr;
+  void* invd = nullptr;  // 1/diag in the loop's precision
+  CgState* st = nullptr;
+  double* partials = nullptr;
+  int red_blocks = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_precond = -1;
+};
+
 }  // namespace
 
 struct fepa_op {
   int nx, ny, nz, p, q, n, form;
   int64_t E, N;
   int device;
+  int cg_mode = FEPA_CG_GRAPH;
   cudaStream_t stream;
   cudaStream_t cap_stream;  // private stream used only to capture graphs
   KernelSet ks;
+  std::vector<float> B32h, G32h;
   // device arrays owned by the op
   double* verts = nullptr;
   int* gmap = nullptr;
@@ -135,30 +179,44 @@ struct fepa_op {
   int* ess = nullptr;
   int64_t ess_count = 0;
   int* flag = nullptr;  // device int used for mesh checks
+  // FP32 operator data (built on first use): padded FP32 D; tables in constant memory
+  float* qd32 = nullptr;
+  bool qd32_valid = false;
+  int* err = nullptr;  // device word set by kernels whose bounded waits expired
   // CG workspace (allocated on first solve)
   double* inv_diag = nullptr;
   bool inv_diag_valid = false;
-  double *r = nullptr, *d = nullptr, *h = nullptr, *xw = nullptr, *bw = nullptr, *xio = nullptr;
-  CgState* st = nullptr;
-  double* partials = nullptr;
-  int red_blocks = 0;
+  double* xw = nullptr;
+  double *bw = nullptr, *xio = nullptr;  // host-buffer solves
+  CgLoop cg64, cg32;
+  // refinement: FP64 residual, its scalars
+  double* h64 = nullptr;
+  CgState* st_ref = nullptr;
+  double* partials_ref = nullptr;
+  bool inv32_valid = false;
   CgState* st_host = nullptr;  // pinned
   int* st_host_flag = nullptr;  // pinned
-  cudaGraphExec_t graph_exec = nullptr;
-  cudaGraph_t graph = nullptr;
-  int graph_precond = -1;
 };
 
 namespace {
 
+void free_loop(CgLoop& L) {
+  if (L.exec) cudaGraphExecDestroy(L.exec);
+  if (L.graph) cudaGraphDestroy(L.graph);
+  for (void* p : {L.x, L.r, L.d, L.h, L.invd, (void*)L.st, (void*)L.partials})
+    if (p) cudaFree(p);
+  L = CgLoop();
+}
+
 void free_op(fepa_op* op) {
   if (!op) return;
   cudaStreamSynchronize(op->stream);
-  if (op->graph_exec) cudaGraphExecDestroy(op->graph_exec);
-  if (op->graph) cudaGraphDestroy(op->graph);
+  free_loop(op->cg64);
+  free_loop(op->cg32);
   for (void* p : {(void*)op->verts, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
-                  (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->inv_diag, (void*)op->r, (void*)op->d,
-                  (void*)op->h, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->st, (void*)op->partials})
+                  (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->err,
+                  (void*)op->inv_diag, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->h64,
+                  (void*)op->st_ref, (void*)op->partials_ref})
     if (p) cudaFree(p);
   if (op->st_host) cudaFreeHost(op->st_host);
   if (op->st_host_flag) cudaFreeHost(op->st_host_flag);
@@ -177,12 +235,7 @@ int dalloc(T** p, size_t count) {
   return FEPA_OK;
 }
 
-#define TRY(call)              \
-  do {                         \
-    int rc_ = (call);          \
-    if (rc_ != FEPA_OK) return rc_; \
-  } while (0)
-
+// y += A x in FP64 (launch only; counted)
 int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
   const KernelSet& k = op->ks;
   const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
@@ -192,18 +245,52 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
   return FEPA_OK;
 }
 
-int ensure_workspace(fepa_op* op) {
-  if (op->r) return FEPA_OK;
-  TRY(dalloc(&op->r, op->N));
-  TRY(dalloc(&op->d, op->N));
-  TRY(dalloc(&op->h, op->N));
-  TRY(dalloc(&op->xw, op->N));
-  TRY(dalloc(&op->st, 1));
-  op->red_blocks = grid_for(op->N, RED_THREADS, 148 * 8);
-  TRY(dalloc(&op->partials, 3 * (size_t)op->red_blocks));
-  CUDA_TRY(cudaMemsetAsync(op->st, 0, sizeof(CgState), op->stream));
-  CUDA_TRY(cudaMallocHost((void**)&op->st_host, sizeof(CgState)));
+// y += A x in FP32 (launch only; not counted: used inside loop bodies and by callers that count)
+int launch_apply32_nocount(fepa_op* op, const float* x, float* y, const int* skip, cudaStream_t s) {
+  const KernelSet& k = op->ks;
+  const int grid = (int)((op->E + k.apply32_ne - 1) / k.apply32_ne);
+  k.apply32<<<grid, dim3(k.apply_tpe, k.apply32_ne), k.apply32_smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip,
+                                                                          op->err);
+  BODY_CHECK();
   return FEPA_OK;
+}
+
+int launch_apply_nocount(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
+  const KernelSet& k = op->ks;
+  const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
+  k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x, y,
+                                                                    skip);
+  BODY_CHECK();
+  return FEPA_OK;
+}
+
+int ensure_host_state(fepa_op* op) {
+  if (!op->st_host) CUDA_TRY(cudaMallocHost((void**)&op->st_host, sizeof(CgState)));
+  return FEPA_OK;
+}
+
+template <typename T>
+int ensure_loop(fepa_op* op, CgLoop& L, bool own_x) {
+  if (L.r) return FEPA_OK;
+  T *r, *d, *h, *iv;
+  TRY(dalloc(&r, op->N));
+  L.r = r;
+  TRY(dalloc(&d, op->N));
+  L.d = d;
+  TRY(dalloc(&h, op->N));
+  L.h = h;
+  TRY(dalloc(&iv, op->N));
+  L.invd = iv;
+  if (own_x) {
+    T* x;
+    TRY(dalloc(&x, op->N));
+    L.x = x;
+  }
+  TRY(dalloc(&L.st, 1));
+  L.red_blocks = grid_for(op->N, RED_THREADS, 148 * 8);
+  TRY(dalloc(&L.partials, 3 * (size_t)L.red_blocks));
+  CUDA_TRY(cudaMemsetAsync(L.st, 0, sizeof(CgState), op->stream));
+  return ensure_host_state(op);
 }
 
 int compute_diagonal(fepa_op* op, double* out, cudaStream_t s) {
@@ -213,6 +300,7 @@ int compute_diagonal(fepa_op* op, double* out, cudaStream_t s) {
   return FEPA_OK;
 }
 
+// 1/diag(A) in FP64, kept in op->inv_diag until the mesh or the essential set changes
 int ensure_inv_diag(fepa_op* op) {
   if (op->inv_diag_valid) return FEPA_OK;
   if (!op->inv_diag) TRY(dalloc(&op->inv_diag, op->N));
@@ -220,91 +308,263 @@ int ensure_inv_diag(fepa_op* op) {
   reciprocal<<<grid_for(op->N, 256, 148 * 16), 256, 0, op->stream>>>(op->N, op->inv_diag, op->inv_diag);
   LAUNCH_CHECK();
   op->inv_diag_valid = true;
+  op->inv32_valid = false;
   return FEPA_OK;
 }
 
-// One CG iteration as four kernels, captured into the body of a while-node.
-int build_graph(fepa_op* op, int precond) {
-  if (op->graph_exec && op->graph_precond == precond) return FEPA_OK;
-  if (op->graph_exec) {
-    cudaGraphExecDestroy(op->graph_exec);
-    op->graph_exec = nullptr;
+// FP32 copy of D (each component padded to a 16-byte multiple) and the FP32 1D tables
+// (constant memory, slot of this (p, q)) for the mixed-precision operator
+int ensure_f32(fepa_op* op) {
+  cudaStream_t s = op->stream;
+  const int ncomp = op->form == FEPA_DIFFUSION ? 6 : 1;
+  const int q3 = op->q * op->q * op->q;
+  const int64_t count = op->E * ncomp * (int64_t)op->ks.d32_stride;
+  if (!op->qd32) {
+    TRY(dalloc(&op->qd32, count));
+    const size_t slot = (size_t)((op->p - 1) * 2 + (op->q - op->p - 1)) * TAB_SLOT;
+    CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->B32h.data(), op->B32h.size() * sizeof(float), slot * sizeof(float),
+                                     cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->G32h.data(), op->G32h.size() * sizeof(float),
+                                     (slot + 100) * sizeof(float), cudaMemcpyHostToDevice, s));
+    TRY(allow_smem((const void*)op->ks.apply32, op->ks.apply32_smem));
   }
-  if (op->graph) {
-    cudaGraphDestroy(op->graph);
-    op->graph = nullptr;
+  if (!op->qd32_valid) {
+    pad_to_f32<<<grid_for(count, 256, 148 * 32), 256, 0, s>>>(op->E, ncomp, q3, op->ks.d32_stride, op->qd, op->qd32);
+    LAUNCH_CHECK();
+    op->qd32_valid = true;
   }
-  CUDA_TRY(cudaGraphCreate(&op->graph, 0));
+  return FEPA_OK;
+}
+
+// FEPA_ERR_TIMEOUT if a kernel of this op gave up a bounded wait (checked at sync points)
+int check_err(fepa_op* op) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, op->err, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  if (h) return fail(FEPA_ERR_TIMEOUT, "a kernel's bounded wait for its staged data expired");
+  return FEPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG loop bodies: one iteration = apply, (d,h), update, direction
+// ---------------------------------------------------------------------------
+int body64(fepa_op* op, CgLoop& L, const double* invd, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+  const int rb = L.red_blocks;
+  double *x = op->xw, *r = (double*)L.r, *d = (double*)L.d, *h = (double*)L.h;
+  TRY(launch_apply_nocount(op, d, h, &L.st->done, s));
+  cg_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
+  BODY_CHECK();
+  cg_update<<<rb, RED_THREADS, 0, s>>>(op->N, x, r, d, h, invd, L.st, L.partials);
+  BODY_CHECK();
+  cg_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, L.st, cond, use_cond);
+  BODY_CHECK();
+  return FEPA_OK;
+}
+
+int body32(fepa_op* op, CgLoop& L, const float* invd, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
+  const int rb = L.red_blocks;
+  float *x = (float*)L.x, *r = (float*)L.r, *d = (float*)L.d, *h = (float*)L.h;
+  TRY(launch_apply32_nocount(op, d, h, &L.st->done, s));
+  cg32_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
+  BODY_CHECK();
+  cg32_update<<<rb, RED_THREADS, 0, s>>>(op->N, x, r, d, h, invd, L.st, L.partials);
+  BODY_CHECK();
+  cg32_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, L.st, cond, use_cond);
+  BODY_CHECK();
+  return FEPA_OK;
+}
+
+constexpr int KERNELS_PER_ITER = 4;
+constexpr int STREAM_CHUNK = 8;
+
+// Capture one iteration into the body of a while-node (once per loop and precond).
+template <typename Body>
+int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
+  if (L.exec && L.graph_precond == precond) return FEPA_OK;
+  if (L.exec) { cudaGraphExecDestroy(L.exec); L.exec = nullptr; }
+  if (L.graph) { cudaGraphDestroy(L.graph); L.graph = nullptr; }
+  CUDA_TRY(cudaGraphCreate(&L.graph, 0));
   cudaGraphConditionalHandle cond;
-  CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, op->graph, 1, cudaGraphCondAssignDefault));
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, L.graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-  np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = cond;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
   cudaGraphNode_t node;
-  CUDA_TRY(cudaGraphAddNode(&node, op->graph, nullptr, nullptr, 0, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  CUDA_TRY(cudaStreamBeginCaptureToGraph(op->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  const double* invd = precond ? op->inv_diag : nullptr;
-  const int rb = op->red_blocks;
-  int rc = launch_apply(op, op->d, op->h, &op->st->done, op->cap_stream);
-  if (rc == FEPA_OK) {
-    cg_dot_dh<<<rb, RED_THREADS, 0, op->cap_stream>>>(op->N, op->d, op->h, op->st, op->partials);
-    cg_update<<<rb, RED_THREADS, 0, op->cap_stream>>>(op->N, op->xw, op->r, op->d, op->h, invd, op->st, op->partials);
-    cg_direction<<<rb, RED_THREADS, 0, op->cap_stream>>>(op->N, op->r, op->d, op->h, invd, op->st, cond, 1);
-  }
+  CUDA_TRY(cudaGraphAddNode(&node, L.graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(op->cap_stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const int rc = body(op->cap_stream, cond, 1);
   cudaGraph_t captured = nullptr;
-  cudaError_t ce = cudaStreamEndCapture(op->cap_stream, &captured);
-  g_launches.fetch_sub(1);  // the captured apply did not run
+  const cudaError_t ce = cudaStreamEndCapture(op->cap_stream, &captured);
   if (rc != FEPA_OK) return rc;
   if (ce != cudaSuccess) return fail(FEPA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-  CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaGraphInstantiate(&op->graph_exec, op->graph, 0));
-  op->graph_precond = precond;
+  CUDA_TRY(cudaGraphInstantiate(&L.exec, L.graph, 0));
+  L.graph_precond = precond;
   return FEPA_OK;
 }
 
-int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int precond, fepa_cg_stats* stats) {
+// Run iterations until the device sets done; leaves the final scalars in *out.
+template <typename Body>
+int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
+  cudaStream_t s = op->stream;
+  if (op->cg_mode == FEPA_CG_GRAPH) {
+    TRY(build_while_graph(op, L, precond, body));
+    CUDA_TRY(cudaGraphLaunch(L.exec, s));
+    CUDA_TRY(cudaMemcpyAsync(out, L.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    g_launches.fetch_add(KERNELS_PER_ITER * (int64_t)(out->iter > 0 ? out->iter : 1));
+    return FEPA_OK;
+  }
+  for (;;) {
+    for (int k = 0; k < STREAM_CHUNK; ++k) TRY(body(s, 0, 0));
+    g_launches.fetch_add(KERNELS_PER_ITER * (int64_t)STREAM_CHUNK);
+    CUDA_TRY(cudaMemcpyAsync(out, L.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (out->done) return FEPA_OK;
+  }
+}
+
+void fill_stats(const CgState& h, fepa_cg_stats* stats) {
+  if (!stats) return;
+  stats->iterations = h.iter;
+  stats->status = h.converged ? FEPA_OK : FEPA_ERR_NOCONV;
+  stats->b_norm = sqrt(h.bb);
+  stats->rel_residual = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
+  stats->precond_norm = sqrt(fabs(h.rho));
+}
+
+int check_solve_args(const fepa_op* op, const void* b, const void* x, double rtol, int maxit, int precond) {
   if (!op || !b || !x) return fail(FEPA_ERR_ARG, "null argument");
   if (maxit < 1) return fail(FEPA_ERR_ARG, "maxit must be >= 1");
   if (!(rtol >= 0.0)) return fail(FEPA_ERR_ARG, "rtol must be >= 0");
   if (precond != FEPA_PRECOND_NONE && precond != FEPA_PRECOND_JACOBI) return fail(FEPA_ERR_ARG, "bad precond");
-  TRY(ensure_workspace(op));
+  return FEPA_OK;
+}
+
+int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int precond, fepa_cg_stats* stats) {
+  TRY(check_solve_args(op, b, x, rtol, maxit, precond));
+  CgLoop& L = op->cg64;
+  TRY(ensure_loop<double>(op, L, false));
+  if (!op->xw) TRY(dalloc(&op->xw, op->N));
   if (precond) TRY(ensure_inv_diag(op));
-  TRY(build_graph(op, precond));
+  const double* invd = precond ? op->inv_diag : nullptr;
   cudaStream_t s = op->stream;
-  const int rb = op->red_blocks;
   CUDA_TRY(cudaMemcpyAsync(op->xw, x, op->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemsetAsync(op->h, 0, op->N * sizeof(double), s));
-  TRY(launch_apply(op, op->xw, op->h, nullptr, s));
-  cg_init<<<rb, RED_THREADS, 0, s>>>(op->N, b, op->r, op->d, op->h, precond ? op->inv_diag : nullptr, op->st,
-                                      rtol * rtol, maxit, op->partials);
+  CUDA_TRY(cudaMemsetAsync(L.h, 0, op->N * sizeof(double), s));
+  TRY(launch_apply(op, op->xw, (double*)L.h, nullptr, s));
+  cg_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, b, (double*)L.r, (double*)L.d, (double*)L.h, invd, L.st,
+                                                rtol * rtol, maxit, L.partials);
   LAUNCH_CHECK();
-  CUDA_TRY(cudaGraphLaunch(op->graph_exec, s));
+  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond, int use_cond) {
+    return body64(op, L, invd, bs, cond, use_cond);
+  };
+  TRY(run_loop(op, L, precond, body, op->st_host));
   CUDA_TRY(cudaMemcpyAsync(x, op->xw, op->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(op->st_host, op->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  const CgState& h = *op->st_host;
-  g_launches.fetch_add(4 * (int64_t)(h.iter > 0 ? h.iter : 1));
-  if (stats) {
-    stats->iterations = h.iter;
-    stats->status = h.converged ? FEPA_OK : FEPA_ERR_NOCONV;
-    stats->b_norm = sqrt(h.bb);
-    stats->rel_residual = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
-    stats->precond_norm = sqrt(fabs(h.rho));
-  }
+  const CgState h = *op->st_host;
+  fill_stats(h, stats);
   if (!h.converged && rtol > 0.0)
     return fail(FEPA_ERR_NOCONV, "CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)", rtol, h.iter,
                 h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0);
   return FEPA_OK;
 }
 
+// Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG.
+int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_outer, double inner_rtol,
+                int inner_maxit, int precond, fepa_refine_stats* stats) {
+  TRY(check_solve_args(op, b, x, rtol, max_outer, precond));
+  if (!(inner_rtol > 0.0 && inner_rtol < 1.0)) return fail(FEPA_ERR_ARG, "inner_rtol must be in (0, 1)");
+  if (inner_maxit < 1) return fail(FEPA_ERR_ARG, "inner_maxit must be >= 1");
+  CgLoop& L = op->cg32;
+  TRY(ensure_loop<float>(op, L, true));
+  TRY(ensure_f32(op));
+  if (!op->h64) {
+    TRY(dalloc(&op->h64, op->N));
+    TRY(dalloc(&op->st_ref, 1));
+    TRY(dalloc(&op->partials_ref, 2 * (size_t)L.red_blocks));
+    CUDA_TRY(cudaMemsetAsync(op->st_ref, 0, sizeof(CgState), op->stream));
+  }
+  cudaStream_t s = op->stream;
+  if (precond) {
+    TRY(ensure_inv_diag(op));
+    if (!op->inv32_valid) {
+      to_f32<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, op->inv_diag, (float*)L.invd);
+      LAUNCH_CHECK();
+      op->inv32_valid = true;
+    }
+  }
+  const float* invd = precond ? (const float*)L.invd : nullptr;
+  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond, int use_cond) {
+    return body32(op, L, invd, bs, cond, use_cond);
+  };
+  int outer = 0, inner_total = 0;
+  double rel = 0.0, bnorm = 0.0;
+  CgState href;
+  for (;;) {
+    // FP64 residual r = b - A x
+    CUDA_TRY(cudaMemsetAsync(op->h64, 0, op->N * sizeof(double), s));
+    TRY(launch_apply(op, x, op->h64, nullptr, s));
+    refine_residual<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, b, op->h64, (float*)L.r, op->st_ref,
+                                                          op->partials_ref);
+    LAUNCH_CHECK();
+    CUDA_TRY(cudaMemcpyAsync(op->st_host, op->st_ref, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    href = *op->st_host;
+    bnorm = sqrt(href.bb);
+    rel = href.bb > 0 ? sqrt(href.rr / href.bb) : 0.0;
+    if (rel <= rtol || outer >= max_outer) break;
+    // FP32 correction: A e = r with relative tolerance inner_rtol
+    cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
+                                                    (float*)L.h, invd, L.st, inner_rtol * inner_rtol, inner_maxit,
+                                                    L.partials);
+    LAUNCH_CHECK();
+    CgState hin;
+    TRY(run_loop(op, L, precond, body, &hin));
+    inner_total += hin.iter;
+    refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
+    LAUNCH_CHECK();
+    ++outer;
+  }
+  TRY(check_err(op));
+  if (stats) {
+    stats->outer_iterations = outer;
+    stats->inner_iterations = inner_total;
+    stats->rel_residual = rel;
+    stats->b_norm = bnorm;
+    stats->status = rel <= rtol ? FEPA_OK : FEPA_ERR_NOCONV;
+  }
+  if (rel > rtol)
+    return fail(FEPA_ERR_NOCONV, "refinement did not reach rtol %.3g in %d outer steps (rel. residual %.3e)", rtol,
+                outer, rel);
+  return FEPA_OK;
+}
+
+// host b/x: staged through op-owned device buffers
+int host_solve(fepa_op* op, const double* b_host, double* x_host,
+                      const std::function<int(const double*, double*)>& solve) {
+  if (!op || !b_host || !x_host) return fail(FEPA_ERR_ARG, "null argument");
+  if (!op->bw) TRY(dalloc(&op->bw, op->N));
+  if (!op->xio) TRY(dalloc(&op->xio, op->N));
+  cudaStream_t s = op->stream;
+  CUDA_TRY(cudaMemcpyAsync(op->bw, b_host, op->N * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(op->xio, x_host, op->N * sizeof(double), cudaMemcpyHostToDevice, s));
+  int rc = solve(op->bw, op->xio);
+  if (rc == FEPA_OK || rc == FEPA_ERR_NOCONV) {
+    const std::string keep = g_err;
+    cudaError_t e = cudaMemcpyAsync(x_host, op->xio, op->N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(FEPA_ERR_CUDA, "host copy back: %s", cudaGetErrorString(e));
+    g_err = keep;
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
 
-const char* fepa_version(void) { return "fepa 0.1 (sm_103a, FP64 partial assembly)"; }
+const char* fepa_version(void) { return "fepa 0.2 (sm_103a, FP64 and FP32 partial assembly)"; }
 
 const char* fepa_last_error(void) { return g_err.c_str(); }
 
@@ -346,6 +606,8 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   basis::gauss_rule(q, gx, gw);
   std::vector<double> Bh, Gh;
   basis::lagrange_tables(nodes, gx, Bh, Gh);
+  op->B32h.assign(Bh.begin(), Bh.end());
+  op->G32h.assign(Gh.begin(), Gh.end());
   std::vector<double> ph(q), wh(q);
   for (int i = 0; i < q; ++i) { ph[i] = (double)gx[i]; wh[i] = (double)gw[i]; }
 
@@ -355,7 +617,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   if ((rc = dalloc(&op->verts, 3 * nv)) || (rc = dalloc(&op->gmap, E * n * n * n)) ||
       (rc = dalloc(&op->qd, E * ncomp * q3)) || (rc = dalloc(&op->B, (size_t)q * n)) ||
       (rc = dalloc(&op->G, (size_t)q * n)) || (rc = dalloc(&op->pts, q)) || (rc = dalloc(&op->wts, q)) ||
-      (rc = dalloc(&op->flag, 1)))
+      (rc = dalloc(&op->flag, 1)) || (rc = dalloc(&op->err, 1)))
     return bail(rc);
   cudaStream_t s = op->stream;
 #define CREATE_TRY(call)                                                                        \
@@ -370,22 +632,20 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   CREATE_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
   CREATE_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
+  CREATE_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
   build_gmap<<<grid_for(E * n * n * n, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, p, op->gmap);
   g_launches.fetch_add(1);
   geom_qdata<<<grid_for(E * q3, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, q, op->verts, op->pts, op->wts,
                                                               form == FEPA_DIFFUSION, op->qd, op->flag);
   g_launches.fetch_add(1);
   CREATE_TRY(cudaGetLastError());
-  int bad = 0;
-  CREATE_TRY(cudaMemcpyAsync(&bad, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CREATE_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CREATE_TRY(cudaStreamSynchronize(s));
-  if (bad) return bail(fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point"));
+  if (*op->st_host_flag) return bail(fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point"));
 #undef CREATE_TRY
   *out = op;
   return FEPA_OK;
 }
-
-void fepa_op_destroy(fepa_op* op) { free_op(op); }
 
 int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device) {
   if (!op || !vertices) return fail(FEPA_ERR_ARG, "null argument");
@@ -399,11 +659,15 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
                                                                   op->wts, op->form == FEPA_DIFFUSION, op->qd, op->flag);
   LAUNCH_CHECK();
   op->inv_diag_valid = false;
+  op->inv32_valid = false;
+  op->qd32_valid = false;
   CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
   return FEPA_OK;
 }
+
+void fepa_op_destroy(fepa_op* op) { free_op(op); }
 
 int64_t fepa_op_ndofs(const fepa_op* op) { return op ? op->N : -1; }
 int64_t fepa_op_nelems(const fepa_op* op) { return op ? op->E : -1; }
@@ -413,6 +677,13 @@ int32_t fepa_op_dcomps(const fepa_op* op) { return op ? (op->form == FEPA_DIFFUS
 int fepa_op_set_stream(fepa_op* op, void* stream) {
   if (!op) return fail(FEPA_ERR_ARG, "op is null");
   op->stream = (cudaStream_t)stream;
+  return FEPA_OK;
+}
+
+int fepa_op_set_cg_mode(fepa_op* op, int32_t mode) {
+  if (!op) return fail(FEPA_ERR_ARG, "op is null");
+  if (mode != FEPA_CG_GRAPH && mode != FEPA_CG_STREAM) return fail(FEPA_ERR_ARG, "unknown CG mode %d", mode);
+  op->cg_mode = mode;
   return FEPA_OK;
 }
 
@@ -460,6 +731,7 @@ int fepa_op_set_essential(fepa_op* op, const int32_t* dofs, int64_t count) {
     op->ess_count = count;
   }
   op->inv_diag_valid = false;
+  op->inv32_valid = false;
   return FEPA_OK;
 }
 
@@ -492,6 +764,16 @@ int fepa_op_apply(fepa_op* op, const double* x, double* y) {
   if (x == y) return fail(FEPA_ERR_ARG, "x and y must not alias");
   CUDA_TRY(cudaMemsetAsync(y, 0, op->N * sizeof(double), op->stream));
   return launch_apply(op, x, y, nullptr, op->stream);
+}
+
+int fepa_op_apply_f32(fepa_op* op, const float* x, float* y) {
+  if (!op || !x || !y) return fail(FEPA_ERR_ARG, "null argument");
+  if (x == y) return fail(FEPA_ERR_ARG, "x and y must not alias");
+  TRY(ensure_f32(op));
+  CUDA_TRY(cudaMemsetAsync(y, 0, op->N * sizeof(float), op->stream));
+  TRY(launch_apply32_nocount(op, x, y, nullptr, op->stream));
+  g_launches.fetch_add(1);
+  return FEPA_OK;
 }
 
 int fepa_op_diagonal(fepa_op* op, double* diag) {
@@ -530,31 +812,26 @@ int fepa_cg_solve(fepa_op* op, const double* b, double* x, double rtol, int32_t 
 
 int fepa_cg_solve_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t maxit, int32_t precond,
                        fepa_cg_stats* stats) {
-  if (!op || !b_host || !x_host) return fail(FEPA_ERR_ARG, "null argument");
-  TRY(ensure_workspace(op));
-  if (!op->bw) TRY(dalloc(&op->bw, op->N));
-  if (!op->xio) TRY(dalloc(&op->xio, op->N));
-  double* xd = op->xio;
-  cudaStream_t s = op->stream;
-  cudaError_t e = cudaMemcpyAsync(op->bw, b_host, op->N * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(xd, x_host, op->N * sizeof(double), cudaMemcpyHostToDevice, s);
-  int rc = FEPA_OK;
-  if (e != cudaSuccess) rc = fail(FEPA_ERR_CUDA, "host copy: %s", cudaGetErrorString(e));
-  if (rc == FEPA_OK) rc = run_cg(op, op->bw, xd, rtol, maxit, precond, stats);
-  if (rc == FEPA_OK || rc == FEPA_ERR_NOCONV) {
-    std::string keep = g_err;
-    e = cudaMemcpyAsync(x_host, xd, op->N * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) rc = fail(FEPA_ERR_CUDA, "host copy back: %s", cudaGetErrorString(e));
-    else g_err = keep;
-  }
-  return rc;
+  return host_solve(op, b_host, x_host, [&](const double* b, double* x) {
+    return run_cg(op, b, x, rtol, maxit, precond, stats);
+  });
 }
 
 int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, int32_t precond, fepa_cg_stats* stats) {
   if (iters < 1) return fail(FEPA_ERR_ARG, "iters must be >= 1");
-  int rc = run_cg(op, b, x, 0.0, iters, precond, stats);
-  return rc;
+  return run_cg(op, b, x, 0.0, iters, precond, stats);
+}
+
+int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int32_t max_outer, double inner_rtol,
+                       int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats) {
+  return run_refined(op, b, x, rtol, max_outer, inner_rtol, inner_maxit, precond, stats);
+}
+
+int fepa_solve_refined_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t max_outer,
+                            double inner_rtol, int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats) {
+  return host_solve(op, b_host, x_host, [&](const double* b, double* x) {
+    return run_refined(op, b, x, rtol, max_outer, inner_rtol, inner_maxit, precond, stats);
+  });
 }
 
 }  // extern "C"

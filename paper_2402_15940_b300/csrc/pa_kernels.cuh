@@ -169,36 +169,37 @@ __global__ void unflag_gmap(int64_t total, const int* __restrict__ gmap, int* __
 // ---------------------------------------------------------------------------
 // fused operator action
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool DIFF>
+template <typename T, int P, int Q, bool DIFF>
 struct PaShape {
   static constexpr int N = P + 1;
   static constexpr int NC1 = DIFF ? 2 : 1;  // stage-1 arrays (B x, G x)
   static constexpr int NC2 = DIFF ? 3 : 1;  // stage-2 arrays
-  static constexpr int ELEM = N * N * N + NC1 * N * N * Q + NC2 * N * Q * Q;  // doubles per element
+  static constexpr int ELEM = N * N * N + NC1 * N * N * Q + NC2 * N * Q * Q;  // values per element
   static constexpr int TPE = Q * Q;                                             // threads per element
   static constexpr int NE = (256 / TPE) > 0 ? (256 / TPE) : 1;                  // elements per block
-  static constexpr int SMEM = (2 * Q * N + NE * ELEM) * 8;                     // bytes
+  static constexpr int SMEM = (2 * Q * N + NE * ELEM) * (int)sizeof(T);        // bytes
 };
 
 // Each element is handled by Q*Q threads (threadIdx.x) and each block holds NE elements
 // (threadIdx.y).  Stage 1 contracts the x index, stage 2 the y index, stage 3 the z index
 // per (i,j) column, fused with D and the transposed z contraction in registers; the
 // transposed y and x stages follow through shared memory, and the result is
-// scatter-added to y (G^T).
-template <int P, int Q, bool DIFF>
-__global__ void __launch_bounds__(PaShape<P, Q, DIFF>::TPE * PaShape<P, Q, DIFF>::NE)
-pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd, const double* __restrict__ Btab,
-             const double* __restrict__ Gtab, const double* __restrict__ x, double* __restrict__ y,
-             const int* __restrict__ skip) {
-  using S = PaShape<P, Q, DIFF>;
+// scatter-added to y (G^T).  R is the arithmetic type: double for the FP64 operator,
+// float for the FP32 operator of the mixed-precision solve (D, tables, x, y all in R).
+template <typename R, int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(PaShape<R, P, Q, DIFF>::TPE * PaShape<R, P, Q, DIFF>::NE)
+pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R* __restrict__ Btab,
+         const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip) {
+  using S = PaShape<R, P, Q, DIFF>;
   constexpr int n = S::N, T = S::TPE;
   if (skip && *skip) return;
-  extern __shared__ double smem[];
-  double* sB = smem;
-  double* sG = sB + Q * n;
-  double* sX = sG + Q * n + threadIdx.y * S::ELEM;
-  double* S1 = sX + n * n * n;
-  double* S2 = S1 + S::NC1 * n * n * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* smem = reinterpret_cast<R*>(smem_raw);
+  R* sB = smem;
+  R* sG = sB + Q * n;
+  R* sX = sG + Q * n + threadIdx.y * S::ELEM;
+  R* S1 = sX + n * n * n;
+  R* S2 = S1 + S::NC1 * n * n * Q;
   const int tid = threadIdx.x;
   const int64_t e = (int64_t)blockIdx.x * S::NE + threadIdx.y;
   const bool live = e < E;
@@ -211,7 +212,7 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
   if (live)
     for (int l = tid; l < n * n * n; l += T) {
       const int gi = g[l];
-      sX[l] = gi >= 0 ? x[gi] : 0.0;
+      sX[l] = gi >= 0 ? x[gi] : R(0);
     }
   __syncthreads();
 
@@ -219,11 +220,11 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
   if (live)
     for (int w = tid; w < n * n * Q; w += T) {
       const int i = w % Q, cb = w / Q;
-      const double* xr = sX + cb * n;
-      double s0 = 0.0, s1 = 0.0;
+      const R* xr = sX + cb * n;
+      R s0 = R(0), s1 = R(0);
 #pragma unroll
       for (int a = 0; a < n; ++a) {
-        const double v = xr[a];
+        const R v = xr[a];
         s0 += sB[i * n + a] * v;
         if (DIFF) s1 += sG[i * n + a] * v;
       }
@@ -237,11 +238,11 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
   if (live)
     for (int w = tid; w < n * Q * Q; w += T) {
       const int i = w % Q, j = (w / Q) % Q, c = w / (Q * Q);
-      const double* sb = S1 + c * n * Q + i;
-      double sBB = 0.0, sBG = 0.0, sGB = 0.0;
+      const R* sb = S1 + c * n * Q + i;
+      R sBB = R(0), sBG = R(0), sGB = R(0);
 #pragma unroll
       for (int b = 0; b < n; ++b) {
-        const double vb = sb[b * Q];
+        const R vb = sb[b * Q];
         sBB += sB[j * n + b] * vb;
         if (DIFF) {
           sBG += sG[j * n + b] * vb;
@@ -260,8 +261,8 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
 
   // stage 3 + D + stage 3^T, one (i,j) column per thread, in registers
   if (live) {
-    double c0[n], c1[n], c2[n];   // forward columns over c
-    double a0[n], a1[n], a2[n];   // transposed accumulators over c
+    R c0[n], c1[n], c2[n];   // forward columns over c
+    R a0[n], a1[n], a2[n];   // transposed accumulators over c
 #pragma unroll
     for (int c = 0; c < n; ++c) {
       c0[c] = S2[c * Q * Q + tid];
@@ -269,27 +270,27 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
         c1[c] = S2[n * Q * Q + c * Q * Q + tid];
         c2[c] = S2[2 * n * Q * Q + c * Q * Q + tid];
       }
-      a0[c] = 0.0;
-      if (DIFF) { a1[c] = 0.0; a2[c] = 0.0; }
+      a0[c] = R(0);
+      if (DIFF) { a1[c] = R(0); a2[c] = R(0); }
     }
     constexpr int Q3 = Q * Q * Q;
-    const double* de = qd + e * (DIFF ? 6 : 1) * Q3 + tid;
+    const R* de = qd + e * (DIFF ? 6 : 1) * Q3 + tid;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       if (DIFF) {
-        double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+        R u0 = R(0), u1 = R(0), u2 = R(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) {
           u0 += sB[k * n + c] * c0[c];  // d/dx: G_x B_y B_z
           u1 += sB[k * n + c] * c1[c];  // d/dy: B_x G_y B_z
           u2 += sG[k * n + c] * c2[c];  // d/dz: B_x B_y G_z
         }
-        const double* dk = de + k * Q * Q;
-        const double d00 = dk[0], d01 = dk[Q3], d02 = dk[2 * Q3], d11 = dk[3 * Q3], d12 = dk[4 * Q3],
+        const R* dk = de + k * Q * Q;
+        const R d00 = dk[0], d01 = dk[Q3], d02 = dk[2 * Q3], d11 = dk[3 * Q3], d12 = dk[4 * Q3],
                      d22 = dk[5 * Q3];
-        const double v0 = d00 * u0 + d01 * u1 + d02 * u2;
-        const double v1 = d01 * u0 + d11 * u1 + d12 * u2;
-        const double v2 = d02 * u0 + d12 * u1 + d22 * u2;
+        const R v0 = d00 * u0 + d01 * u1 + d02 * u2;
+        const R v1 = d01 * u0 + d11 * u1 + d12 * u2;
+        const R v2 = d02 * u0 + d12 * u1 + d22 * u2;
 #pragma unroll
         for (int c = 0; c < n; ++c) {
           a0[c] += sB[k * n + c] * v0;
@@ -297,10 +298,10 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
           a2[c] += sG[k * n + c] * v2;
         }
       } else {
-        double u = 0.0;
+        R u = R(0);
 #pragma unroll
         for (int c = 0; c < n; ++c) u += sB[k * n + c] * c0[c];
-        const double v = de[k * Q * Q] * u;
+        const R v = de[k * Q * Q] * u;
 #pragma unroll
         for (int c = 0; c < n; ++c) a0[c] += sB[k * n + c] * v;
       }
@@ -322,8 +323,8 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
   if (live)
     for (int w = tid; w < n * n * Q; w += T) {
       const int i = w % Q, b = (w / Q) % n, c = w / (n * Q);
-      const double* sa = S2 + c * Q * Q + i;
-      double t0 = 0.0, t1 = 0.0;
+      const R* sa = S2 + c * Q * Q + i;
+      R t0 = R(0), t1 = R(0);
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
         t0 += sB[j * n + b] * sa[j * Q];
@@ -338,8 +339,8 @@ pa_apply_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd,
   if (live)
     for (int w = tid; w < n * n * n; w += T) {
       const int a = w % n, cb = w / n;
-      const double* st = S1 + cb * Q;
-      double s = 0.0;
+      const R* st = S1 + cb * Q;
+      R s = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         if (DIFF)

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfepa.so")
 
 OK = 0
-ERR_ARG, ERR_OOM, ERR_CUDA, ERR_MESH, ERR_NOCONV, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -7
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_MESH, ERR_NOCONV, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 MASS, DIFFUSION = 0, 1
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
 MAX_ORDER = 8
@@ -36,6 +36,16 @@ class CgStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RefineStats(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int32), ("inner_iterations", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("b_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+CG_GRAPH, CG_STREAM = 0, 1
+
 SIGNATURES = [
     ("fepa_version", ctypes.c_char_p, []),
     ("fepa_last_error", ctypes.c_char_p, []),
@@ -48,18 +58,23 @@ SIGNATURES = [
     ("fepa_op_q1d", _I32, [_P]),
     ("fepa_op_dcomps", _I32, [_P]),
     ("fepa_op_set_stream", ctypes.c_int, [_P, _P]),
+    ("fepa_op_set_cg_mode", ctypes.c_int, [_P, _I32]),
     ("fepa_op_boundary_dofs", ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
     ("fepa_op_set_essential", ctypes.c_int, [_P, _P, _I64]),
     ("fepa_op_elem_dofs", ctypes.c_int, [_P, _P]),
     ("fepa_op_qdata", ctypes.c_int, [_P, _P]),
     ("fepa_op_qp_coords", ctypes.c_int, [_P, _P]),
     ("fepa_op_apply", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_op_apply_f32", ctypes.c_int, [_P, _P, _P]),
     ("fepa_op_diagonal", ctypes.c_int, [_P, _P]),
     ("fepa_op_rhs", ctypes.c_int, [_P, _P, _P]),
     ("fepa_op_rhs_sine", ctypes.c_int, [_P, _D, _P]),
     ("fepa_cg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_solve_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_iterations", ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_solve_refined", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
+    ("fepa_solve_refined_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32,
+                                               ctypes.POINTER(RefineStats)]),
     ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
 ]
 NOALLOC_MAX_DOFS = 131072
@@ -221,6 +236,19 @@ class Operator:
         _check(self._lib.fepa_op_apply(self._h, px, py))
         return y
 
+    def apply_f32(self, x, out=None):
+        """FP32 action (the mixed-precision operator); x, out: float32 CUDA tensors."""
+        torch = _torch()
+        y = torch.empty(self.N, dtype=torch.float32, device="cuda") if out is None else out
+        px = _dev_ptr(x, torch.float32, self.N, "x")
+        py = _dev_ptr(y, torch.float32, self.N, "y")
+        self._sync_stream()
+        _check(self._lib.fepa_op_apply_f32(self._h, px, py))
+        return y
+
+    def set_cg_mode(self, mode):
+        _check(self._lib.fepa_op_set_cg_mode(self._h, {"graph": CG_GRAPH, "stream": CG_STREAM}.get(mode, mode)))
+
     def diagonal(self, out=None):
         torch = _torch()
         y = self._vec(out)
@@ -269,6 +297,34 @@ class Operator:
                                           _PRECONDS[precond], ctypes.byref(st))
         if rc != ERR_NOCONV or raise_on_noconv:
             _check(rc)
+        return x, st.as_dict()
+
+    def solve_refined(self, b, x=None, rtol=1e-10, max_outer=50, inner_rtol=1e-4, inner_maxit=20000,
+                      precond="jacobi", raise_on_noconv=True):
+        """FP64 iterative refinement around an FP32 Jacobi-PCG (mixed precision)."""
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = RefineStats()
+        self._sync_stream()
+        rc = self._lib.fepa_solve_refined(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                          _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(max_outer),
+                                          float(inner_rtol), int(inner_maxit), _PRECONDS[precond], ctypes.byref(st))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        return x, st.as_dict()
+
+    def solve_refined_host(self, b, x=None, rtol=1e-10, max_outer=50, inner_rtol=1e-4, inner_maxit=20000,
+                           precond="jacobi"):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.N) if x is None else x
+        if b.shape != (self.N,) or x.shape != (self.N,) or x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("b and x must be contiguous float64 arrays of length N")
+        st = RefineStats()
+        self._sync_stream()
+        _check(self._lib.fepa_solve_refined_host(self._h, b.ctypes.data_as(ctypes.c_void_p),
+                                                 x.ctypes.data_as(ctypes.c_void_p), float(rtol), int(max_outer),
+                                                 float(inner_rtol), int(inner_maxit), _PRECONDS[precond],
+                                                 ctypes.byref(st)))
         return x, st.as_dict()
 
     def iterations(self, b, x, iters, precond="jacobi"):

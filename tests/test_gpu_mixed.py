@@ -1,0 +1,161 @@
+"""GPU parity of the mixed-precision path: the FP32 operator and FP64 iterative
+refinement around an FP32 Jacobi-PCG, against the CPU FP64 oracle.
+
+FP32 action tolerance: every output is a sum through 3 forward contractions (n terms
+each), the 3x3 D product, 3 transposed contractions (q terms each) and at most 8
+element contributions, all rounded to binary32 (unit roundoff u = 2^-24 ~ 6e-8), plus
+the rounding of D and of the 1D tables.  The standard bound gives about
+(3n + 3q + 14) u ~ 3e-6 of |B^T| |D| |B| |x| per entry at p = 8; for the random x used
+here ||A x|| is within a small factor of that, so relative l2 error <= 1e-5 is the
+bound asserted (measured values are near 1e-7).
+
+Refined solve: the FP64 residual decides when to stop, so the solution is checked
+against the oracle's FP64 solution to 1e-10 relative error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import fem_inputs as FI
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+SHAPES = {1: (5, 4, 3), 2: (4, 3, 3), 3: (3, 3, 3), 4: (3, 3, 2), 5: (3, 2, 2), 6: (3, 2, 1), 7: (2, 2, 2),
+          8: (3, 1, 1)}
+
+
+def F():
+    import paper_2402_15940_b300 as mod
+    return mod
+
+
+def make(shape, p, form, seed=0):
+    verts = FI.perturbed_cube_vertices(*shape, seed=seed)
+    return F().Operator(*shape, verts, p, form=form), O.HexGridMesh(*shape, verts)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def oracle_action(mesh, p, form, x, ess=None):
+    if p <= 5:
+        A = O.assemble_csr(mesh, p, p + 2, form)
+        if ess is not None:
+            A = O.constrain(A, ess)
+        return A @ x
+    return O.action_elementwise(mesh, p, p + 2, form, x, ess=ess)
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", list(range(1, 9)))
+def test_apply_f32_matches_oracle(p, form):
+    op, mesh = make(SHAPES[p], p, form, seed=p)
+    x32 = FI.uniform_vector(op.N, seed=200 + p).astype(np.float32)
+    y = op.apply_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    ref = oracle_action(mesh, p, form, x32.astype(np.float64))
+    e = rel(y, ref)
+    assert e <= TOL32, e
+
+
+@pytest.mark.parametrize("p", [2, 5, 8])
+def test_apply_f32_constrained(p):
+    op, mesh = make(SHAPES[p], p, "diffusion", seed=3)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    x32 = FI.uniform_vector(op.N, seed=5).astype(np.float32)
+    y = op.apply_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert rel(y, oracle_action(mesh, p, "diffusion", x32.astype(np.float64), ess=ess.astype(np.int64))) <= TOL32
+
+
+def test_apply_f32_follows_new_vertices():
+    op, _ = make((3, 3, 3), 3, "diffusion", seed=1)
+    x32 = torch.from_numpy(FI.uniform_vector(op.N, seed=1).astype(np.float32)).cuda()
+    op.apply_f32(x32)
+    verts2 = FI.perturbed_cube_vertices(3, 3, 3, seed=2)
+    op.set_vertices(verts2)
+    y = op.apply_f32(x32).cpu().numpy()
+    mesh2 = O.HexGridMesh(3, 3, 3, verts2)
+    assert rel(y, oracle_action(mesh2, 3, "diffusion", x32.cpu().numpy().astype(np.float64))) <= TOL32
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 2, (4, 4, 4)), ("diffusion", 4, (3, 3, 3)),
+                                          ("diffusion", 6, (2, 2, 2)), ("mass", 3, (3, 4, 2)),
+                                          ("diffusion", 8, (2, 1, 2))])
+def test_refined_solution_matches_oracle(form, p, shape):
+    op, mesh = make(shape, p, form, seed=41)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    if form == "diffusion":
+        op.set_essential(prob.ess.astype(np.int32))
+        b = op.rhs_sine(3 * math.pi ** 2)
+        bo = prob.sine_rhs()
+    else:
+        bo = FI.uniform_vector(op.N, seed=42)
+        b = torch.from_numpy(bo).cuda()
+    x, st = op.solve_refined(b, rtol=1e-12, inner_rtol=1e-4)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-12 and st["outer_iterations"] >= 1
+    xo, _, _ = prob.solve(bo, rtol=1e-14)
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
+
+
+def test_refined_counts_and_host_buffers():
+    op, mesh = make((4, 4, 4), 3, "diffusion", seed=43)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    xd, sd = op.solve_refined(b, rtol=1e-10)
+    xh, sh = op.solve_refined_host(b.cpu().numpy(), rtol=1e-10)
+    assert sd["outer_iterations"] == sh["outer_iterations"]
+    assert abs(sd["inner_iterations"] - sh["inner_iterations"]) <= 2
+    assert rel(xh, xd.cpu().numpy()) <= 1e-9
+    # the plain FP64 solve reaches the same solution
+    x64, _ = op.solve(b, rtol=1e-10)
+    assert rel(xd.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
+
+
+def test_refined_noconv():
+    op, _ = make((4, 4, 4), 2, "diffusion", seed=44)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    x, st = op.solve_refined(b, rtol=1e-14, max_outer=1, raise_on_noconv=False)
+    assert st["status"] == -5 and st["outer_iterations"] == 1
+
+
+@pytest.mark.parametrize("solver", ["cg", "refined"])
+def test_stream_mode_equals_graph_mode(solver):
+    op, _ = make((5, 4, 4), 3, "diffusion", seed=45)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    run = (lambda: op.solve(b, rtol=1e-10)) if solver == "cg" else (lambda: op.solve_refined(b, rtol=1e-10))
+    xg, sg = run()
+    op.set_cg_mode("stream")
+    xs, ss = run()
+    op.set_cg_mode("graph")
+    key = "iterations" if solver == "cg" else "inner_iterations"
+    assert abs(sg[key] - ss[key]) <= 1
+    assert rel(xs.cpu().numpy(), xg.cpu().numpy()) <= 1e-9
+
+
+@pytest.mark.parametrize("p,n", [(4, 64), (6, 32)])
+def test_refined_full_size_sampled(p, n):
+    """The refined solve at the sizes of the mixed-precision configuration (diffusion,
+    p=4 on 64^3 and p=6 on 32^3 perturbed hexes, sine RHS): sampled rows of the FP64
+    residual checked one by one by the oracle, and agreement with the plain FP64 solve."""
+    op, mesh = make((n, n, n), p, "diffusion", seed=0)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    b = op.rhs_sine(3 * math.pi ** 2)
+    x, st = op.solve_refined(b, rtol=1e-10)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    xh, bh = x.cpu().numpy(), b.cpu().numpy()
+    rng = np.random.default_rng(7)
+    rows = rng.choice(op.N, 40, replace=False)
+    Ax = O.action_rows(mesh, p, p + 2, O.DIFFUSION, xh, rows, ess=ess.astype(np.int64))
+    assert np.max(np.abs(bh[rows] - Ax)) <= 1e-10 * np.linalg.norm(bh)
+    x64, s64 = op.solve(b, rtol=1e-12, maxit=20000)
+    assert rel(xh, x64.cpu().numpy()) <= 1e-9
