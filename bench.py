@@ -311,7 +311,8 @@ def run_ours(args, rank, world, dist):
             fl = flops_per_elem(p + 1, q, "diffusion") * E
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak, "traffic": args.traffic_fp32,
-                             "kernel": f"pa_apply<float,{p},{q},diffusion>", "apply_ms": 1e3 * t_apply,
+                             "kernel": f"pa_apply_f32_tma<{p},{q},diffusion> variant {op.f32_variant()[0]} "
+                                       f"({op.f32_variant()[1]}, autotuned)", "apply_ms": 1e3 * t_apply,
                              "peak_note": f"HBM copy bandwidth ({hbm_src})",
                              "fp32_tflops": fl / t_apply / 1e12}
         r["apply_gdofs"] = N / t_apply / 1e9

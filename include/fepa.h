@@ -179,6 +179,17 @@ int fepa_op_apply(fepa_op* op, const double* x, double* y);
  */
 int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
 
+/*
+ * Launch shape of the FP32 kernel.  Variants: 0 = D staged into shared memory by a TMA
+ * bulk copy, 1 = D read directly from HBM (smaller blocks, more warps per SM), 2 = as 1
+ * with half as many elements per block.  By default (variant -1) the first FP32 use
+ * times every variant on this op's mesh and keeps the fastest; the choice is cached per
+ * device and (p, q, form) for the process.  All variants compute the same result.
+ */
+int fepa_op_set_f32_variant(fepa_op* op, int32_t variant);
+int32_t fepa_op_f32_variant(const fepa_op* op);          /* -1 until chosen */
+const char* fepa_f32_variant_name(int32_t variant);
+
 /* diag(A) (of the constrained operator: 1 on essential rows), computed without
  * assembling A by sum factorisation (Sec. 2.1).  diag: device, N doubles. */
 int fepa_op_diagonal(fepa_op* op, double* diag);

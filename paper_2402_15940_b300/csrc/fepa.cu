@@ -83,14 +83,22 @@ template <typename R>
 using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*);
 using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
 
+constexpr int N32_VARIANTS = 3;  // (staged D, NE), (direct D, NE), (direct D, NE/2)
+
+struct Apply32Variant {
+  Apply32Fn fn;
+  int smem, ne;
+  const char* name;
+};
+
 struct KernelSet {
   ApplyFn<double> apply;
-  Apply32Fn apply32;
+  Apply32Variant v32[N32_VARIANTS];
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   void (*rhs)(int, int, const double*, const int*, const double*, const double*, const double*, const double*,
               double, double*);
   int apply_smem, apply_tpe, apply_ne;
-  int apply32_smem, apply32_ne, d32_stride;
+  int d32_stride;
   int diag_smem, rhs_smem;
 };
 
@@ -98,14 +106,18 @@ template <int P, int Q, bool DIFF>
 KernelSet make_set() {
   KernelSet k;
   k.apply = pa_apply<double, P, Q, DIFF>;
-  k.apply32 = pa_apply_f32_tma<P, Q, DIFF>;
+  k.v32[0] = {pa_apply_f32_tma<P, Q, DIFF, true, 1>, TmaShape<P, Q, DIFF, true, 1>::SMEM,
+              TmaShape<P, Q, DIFF, true, 1>::NE, "tma-staged D"};
+  k.v32[1] = {pa_apply_f32_tma<P, Q, DIFF, false, 1>, TmaShape<P, Q, DIFF, false, 1>::SMEM,
+              TmaShape<P, Q, DIFF, false, 1>::NE, "direct D"};
+  k.v32[2] = {pa_apply_f32_tma<P, Q, DIFF, false, 2>, TmaShape<P, Q, DIFF, false, 2>::SMEM,
+              TmaShape<P, Q, DIFF, false, 2>::NE, "direct D, half block"};
+
   k.diag = pa_diag_f64<P, Q, DIFF>;
   k.rhs = pa_rhs_f64<P, Q>;
   k.apply_smem = PaShape<double, P, Q, DIFF>::SMEM;
   k.apply_tpe = PaShape<double, P, Q, DIFF>::TPE;
   k.apply_ne = PaShape<double, P, Q, DIFF>::NE;
-  k.apply32_smem = TmaShape<P, Q, DIFF>::SMEM;
-  k.apply32_ne = TmaShape<P, Q, DIFF>::NE;
   k.d32_stride = TmaShape<P, Q, DIFF>::DSTRIDE;
   k.diag_smem = DiagShape<P, Q, DIFF>::SMEM;
   k.rhs_smem = RhsShape<P, Q>::SMEM;
@@ -182,6 +194,8 @@ struct fepa_op {
   // FP32 operator data (built on first use): padded FP32 D; tables in constant memory
   float* qd32 = nullptr;
   bool qd32_valid = false;
+  int v32 = -1;        // FP32 kernel variant in use (-1: not chosen yet)
+  int v32_forced = -1; // variant set by the caller (-1: autotune)
   int* err = nullptr;  // device word set by kernels whose bounded waits expired
   // CG workspace (allocated on first solve)
   double* inv_diag = nullptr;
@@ -245,14 +259,17 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
   return FEPA_OK;
 }
 
-// y += A x in FP32 (launch only; not counted: used inside loop bodies and by callers that count)
-int launch_apply32_nocount(fepa_op* op, const float* x, float* y, const int* skip, cudaStream_t s) {
-  const KernelSet& k = op->ks;
-  const int grid = (int)((op->E + k.apply32_ne - 1) / k.apply32_ne);
-  k.apply32<<<grid, dim3(k.apply_tpe, k.apply32_ne), k.apply32_smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip,
-                                                                          op->err);
+// y += A x in FP32 with variant v (launch only; not counted)
+int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const int* skip, cudaStream_t s) {
+  const Apply32Variant& k = op->ks.v32[v];
+  const int grid = (int)((op->E + k.ne - 1) / k.ne);
+  k.fn<<<grid, dim3(op->ks.apply_tpe, k.ne), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip, op->err);
   BODY_CHECK();
   return FEPA_OK;
+}
+
+int launch_apply32_nocount(fepa_op* op, const float* x, float* y, const int* skip, cudaStream_t s) {
+  return launch_apply32_variant(op, op->v32, x, y, skip, s);
 }
 
 int launch_apply_nocount(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
@@ -312,6 +329,77 @@ int ensure_inv_diag(fepa_op* op) {
   return FEPA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the FP32 kernel's launch shape: the compiled variants (TMA-staged or
+// direct D, elements per block) are timed on the op's own mesh the first time a
+// (device, p, q, form) is used in this process; the fastest is cached and reused.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mutex;
+int g_tuned[64][FEPA_MAX_ORDER + 1][2][2];
+bool g_tuned_init = false;
+
+int time_variants32(fepa_op* op, int* best) {
+  cudaStream_t s = op->stream;
+  float *x = nullptr, *y = nullptr;
+  TRY(dalloc(&x, op->N));
+  int rc = dalloc(&y, op->N);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best_ms = 1e30f;
+  *best = 0;
+  if (rc == FEPA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(FEPA_ERR_CUDA, "event creation failed");
+  if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(float), s) != cudaSuccess)
+    rc = fail(FEPA_ERR_CUDA, "memset failed");
+  for (int v = 0; rc == FEPA_OK && v < N32_VARIANTS; ++v) {
+    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply32_variant(op, v, x, y, nullptr, s);
+    if (rc != FEPA_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = launch_apply32_variant(op, v, x, y, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (rc != FEPA_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = fail(FEPA_ERR_CUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    g_launches.fetch_add(7);
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = v;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x);
+  if (y) cudaFree(y);
+  return rc;
+}
+
+int choose_variant32(fepa_op* op) {
+  if (op->v32_forced >= 0) {
+    op->v32 = op->v32_forced;
+    return FEPA_OK;
+  }
+  const int dev = op->device < 64 ? op->device : 63;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (!g_tuned_init) {
+    for (auto& a : g_tuned)
+      for (auto& b : a)
+        for (auto& c : b)
+          for (int& d : c) d = -1;
+    g_tuned_init = true;
+  }
+  int& slot = g_tuned[dev][op->p][op->q - op->p - 1][op->form];
+  if (slot < 0) {
+    int best = 0;
+    TRY(time_variants32(op, &best));
+    slot = best;
+  }
+  op->v32 = slot;
+  return FEPA_OK;
+}
+
 // FP32 copy of D (each component padded to a 16-byte multiple) and the FP32 1D tables
 // (constant memory, slot of this (p, q)) for the mixed-precision operator
 int ensure_f32(fepa_op* op) {
@@ -326,13 +414,14 @@ int ensure_f32(fepa_op* op) {
                                      cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->G32h.data(), op->G32h.size() * sizeof(float),
                                      (slot + 100) * sizeof(float), cudaMemcpyHostToDevice, s));
-    TRY(allow_smem((const void*)op->ks.apply32, op->ks.apply32_smem));
+    for (int v = 0; v < N32_VARIANTS; ++v) TRY(allow_smem((const void*)op->ks.v32[v].fn, op->ks.v32[v].smem));
   }
   if (!op->qd32_valid) {
     pad_to_f32<<<grid_for(count, 256, 148 * 32), 256, 0, s>>>(op->E, ncomp, q3, op->ks.d32_stride, op->qd, op->qd32);
     LAUNCH_CHECK();
     op->qd32_valid = true;
   }
+  if (op->v32 < 0) TRY(choose_variant32(op));
   return FEPA_OK;
 }
 
@@ -774,6 +863,22 @@ int fepa_op_apply_f32(fepa_op* op, const float* x, float* y) {
   TRY(launch_apply32_nocount(op, x, y, nullptr, op->stream));
   g_launches.fetch_add(1);
   return FEPA_OK;
+}
+
+int fepa_op_set_f32_variant(fepa_op* op, int32_t variant) {
+  if (!op) return fail(FEPA_ERR_ARG, "op is null");
+  if (variant < -1 || variant >= N32_VARIANTS) return fail(FEPA_ERR_ARG, "variant %d outside -1..%d", variant,
+                                                            N32_VARIANTS - 1);
+  op->v32_forced = variant;
+  op->v32 = variant;  // -1: choose again at next use
+  return FEPA_OK;
+}
+
+int32_t fepa_op_f32_variant(const fepa_op* op) { return op ? op->v32 : -1; }
+
+const char* fepa_f32_variant_name(int32_t variant) {
+  static const char* names[N32_VARIANTS] = {"tma-staged D", "direct D", "direct D, half block"};
+  return (variant >= 0 && variant < N32_VARIANTS) ? names[variant] : "unknown";
 }
 
 int fepa_op_diagonal(fepa_op* op, double* diag) {

@@ -33,7 +33,11 @@ struct Tab32 {
   static __device__ __forceinline__ float G(int i, int a) { return c_tab32[OFF + 100 + i * (P + 1) + a]; }
 };
 
-template <int P, int Q, bool DIFF>
+// Launch shape of one compiled variant.  STAGE_D: D of the block's elements is brought
+// into shared memory by one TMA bulk copy (true) or read by each thread straight from
+// HBM in stage 3 (false: a smaller block footprint, so more warps per SM).  NE_DIV
+// divides the default number of elements per block.
+template <int P, int Q, bool DIFF, bool STAGE_D = true, int NE_DIV = 1>
 struct TmaShape {
   static constexpr int N = P + 1;
   static constexpr int NC = DIFF ? 6 : 1;
@@ -44,8 +48,9 @@ struct TmaShape {
   static constexpr int NC2 = DIFF ? 3 : 1;
   static constexpr int WORK = N * N * N + NC1 * N * N * Q + NC2 * N * Q * Q;  // stage buffers, floats
   static constexpr int TPE = Q * Q;
-  static constexpr int NE = (256 / TPE) > 0 ? (256 / TPE) : 1;
-  static constexpr int SMEM = 16 + NE * (DELEM + WORK) * 4;
+  static constexpr int NE0 = (256 / TPE) > 0 ? (256 / TPE) : 1;
+  static constexpr int NE = (NE0 / NE_DIV) > 0 ? (NE0 / NE_DIV) : 1;
+  static constexpr int SMEM = 16 + NE * ((STAGE_D ? DELEM : 0) + WORK) * 4;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -85,22 +90,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
   return false;
 }
 
-template <int P, int Q, bool DIFF>
-__global__ void __launch_bounds__(TmaShape<P, Q, DIFF>::TPE * TmaShape<P, Q, DIFF>::NE)
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV>
+__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
-  using S = TmaShape<P, Q, DIFF>;
+  using S = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>;
   using T = Tab32<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
   if (skip && *skip) return;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
-  float* sD = reinterpret_cast<float*>(smem_raw + 16);
-  float* sW = sD + NE * S::DELEM;
+  extern __shared__ __align__(16) unsigned char smem_tma[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma);
+  float* sD = reinterpret_cast<float*>(smem_tma + 16);
+  float* sW = sD + (STAGE_D ? NE * S::DELEM : 0);
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
-  if (tid == 0 && el == 0) {
+  if (STAGE_D && tid == 0 && el == 0) {
     mbar_init(mbar, 1);
     const uint32_t bytes = (uint32_t)ne * S::DELEM * 4u;
     mbar_expect_tx(mbar, bytes);
@@ -169,14 +174,18 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     }
   }
 
-  // D must have landed before stage 3; every thread observes the barrier (bounded)
-  const bool ok = mbar_wait_bounded(mbar);
-  if (__syncthreads_or(!ok)) {
-    if (tid == 0 && el == 0) {
-      atomicOr(err, 1);
-      mbar_wait_bounded(mbar);  // let the copy in flight finish before the block exits
+  if (STAGE_D) {
+    // D must have landed before stage 3; every thread observes the barrier (bounded)
+    const bool ok = mbar_wait_bounded(mbar);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && el == 0) {
+        atomicOr(err, 1);
+        mbar_wait_bounded(mbar);  // let the copy in flight finish before the block exits
+      }
+      return;
     }
-    return;
+  } else {
+    __syncthreads();
   }
 
   // stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers
@@ -192,7 +201,7 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
       a0[c] = 0.f;
       if (DIFF) a1[c] = a2[c] = 0.f;
     }
-    const float* dE = sD + el * S::DELEM + tid;
+    const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       if (DIFF) {

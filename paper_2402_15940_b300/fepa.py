@@ -66,6 +66,9 @@ SIGNATURES = [
     ("fepa_op_qp_coords", ctypes.c_int, [_P, _P]),
     ("fepa_op_apply", ctypes.c_int, [_P, _P, _P]),
     ("fepa_op_apply_f32", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_op_set_f32_variant", ctypes.c_int, [_P, _I32]),
+    ("fepa_op_f32_variant", _I32, [_P]),
+    ("fepa_f32_variant_name", ctypes.c_char_p, [_I32]),
     ("fepa_op_diagonal", ctypes.c_int, [_P, _P]),
     ("fepa_op_rhs", ctypes.c_int, [_P, _P, _P]),
     ("fepa_op_rhs_sine", ctypes.c_int, [_P, _D, _P]),
@@ -245,6 +248,14 @@ class Operator:
         self._sync_stream()
         _check(self._lib.fepa_op_apply_f32(self._h, px, py))
         return y
+
+    def set_f32_variant(self, variant):
+        """-1: autotune at next FP32 use; 0..2: force a compiled launch shape."""
+        _check(self._lib.fepa_op_set_f32_variant(self._h, int(variant)))
+
+    def f32_variant(self):
+        v = int(self._lib.fepa_op_f32_variant(self._h))
+        return v, self._lib.fepa_f32_variant_name(v).decode()
 
     def set_cg_mode(self, mode):
         _check(self._lib.fepa_op_set_cg_mode(self._h, {"graph": CG_GRAPH, "stream": CG_STREAM}.get(mode, mode)))

@@ -64,6 +64,29 @@ def test_apply_f32_matches_oracle(p, form):
     assert e <= TOL32, e
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("form,p", [("diffusion", 1), ("diffusion", 4), ("mass", 3), ("diffusion", 8),
+                                    ("mass", 6)])
+def test_every_f32_variant_matches_oracle(form, p, variant):
+    op, mesh = make(SHAPES[p], p, form, seed=11 + p)
+    op.set_f32_variant(variant)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    x32 = FI.uniform_vector(op.N, seed=13).astype(np.float32)
+    y = op.apply_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert op.f32_variant()[0] == variant
+    assert rel(y, oracle_action(mesh, p, form, x32.astype(np.float64), ess=ess.astype(np.int64))) <= TOL32
+
+
+def test_autotuned_variant_is_recorded():
+    op, _ = make((4, 4, 4), 3, "diffusion", seed=3)
+    x32 = torch.zeros(op.N, dtype=torch.float32, device="cuda")
+    assert op.f32_variant()[0] == -1
+    op.apply_f32(x32)
+    v, name = op.f32_variant()
+    assert 0 <= v <= 2 and name != "unknown"
+
+
 @pytest.mark.parametrize("p", [2, 5, 8])
 def test_apply_f32_constrained(p):
     op, mesh = make(SHAPES[p], p, "diffusion", seed=3)
