@@ -182,7 +182,9 @@ int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
 /*
  * Launch shape of the FP32 kernel.  Variants: 0 = D staged into shared memory by a TMA
  * bulk copy, 1 = D read directly from HBM (smaller blocks, more warps per SM), 2 = as 1
- * with half as many elements per block.  By default (variant -1) the first FP32 use
+ * with half as many elements per block, 3 = persistent blocks pipelined over element
+ * groups (TMA copy of the next group's D and cp.async gather of its x overlap the
+ * current group's arithmetic).  By default (variant -1) the first FP32 use
  * times every variant on this op's mesh and keeps the fastest; the choice is cached per
  * device and (p, q, form) for the process.  All variants compute the same result.
  */

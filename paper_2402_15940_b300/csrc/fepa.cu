@@ -83,12 +83,12 @@ template <typename R>
 using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*);
 using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
 
-constexpr int N32_VARIANTS = 3;  // (staged D, NE), (direct D, NE), (direct D, NE/2)
+constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
 
 struct Apply32Variant {
   Apply32Fn fn;
-  int smem, ne;
-  const char* name;
+  int smem, ne, threads_y;
+  bool persistent;
 };
 
 struct KernelSet {
@@ -107,11 +107,13 @@ KernelSet make_set() {
   KernelSet k;
   k.apply = pa_apply<double, P, Q, DIFF>;
   k.v32[0] = {pa_apply_f32_tma<P, Q, DIFF, true, 1>, TmaShape<P, Q, DIFF, true, 1>::SMEM,
-              TmaShape<P, Q, DIFF, true, 1>::NE, "tma-staged D"};
+              TmaShape<P, Q, DIFF, true, 1>::NE, TmaShape<P, Q, DIFF, true, 1>::NE, false};
   k.v32[1] = {pa_apply_f32_tma<P, Q, DIFF, false, 1>, TmaShape<P, Q, DIFF, false, 1>::SMEM,
-              TmaShape<P, Q, DIFF, false, 1>::NE, "direct D"};
+              TmaShape<P, Q, DIFF, false, 1>::NE, TmaShape<P, Q, DIFF, false, 1>::NE, false};
   k.v32[2] = {pa_apply_f32_tma<P, Q, DIFF, false, 2>, TmaShape<P, Q, DIFF, false, 2>::SMEM,
-              TmaShape<P, Q, DIFF, false, 2>::NE, "direct D, half block"};
+              TmaShape<P, Q, DIFF, false, 2>::NE, TmaShape<P, Q, DIFF, false, 2>::NE, false};
+  k.v32[3] = {pa_apply_f32_pipe<P, Q, DIFF>, PipeShape<P, Q, DIFF>::SMEM, PipeShape<P, Q, DIFF>::NE,
+              PipeShape<P, Q, DIFF>::NE, true};
 
   k.diag = pa_diag_f64<P, Q, DIFF>;
   k.rhs = pa_rhs_f64<P, Q>;
@@ -195,6 +197,7 @@ struct fepa_op {
   float* qd32 = nullptr;
   bool qd32_valid = false;
   int v32 = -1;        // FP32 kernel variant in use (-1: not chosen yet)
+  int v32_grid[4] = {0, 0, 0, 0};  // launch grid per variant (persistent: SMs x resident blocks)
   int v32_forced = -1; // variant set by the caller (-1: autotune)
   int* err = nullptr;  // device word set by kernels whose bounded waits expired
   // CG workspace (allocated on first solve)
@@ -262,9 +265,30 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
 // y += A x in FP32 with variant v (launch only; not counted)
 int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const int* skip, cudaStream_t s) {
   const Apply32Variant& k = op->ks.v32[v];
-  const int grid = (int)((op->E + k.ne - 1) / k.ne);
-  k.fn<<<grid, dim3(op->ks.apply_tpe, k.ne), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip, op->err);
+  const int grid = op->v32_grid[v];
+  if (grid <= 0) return fail(FEPA_ERR_UNSUPPORTED, "FP32 variant %d cannot run with this shape", v);
+  k.fn<<<grid, dim3(op->ks.apply_tpe, k.threads_y), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip,
+                                                                  op->err);
   BODY_CHECK();
+  return FEPA_OK;
+}
+
+// grid of every variant: one block per group, or SMs x resident blocks (persistent)
+int size_variants32(fepa_op* op) {
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->device));
+  for (int v = 0; v < N32_VARIANTS; ++v) {
+    const Apply32Variant& k = op->ks.v32[v];
+    const int64_t groups = (op->E + k.ne - 1) / k.ne;
+    if (!k.persistent) {
+      op->v32_grid[v] = (int)groups;
+      continue;
+    }
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, op->ks.apply_tpe * k.threads_y, k.smem));
+    const int64_t g = (int64_t)per_sm * sms;
+    op->v32_grid[v] = (int)(g < groups ? g : groups);
+  }
   return FEPA_OK;
 }
 
@@ -351,6 +375,7 @@ int time_variants32(fepa_op* op, int* best) {
   if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(float), s) != cudaSuccess)
     rc = fail(FEPA_ERR_CUDA, "memset failed");
   for (int v = 0; rc == FEPA_OK && v < N32_VARIANTS; ++v) {
+    if (op->v32_grid[v] <= 0) continue;
     for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply32_variant(op, v, x, y, nullptr, s);
     if (rc != FEPA_OK) break;
     cudaEventRecord(e0, s);
@@ -415,6 +440,7 @@ int ensure_f32(fepa_op* op) {
     CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->G32h.data(), op->G32h.size() * sizeof(float),
                                      (slot + 100) * sizeof(float), cudaMemcpyHostToDevice, s));
     for (int v = 0; v < N32_VARIANTS; ++v) TRY(allow_smem((const void*)op->ks.v32[v].fn, op->ks.v32[v].smem));
+    TRY(size_variants32(op));
   }
   if (!op->qd32_valid) {
     pad_to_f32<<<grid_for(count, 256, 148 * 32), 256, 0, s>>>(op->E, ncomp, q3, op->ks.d32_stride, op->qd, op->qd32);
@@ -877,7 +903,8 @@ int fepa_op_set_f32_variant(fepa_op* op, int32_t variant) {
 int32_t fepa_op_f32_variant(const fepa_op* op) { return op ? op->v32 : -1; }
 
 const char* fepa_f32_variant_name(int32_t variant) {
-  static const char* names[N32_VARIANTS] = {"tma-staged D", "direct D", "direct D, half block"};
+  static const char* names[N32_VARIANTS] = {"tma-staged D", "direct D", "direct D, half block",
+                                             "persistent pipeline (TMA D, cp.async gather)"};
   return (variant >= 0 && variant < N32_VARIANTS) ? names[variant] : "unknown";
 }
 

@@ -1,15 +1,21 @@
 // FP32 fused partial-assembly action for the mixed-precision solve (the operator
 // y = G^T B^T D B G x of Fig. fig_feod, arXiv 2402.15940), built for an HBM-bound
-// kernel on sm_103a:
-//   * each thread block owns NE consecutive elements; at entry one thread issues a
-//     single TMA bulk copy (cp.async.bulk, completion on an mbarrier) of the block's
-//     D data -- contiguous in HBM -- into shared memory, which overlaps the gather
-//     and the first two contraction stages;
+// kernel on sm_103a.  Common to all variants:
 //   * the 1D tables live in __constant__ memory at compile-time offsets, so with the
 //     loops unrolled they are free FMA operands;
 //   * every stage is register-blocked: a thread loads one line of its element once
-//     and produces all outputs of that line (stage 3, the pointwise D and the
-//     transposed stage 3 stay in registers per (i,j) column, as in the FP64 kernel).
+//     and produces all outputs of that line; stage 3, the pointwise D and the
+//     transposed stage 3 stay in registers per (i,j) column;
+//   * shared-memory line and plane strides are padded to spread banks.
+// Variants (chosen per (p, q, form) by the autotuner in fepa.cu):
+//   0  one element group per block, the group's D staged by one TMA bulk copy
+//      (cp.async.bulk + mbarrier) that overlaps the gather and stages 1-2;
+//   1  as 0 with D read straight from HBM in stage 3 (smaller footprint, more warps);
+//   2  as 1 with half as many elements per block;
+//   3  persistent blocks, software-pipelined over element groups: while group g is
+//      computed, D(g+1) arrives by TMA, the map of g+1 is loaded into registers and
+//      x(g+1) is gathered by cp.async (asynchronous 4-byte copies) into the other
+//      buffer, so the dependent map -> x -> compute latency chain is hidden.
 // D here is the FP32 copy with each component padded to a multiple of 4 floats, so
 // every element's block is a multiple of 16 bytes (the bulk-copy granularity).
 #pragma once
@@ -33,24 +39,48 @@ struct Tab32 {
   static __device__ __forceinline__ float G(int i, int a) { return c_tab32[OFF + 100 + i * (P + 1) + a]; }
 };
 
-// Launch shape of one compiled variant.  STAGE_D: D of the block's elements is brought
-// into shared memory by one TMA bulk copy (true) or read by each thread straight from
-// HBM in stage 3 (false: a smaller block footprint, so more warps per SM).  NE_DIV
-// divides the default number of elements per block.
-template <int P, int Q, bool DIFF, bool STAGE_D = true, int NE_DIV = 1>
-struct TmaShape {
+// Shared-memory layout of one element's stage buffers (floats), padded:
+//   X  [c][b][a]     line (b,c) of length n at stride XL (odd)
+//   S1 [m][c][b][i]  line (b,c) of length Q at stride Q1 (odd)
+//   S2 [m][c][j][i]  plane c of Q*Q at stride P2 (P2 = Q mod 32: consecutive planes
+//                    start Q banks apart)
+template <int P, int Q, bool DIFF>
+struct F32Layout {
   static constexpr int N = P + 1;
   static constexpr int NC = DIFF ? 6 : 1;
   static constexpr int Q3 = Q * Q * Q;
-  static constexpr int DSTRIDE = (Q3 + 3) & ~3;  // floats per stored component (16-byte multiple)
+  static constexpr int DSTRIDE = (Q3 + 3) & ~3;  // floats per stored D component (16-byte multiple)
   static constexpr int DELEM = NC * DSTRIDE;     // floats of D per element
   static constexpr int NC1 = DIFF ? 2 : 1;
   static constexpr int NC2 = DIFF ? 3 : 1;
-  static constexpr int WORK = N * N * N + NC1 * N * N * Q + NC2 * N * Q * Q;  // stage buffers, floats
+  static constexpr int XL = N | 1;
+  static constexpr int Q1 = Q | 1;
+  static constexpr int P2 = Q * Q + (((Q - (Q * Q) % 32) % 32) + 32) % 32;
+  static constexpr int XSZ = XL * N * N;
+  static constexpr int S1C = Q1 * N * N;  // one S1 component
+  static constexpr int S2C = P2 * N;      // one S2 component
+  static constexpr int WORK = NC1 * S1C + NC2 * S2C;
   static constexpr int TPE = Q * Q;
   static constexpr int NE0 = (256 / TPE) > 0 ? (256 / TPE) : 1;
-  static constexpr int NE = (NE0 / NE_DIV) > 0 ? (NE0 / NE_DIV) : 1;
-  static constexpr int SMEM = 16 + NE * ((STAGE_D ? DELEM : 0) + WORK) * 4;
+};
+
+// Launch shape of variants 0-2.
+template <int P, int Q, bool DIFF, bool STAGE_D = true, int NE_DIV = 1>
+struct TmaShape : F32Layout<P, Q, DIFF> {
+  using L = F32Layout<P, Q, DIFF>;
+  static constexpr int NE = (L::NE0 / NE_DIV) > 0 ? (L::NE0 / NE_DIV) : 1;
+  static constexpr int SMEM = 16 + NE * ((STAGE_D ? L::DELEM : 0) + L::XSZ + L::WORK) * 4;
+};
+
+// Launch shape of variant 3 (double-buffered D, x and map per block).
+template <int P, int Q, bool DIFF>
+struct PipeShape : F32Layout<P, Q, DIFF> {
+  using L = F32Layout<P, Q, DIFF>;
+  static constexpr int NE = L::NE0;
+  static constexpr int T = L::TPE * NE;
+  static constexpr int IDX = NE * L::N * L::N * L::N;  // map entries per group
+  static constexpr int IDXR = (IDX + T - 1) / T;       // per thread
+  static constexpr int SMEM = 16 + 2 * NE * L::DELEM * 4 + 2 * NE * L::XSZ * 4 + 2 * IDX * 4 + NE * L::WORK * 4;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -83,25 +113,226 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase 0 of the barrier: false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar) {
+// Bounded wait for the given phase parity of the barrier: false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity = 0) {
   for (int it = 0; it < (1 << 22); ++it)
-    if (mbar_try_wait(bar, 0)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
 
+// asynchronous 4-byte global -> shared copy (no register round trip)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// stages (called by every thread of the block; `tid` is the thread's index within
+// its element, `live` whether its element exists)
+// ---------------------------------------------------------------------------
+
+// stage 1 (x): line (b,c) -> S1[m][c][b][i] for all i
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage1(int tid, bool live, const float* sX, float* S1) {
+  using L = F32Layout<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!(live && tid < n * n)) return;
+  float xv[n];
+#pragma unroll
+  for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float sb = 0.f, sg = 0.f;
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      sb = fmaf(T::B(i, a), xv[a], sb);
+      if (DIFF) sg = fmaf(T::G(i, a), xv[a], sg);
+    }
+    S1[tid * L::Q1 + i] = sb;
+    if (DIFF) S1[L::S1C + tid * L::Q1 + i] = sg;
+  }
+}
+
+// stage 2 (y): line (i,c) -> S2[m][c][j][i] for all j
+//   DIFF: m=0 (x:G,y:B), m=1 (x:B,y:G), m=2 (x:B,y:B); mass: m=0 (B,B)
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage2(int tid, bool live, const float* S1, float* S2) {
+  using L = F32Layout<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!(live && tid < Q * n)) return;
+  const int i = tid % Q, c = tid / Q;
+  float vb[n], vg[n];
+#pragma unroll
+  for (int b = 0; b < n; ++b) {
+    vb[b] = S1[(b + n * c) * L::Q1 + i];
+    if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * L::Q1 + i];
+  }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    float bb = 0.f, bg = 0.f, gb = 0.f;
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      bb = fmaf(T::B(j, b), vb[b], bb);
+      if (DIFF) {
+        bg = fmaf(T::G(j, b), vb[b], bg);
+        gb = fmaf(T::B(j, b), vg[b], gb);
+      }
+    }
+    const int o = c * L::P2 + j * Q + i;
+    if (DIFF) {
+      S2[o] = gb;
+      S2[L::S2C + o] = bg;
+      S2[2 * L::S2C + o] = bb;
+    } else {
+      S2[o] = bb;
+    }
+  }
+}
+
+// stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers; D at dE
+// (shared or global), component stride DSTRIDE, point k at dE[k*Q*Q]
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE) {
+  using L = F32Layout<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!live) return;
+  float c0[n], c1[n], c2[n], a0[n], a1[n], a2[n];
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    c0[c] = S2[c * L::P2 + tid];
+    if (DIFF) {
+      c1[c] = S2[L::S2C + c * L::P2 + tid];
+      c2[c] = S2[2 * L::S2C + c * L::P2 + tid];
+    }
+    a0[c] = 0.f;
+    if (DIFF) a1[c] = a2[c] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    if (DIFF) {
+      float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        u0 = fmaf(T::B(k, c), c0[c], u0);
+        u1 = fmaf(T::B(k, c), c1[c], u1);
+        u2 = fmaf(T::G(k, c), c2[c], u2);
+      }
+      const float* dk = dE + k * Q * Q;
+      const float d00 = dk[0], d01 = dk[L::DSTRIDE], d02 = dk[2 * L::DSTRIDE], d11 = dk[3 * L::DSTRIDE],
+                  d12 = dk[4 * L::DSTRIDE], d22 = dk[5 * L::DSTRIDE];
+      const float v0 = fmaf(d00, u0, fmaf(d01, u1, d02 * u2));
+      const float v1 = fmaf(d01, u0, fmaf(d11, u1, d12 * u2));
+      const float v2 = fmaf(d02, u0, fmaf(d12, u1, d22 * u2));
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        a0[c] = fmaf(T::B(k, c), v0, a0[c]);
+        a1[c] = fmaf(T::B(k, c), v1, a1[c]);
+        a2[c] = fmaf(T::G(k, c), v2, a2[c]);
+      }
+    } else {
+      float u = 0.f;
+#pragma unroll
+      for (int c = 0; c < n; ++c) u = fmaf(T::B(k, c), c0[c], u);
+      const float v = dE[k * Q * Q] * u;
+#pragma unroll
+      for (int c = 0; c < n; ++c) a0[c] = fmaf(T::B(k, c), v, a0[c]);
+    }
+  }
+  // each thread overwrites only its own column
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    S2[c * L::P2 + tid] = a0[c];
+    if (DIFF) {
+      S2[L::S2C + c * L::P2 + tid] = a1[c];
+      S2[2 * L::S2C + c * L::P2 + tid] = a2[c];
+    }
+  }
+}
+
+// stage 2^T (y): line (i,c) -> S1[0][c][b][i] = sum_j B[j][b] A0,
+//                             S1[1][c][b][i] = sum_j G[j][b] A1 + B[j][b] A2
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage2t(int tid, bool live, const float* S2, float* S1) {
+  using L = F32Layout<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!(live && tid < Q * n)) return;
+  const int i = tid % Q, c = tid / Q;
+  float v0[Q], v1[Q], v2[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    v0[j] = S2[c * L::P2 + j * Q + i];
+    if (DIFF) {
+      v1[j] = S2[L::S2C + c * L::P2 + j * Q + i];
+      v2[j] = S2[2 * L::S2C + c * L::P2 + j * Q + i];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < n; ++b) {
+    float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      t0 = fmaf(T::B(j, b), v0[j], t0);
+      if (DIFF) t1 = fmaf(T::G(j, b), v1[j], fmaf(T::B(j, b), v2[j], t1));
+    }
+    S1[(b + n * c) * L::Q1 + i] = t0;
+    if (DIFF) S1[L::S1C + (b + n * c) * L::Q1 + i] = t1;
+  }
+}
+
+// stage 1^T (x) and G^T: line (b,c) -> y[g(a,b,c)] += sum_i G[i][a] T0 + B[i][a] T1.
+// gl: the element's n^3 map entries (global or shared memory).
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1, const int* gl,
+                                            const float* __restrict__ x, float* __restrict__ y) {
+  using L = F32Layout<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!(live && tid < n * n)) return;
+  float t0[Q], t1[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    t0[i] = S1[tid * L::Q1 + i];
+    if (DIFF) t1[i] = S1[L::S1C + tid * L::Q1 + i];
+  }
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (DIFF)
+        s = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], s));
+      else
+        s = fmaf(T::B(i, a), t0[i], s);
+    }
+    const int gi = gl[a + n * tid];
+    if (gi >= 0) {
+      atomicAdd(y + gi, s);
+    } else if (!((~gi) & ESS_SKIP)) {
+      atomicAdd(y + (~gi), x[~gi]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// variants 0-2: one element group per block
+// ---------------------------------------------------------------------------
 template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
   using S = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>;
-  using T = Tab32<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_tma[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma);
   float* sD = reinterpret_cast<float*>(smem_tma + 16);
-  float* sW = sD + (STAGE_D ? NE * S::DELEM : 0);
+  float* sXall = sD + (STAGE_D ? NE * S::DELEM : 0);
+  float* sWall = sXall + NE * S::XSZ;
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
@@ -112,68 +343,19 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     bulk_copy_g2s(sD, qd32 + e0 * S::DELEM, bytes, mbar);
   }
   const bool live = el < ne;
-  float* sX = sW + el * S::WORK;
-  float* S1 = sX + n * n * n;
-  float* S2 = S1 + S::NC1 * n * n * Q;
+  float* sX = sXall + el * S::XSZ;
+  float* S1 = sWall + el * S::WORK;
+  float* S2 = S1 + S::NC1 * S::S1C;
   const int* g = gmap + (e0 + el) * (n * n * n);
   if (live)
     for (int l = tid; l < n * n * n; l += TPE) {
       const int gi = g[l];
-      sX[l] = gi >= 0 ? x[gi] : 0.f;
+      sX[(l / n) * S::XL + l % n] = gi >= 0 ? x[gi] : 0.f;
     }
   __syncthreads();
-
-  // stage 1 (x): line (b,c) -> S1[m][c][b][i] for all i
-  if (live && tid < n * n) {
-    float xv[n];
-#pragma unroll
-    for (int a = 0; a < n; ++a) xv[a] = sX[tid * n + a];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float sb = 0.f, sg = 0.f;
-#pragma unroll
-      for (int a = 0; a < n; ++a) {
-        sb = fmaf(T::B(i, a), xv[a], sb);
-        if (DIFF) sg = fmaf(T::G(i, a), xv[a], sg);
-      }
-      S1[tid * Q + i] = sb;
-      if (DIFF) S1[n * n * Q + tid * Q + i] = sg;
-    }
-  }
+  f32_stage1<P, Q, DIFF>(tid, live, sX, S1);
   __syncthreads();
-
-  // stage 2 (y): line (i,c) -> S2[m][c][j][i] for all j
-  //   DIFF: m=0 (x:G,y:B), m=1 (x:B,y:G), m=2 (x:B,y:B); mass: m=0 (B,B)
-  if (live && tid < Q * n) {
-    const int i = tid % Q, c = tid / Q;
-    float vb[n], vg[n];
-#pragma unroll
-    for (int b = 0; b < n; ++b) {
-      vb[b] = S1[i + Q * (b + n * c)];
-      if (DIFF) vg[b] = S1[n * n * Q + i + Q * (b + n * c)];
-    }
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      float bb = 0.f, bg = 0.f, gb = 0.f;
-#pragma unroll
-      for (int b = 0; b < n; ++b) {
-        bb = fmaf(T::B(j, b), vb[b], bb);
-        if (DIFF) {
-          bg = fmaf(T::G(j, b), vb[b], bg);
-          gb = fmaf(T::B(j, b), vg[b], gb);
-        }
-      }
-      const int o = c * Q * Q + j * Q + i;
-      if (DIFF) {
-        S2[o] = gb;
-        S2[n * Q * Q + o] = bg;
-        S2[2 * n * Q * Q + o] = bb;
-      } else {
-        S2[o] = bb;
-      }
-    }
-  }
-
+  f32_stage2<P, Q, DIFF>(tid, live, S1, S2);
   if (STAGE_D) {
     // D must have landed before stage 3; every thread observes the barrier (bounded)
     const bool ok = mbar_wait_bounded(mbar);
@@ -187,115 +369,123 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   } else {
     __syncthreads();
   }
-
-  // stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers
-  if (live) {
-    float c0[n], c1[n], c2[n], a0[n], a1[n], a2[n];
-#pragma unroll
-    for (int c = 0; c < n; ++c) {
-      c0[c] = S2[c * Q * Q + tid];
-      if (DIFF) {
-        c1[c] = S2[n * Q * Q + c * Q * Q + tid];
-        c2[c] = S2[2 * n * Q * Q + c * Q * Q + tid];
-      }
-      a0[c] = 0.f;
-      if (DIFF) a1[c] = a2[c] = 0.f;
-    }
-    const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      if (DIFF) {
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          u0 = fmaf(T::B(k, c), c0[c], u0);
-          u1 = fmaf(T::B(k, c), c1[c], u1);
-          u2 = fmaf(T::G(k, c), c2[c], u2);
-        }
-        const float* dk = dE + k * Q * Q;
-        const float d00 = dk[0], d01 = dk[S::DSTRIDE], d02 = dk[2 * S::DSTRIDE], d11 = dk[3 * S::DSTRIDE],
-                    d12 = dk[4 * S::DSTRIDE], d22 = dk[5 * S::DSTRIDE];
-        const float v0 = fmaf(d00, u0, fmaf(d01, u1, d02 * u2));
-        const float v1 = fmaf(d01, u0, fmaf(d11, u1, d12 * u2));
-        const float v2 = fmaf(d02, u0, fmaf(d12, u1, d22 * u2));
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          a0[c] = fmaf(T::B(k, c), v0, a0[c]);
-          a1[c] = fmaf(T::B(k, c), v1, a1[c]);
-          a2[c] = fmaf(T::G(k, c), v2, a2[c]);
-        }
-      } else {
-        float u = 0.f;
-#pragma unroll
-        for (int c = 0; c < n; ++c) u = fmaf(T::B(k, c), c0[c], u);
-        const float v = dE[k * Q * Q] * u;
-#pragma unroll
-        for (int c = 0; c < n; ++c) a0[c] = fmaf(T::B(k, c), v, a0[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < n; ++c) {
-      S2[c * Q * Q + tid] = a0[c];
-      if (DIFF) {
-        S2[n * Q * Q + c * Q * Q + tid] = a1[c];
-        S2[2 * n * Q * Q + c * Q * Q + tid] = a2[c];
-      }
-    }
-  }
+  const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
+  f32_stage3<P, Q, DIFF>(tid, live, S2, dE);
   __syncthreads();
-
-  // stage 2^T (y): line (i,c) -> S1[0][c][b][i] = sum_j B[j][b] A0,
-  //                               S1[1][c][b][i] = sum_j G[j][b] A1 + B[j][b] A2
-  if (live && tid < Q * n) {
-    const int i = tid % Q, c = tid / Q;
-    float v0[Q], v1[Q], v2[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      v0[j] = S2[c * Q * Q + j * Q + i];
-      if (DIFF) {
-        v1[j] = S2[n * Q * Q + c * Q * Q + j * Q + i];
-        v2[j] = S2[2 * n * Q * Q + c * Q * Q + j * Q + i];
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < n; ++b) {
-      float t0 = 0.f, t1 = 0.f;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        t0 = fmaf(T::B(j, b), v0[j], t0);
-        if (DIFF) t1 = fmaf(T::G(j, b), v1[j], fmaf(T::B(j, b), v2[j], t1));
-      }
-      S1[i + Q * (b + n * c)] = t0;
-      if (DIFF) S1[n * n * Q + i + Q * (b + n * c)] = t1;
-    }
-  }
+  f32_stage2t<P, Q, DIFF>(tid, live, S2, S1);
   __syncthreads();
+  f32_stage1t<P, Q, DIFF>(tid, live, S1, g, x, y);
+}
 
-  // stage 1^T (x): line (b,c) -> y[g(a,b,c)] += sum_i G[i][a] T0 + B[i][a] T1
-  if (live && tid < n * n) {
-    float t0[Q], t1[Q];
+// ---------------------------------------------------------------------------
+// variant 3: persistent, software-pipelined over element groups
+// ---------------------------------------------------------------------------
+template <int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(PipeShape<P, Q, DIFF>::T)
+pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
+                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
+  using S = PipeShape<P, Q, DIFF>;
+  constexpr int n = S::N, n3 = n * n * n, TPE = S::TPE, NE = S::NE, T = S::T;
+  if (skip && *skip) return;
+  const int G = (E + NE - 1) / NE;
+  int g = blockIdx.x;
+  if (g >= G) return;
+  extern __shared__ __align__(16) unsigned char smem_pipe[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_pipe);  // [2]
+  float* sD = reinterpret_cast<float*>(smem_pipe + 16);     // [2][NE*DELEM]
+  float* sX = sD + 2 * NE * S::DELEM;                       // [2][NE*XSZ]
+  int* sI = reinterpret_cast<int*>(sX + 2 * NE * S::XSZ);   // [2][IDX]
+  float* sW = reinterpret_cast<float*>(sI + 2 * S::IDX);    // [NE][WORK]
+  const int tid = threadIdx.x, el = threadIdx.y, flat = el * TPE + tid;
+  float* S1 = sW + el * S::WORK;
+  float* S2 = S1 + S::NC1 * S::S1C;
+
+  // D of group gg into buffer b (one thread)
+  auto issue_d = [&](int gg, int b) {
+    const int64_t e0 = (int64_t)gg * NE;
+    const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+    const uint32_t bytes = (uint32_t)ne * S::DELEM * 4u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&mbar[b], bytes);
+    bulk_copy_g2s(sD + b * NE * S::DELEM, qd32 + e0 * S::DELEM, bytes, &mbar[b]);
+  };
+  // map entries of group gg held by this thread
+  auto load_idx = [&](int gg, int (&r)[S::IDXR]) {
+    const int64_t base = (int64_t)gg * S::IDX;
+    const int64_t lim = (int64_t)E * n3 - base;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      t0[i] = S1[tid * Q + i];
-      if (DIFF) t1[i] = S1[n * n * Q + tid * Q + i];
+    for (int k = 0; k < S::IDXR; ++k) {
+      const int f = flat + k * T;
+      r[k] = (f < S::IDX && f < lim) ? gmap[base + f] : 0;
     }
+  };
+  // store the map entries and gather x of group gg into buffer b (asynchronously)
+  auto gather = [&](int gg, int b, const int (&r)[S::IDXR]) {
+    const int64_t lim = (int64_t)E * n3 - (int64_t)gg * S::IDX;
 #pragma unroll
-    for (int a = 0; a < n; ++a) {
-      float s = 0.f;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (DIFF)
-          s = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], s));
+    for (int k = 0; k < S::IDXR; ++k) {
+      const int f = flat + k * T;
+      if (f < S::IDX && f < lim) {
+        const int gi = r[k];
+        sI[b * S::IDX + f] = gi;
+        const int e = f / n3, l = f - e * n3;
+        float* dst = sX + b * NE * S::XSZ + e * S::XSZ + (l / n) * S::XL + (l % n);
+        if (gi >= 0)
+          cp_async4(dst, x + gi);
         else
-          s = fmaf(T::B(i, a), t0[i], s);
-      }
-      const int gi = g[a + n * tid];
-      if (gi >= 0) {
-        atomicAdd(y + gi, s);
-      } else if (!((~gi) & ESS_SKIP)) {
-        atomicAdd(y + (~gi), x[~gi]);
+          *dst = 0.f;
       }
     }
+    cp_async_commit();
+  };
+
+  if (flat == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+  }
+  __syncthreads();
+  if (flat == 0) issue_d(g, 0);
+  {
+    int r[S::IDXR];
+    load_idx(g, r);
+    gather(g, 0, r);
+  }
+  uint32_t ph0 = 0u, ph1 = 0u;  // parity of the next wait on buffer 0 / 1
+  int cur = 0;
+  for (; g < G; g += gridDim.x) {
+    const int gn = g + gridDim.x;
+    const bool has_next = gn < G;
+    const int nxt = cur ^ 1;
+    if (has_next && flat == 0) issue_d(gn, nxt);
+    int r[S::IDXR];
+    if (has_next) load_idx(gn, r);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t e0 = (int64_t)g * NE;
+    const bool live = e0 + el < E;
+    f32_stage1<P, Q, DIFF>(tid, live, sX + cur * NE * S::XSZ + el * S::XSZ, S1);
+    __syncthreads();
+    f32_stage2<P, Q, DIFF>(tid, live, S1, S2);
+    if (has_next) gather(gn, nxt, r);
+    const uint32_t pc = cur ? ph1 : ph0, pn = cur ? ph0 : ph1;
+    const bool ok = mbar_wait_bounded(&mbar[cur], pc);
+    if (cur) ph1 ^= 1u; else ph0 ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (flat == 0) {
+        atomicOr(err, 1);
+        mbar_wait_bounded(&mbar[cur], pc);  // let the copies in flight finish before exiting
+        if (has_next) mbar_wait_bounded(&mbar[nxt], pn);
+      }
+      cp_async_wait_all();
+      return;
+    }
+    f32_stage3<P, Q, DIFF>(tid, live, S2, sD + cur * NE * S::DELEM + el * S::DELEM + tid);
+    __syncthreads();
+    f32_stage2t<P, Q, DIFF>(tid, live, S2, S1);
+    __syncthreads();
+    f32_stage1t<P, Q, DIFF>(tid, live, S1, sI + cur * S::IDX + el * n3, x, y);
+    __syncthreads();
+    cur = nxt;
   }
 }
 

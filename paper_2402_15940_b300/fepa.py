@@ -250,7 +250,7 @@ class Operator:
         return y
 
     def set_f32_variant(self, variant):
-        """-1: autotune at next FP32 use; 0..2: force a compiled launch shape."""
+        """-1: autotune at next FP32 use; 0..3: force a compiled launch shape."""
         _check(self._lib.fepa_op_set_f32_variant(self._h, int(variant)))
 
     def f32_variant(self):

@@ -64,7 +64,7 @@ def test_apply_f32_matches_oracle(p, form):
     assert e <= TOL32, e
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("form,p", [("diffusion", 1), ("diffusion", 4), ("mass", 3), ("diffusion", 8),
                                     ("mass", 6)])
 def test_every_f32_variant_matches_oracle(form, p, variant):
@@ -84,7 +84,7 @@ def test_autotuned_variant_is_recorded():
     assert op.f32_variant()[0] == -1
     op.apply_f32(x32)
     v, name = op.f32_variant()
-    assert 0 <= v <= 2 and name != "unknown"
+    assert 0 <= v <= 3 and name != "unknown"
 
 
 @pytest.mark.parametrize("p", [2, 5, 8])
