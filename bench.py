@@ -121,6 +121,19 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def reduce_max_sum(t, work, dist=None, device="cpu"):
+    """Whole-job aggregation over independent replicas: the slowest rank's time and the
+    total work of all ranks (one all-reduce each; no data-path collective)."""
+    if dist is None:
+        return float(t), float(work)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    ww = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(ww[0])
+
+
 # nominal FP64 rate of the B300 (no FP64 tensor-core path); the FP64 pipe bounds this kernel
 FP64_PEAK_GFLOPS = 1250.0
 
@@ -200,14 +213,8 @@ def run_ours(args, rank, world, dist):
         if dist is not None:
             dist.barrier()
 
-    def reduce_max_sum(t, work):
-        if dist is None:
-            return t, float(work)
-        tt = torch.tensor([t, float(work)], dtype=torch.float64, device="cuda")
-        tm = tt[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        return float(tm[0]), float(tt[1])
+    def aggregate(t, work):
+        return reduce_max_sum(t, work, dist, device="cuda")
 
     def solve(prec):
         if prec == "fp64":
@@ -242,7 +249,7 @@ def run_ours(args, rank, world, dist):
         barrier()
         torch.cuda.synchronize()
         launches = F.launch_count() - l0
-        t, work = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, N * sum(its))
+        t, work = aggregate(ev0.elapsed_time(ev1) / 1e3, N * sum(its))
         return {"value": work / t / 1e9, "ms_per_step": 1e3 * t / args.steps, "iterations_per_step": its,
                 "gpu_launches": launches, "clocks": clk.summary(), "stats": stats[-1]}
 
@@ -287,7 +294,7 @@ def run_ours(args, rank, world, dist):
                 _, st = op.solve_refined_host(bh, xh, rtol=args.rtol, inner_rtol=args.inner_rtol)
                 its += st["inner_iterations"]
         torch.cuda.synchronize()
-        te, work = reduce_max_sum(time.perf_counter() - t0, N * its)
+        te, work = aggregate(time.perf_counter() - t0, N * its)
         return {"value": work / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(vh.nbytes + 2 * bh.nbytes),
                 "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": 1e3 * te / args.steps}
 
