@@ -251,6 +251,59 @@ int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int
 int fepa_solve_refined_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t max_outer,
                             double inner_rtol, int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent problems.  Each problem i is its own structured hex mesh,
+ * order and form; the batch owns one concatenated DOF vector (problem i occupies
+ * [off_i, off_{i+1})), so its operator is block diagonal.  Problems with equal
+ * (p, q = p+2, form) share one fused-kernel launch per action; the CG solve advances
+ * every problem at once with per-problem scalars, stopping rule and iteration count,
+ * skips problems that have converged, and runs as one CUDA graph (while-node) until the
+ * last problem stops.  The paper's operator and solver (Fig. fig_feod, Sec. 2.1, 2.3)
+ * applied to many small problems, where launch count and tail effects decide the
+ * throughput (the strong-scaling concern of Sec. 2.3).
+ * ------------------------------------------------------------------------- */
+typedef struct fepa_batch fepa_batch;
+
+typedef struct fepa_batch_stats {
+  int32_t max_iterations;   /* iterations of the slowest problem */
+  int32_t converged;        /* problems that reached rtol */
+  int32_t status;           /* FEPA_OK when all did, else FEPA_ERR_NOCONV */
+  int32_t reserved;
+  double dof_iterations;    /* sum over problems of N_i * iterations_i */
+  double max_rel_residual;  /* largest ||r_i|| / ||b_i|| at exit */
+} fepa_batch_stats;
+
+/*
+ * Create a batch on the current device.
+ *   count               number of problems (>= 1)
+ *   dims                host int32 [count][3]: nx, ny, nz of each problem
+ *   vertices            host array of count host pointers; problem i's vertex grid as in
+ *                       fepa_op_create ((nx+1)(ny+1)(nz+1) x 3 doubles)
+ *   orders, forms       host int32 [count]: p (1..FEPA_MAX_ORDER) and FEPA_MASS/DIFFUSION
+ *   essential_boundary  1: every diffusion problem fixes all its boundary DOFs
+ *   stream              cudaStream_t (as void*)
+ * q = p+2 for every problem.  Blocks until the data is built.
+ */
+int fepa_batch_create(int32_t count, const int32_t* dims, const double* const* vertices, const int32_t* orders,
+                      const int32_t* forms, int32_t essential_boundary, void* stream, fepa_batch** out);
+void fepa_batch_destroy(fepa_batch* batch);
+int64_t fepa_batch_ndofs(const fepa_batch* batch);                   /* total DOFs */
+int fepa_batch_offsets(const fepa_batch* batch, int64_t* offsets);   /* host, count + 1 entries */
+int32_t fepa_batch_groups(const fepa_batch* batch);                  /* distinct (p, form) */
+int fepa_batch_set_stream(fepa_batch* batch, void* stream);
+
+/* y = A x for every problem at once (x, y: device, total DOFs). */
+int fepa_batch_apply(fepa_batch* batch, const double* x, double* y);
+
+/*
+ * Solve every problem by (Jacobi-)PCG as fepa_cg_solve does, all at once.
+ *   b, x        device, total DOFs (x: initial guesses in, solutions out)
+ *   iterations  host int32 [count] receiving each problem's iteration count (may be null)
+ * Blocks until the last problem stops; FEPA_ERR_NOCONV if any problem hit maxit.
+ */
+int fepa_batch_solve(fepa_batch* batch, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
+                     fepa_batch_stats* stats, int32_t* iterations);
+
 /*
  * CG solve that allocates nothing.  The paper has no counterpart: this call exists
  * for callers that cannot allocate device memory once they are running -- for

@@ -1,0 +1,197 @@
+// Batched Jacobi-PCG over many independent problems at once (one concatenated vector,
+// per-problem scalars).  Every reduction block covers a chunk of exactly one problem
+// (the chunk table below); the last block to finish sums each problem's block partials
+// in a fixed order and updates that problem's scalars, so a problem's iterates do not
+// depend on which other problems share the batch (up to the atomic order of G^T).
+// Converged problems are skipped by every kernel; the loop runs inside one CUDA graph
+// while-node until the last problem stops.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cg_kernels.cuh"
+
+namespace fepa {
+
+struct BState {  // per problem
+  double rho, alpha, beta, bb, rr, tol2;
+  int iter, maxit, converged, pad;
+};
+
+struct BGlobal {  // whole batch
+  unsigned int ticket;
+  int active;  // problems still iterating
+  int done;    // 1 when none is
+  int pad;
+};
+
+struct ChunkTable {
+  const int* blk_prob;     // [nblocks] problem of each reduction block
+  const int64_t* blk_lo;   // [nblocks] first DOF (concatenated numbering)
+  const int64_t* blk_hi;   // [nblocks] one past the last DOF
+  const int* pb_first;     // [nprob] first block of each problem
+  const int* pb_count;     // [nprob] blocks of each problem
+  int nprob;
+};
+
+// Sum, per problem, the NV block partials of its blocks (called by the last block);
+// f(j, sums) receives problem j's totals.  Returns the number of problems f reports
+// as active, summed over the block (valid in every thread after the call).
+template <int NV, typename F>
+__device__ __forceinline__ int per_problem(const ChunkTable& t, const double* partials, F f) {
+  __shared__ int active;
+  if (threadIdx.x == 0) active = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int j = threadIdx.x; j < t.nprob; j += blockDim.x) {
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      s[k] = 0.0;
+      for (int b = t.pb_first[j]; b < t.pb_first[j] + t.pb_count[j]; ++b) s[k] += __ldcg(partials + k * gridDim.x + b);
+    }
+    mine += f(j, s) ? 1 : 0;
+  }
+  atomicAdd(&active, mine);
+  __syncthreads();
+  return active;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+bcg_init(ChunkTable t, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ d,
+         double* __restrict__ h, const double* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
+         double rtol2, int maxit, double* partials) {
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - h[i];
+    const double zi = inv_diag ? ri * inv_diag[i] : ri;
+    r[i] = ri;
+    d[i] = zi;
+    h[i] = 0.0;
+    v[0] += zi * ri;
+    v[1] += ri * ri;
+    v[2] += bi * bi;
+  }
+  double blk[3];
+  block_sum<3>(v, blk);
+  if (publish_partials<3>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<3>(t, partials, [&](int j, const double* s) {
+      BState& q = ps[j];
+      q.rho = s[0];
+      q.rr = s[1];
+      q.bb = s[2];
+      q.tol2 = rtol2 * s[2];
+      q.iter = 0;
+      q.maxit = maxit;
+      q.alpha = q.beta = 0.0;
+      q.converged = (s[1] <= q.tol2) ? 1 : 0;
+      pdone[j] = q.converged;
+      return !q.converged;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+bcg_dot_dh(ChunkTable t, const double* __restrict__ d, const double* __restrict__ h, BState* ps,
+           const int* __restrict__ pdone, BGlobal* gs, double* partials) {
+  if (gs->done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  double v[1] = {0.0};
+  if (!pdone[prob]) {
+    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v[0] += d[i] * h[i];
+  }
+  double blk[1];
+  block_sum<1>(v, blk);
+  if (publish_partials<1>(blk, partials, &gs->ticket)) {
+    per_problem<1>(t, partials, [&](int j, const double* s) {
+      if (!pdone[j]) ps[j].alpha = ps[j].rho / s[0];
+      return false;
+    });
+    if (threadIdx.x == 0) gs->ticket = 0;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+bcg_update(ChunkTable t, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
+           const double* __restrict__ h, const double* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
+           double* partials) {
+  if (gs->done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  double v[2] = {0.0, 0.0};
+  if (!pdone[prob]) {
+    const double alpha = ps[prob].alpha;
+    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      x[i] += alpha * d[i];
+      const double ri = r[i] - alpha * h[i];
+      r[i] = ri;
+      const double zi = inv_diag ? ri * inv_diag[i] : ri;
+      v[0] += zi * ri;
+      v[1] += ri * ri;
+    }
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
+      if (pdone[j]) return false;
+      BState& q = ps[j];
+      q.iter += 1;
+      q.rr = s[1];
+      int stop = 0;
+      if (s[1] <= q.tol2) {
+        q.converged = 1;
+        stop = 1;
+      } else if (q.iter >= q.maxit) {
+        stop = 1;
+      }
+      q.beta = s[0] / q.rho;
+      q.rho = s[0];
+      pdone[j] = stop;
+      return !stop;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+// d = z + beta d, h = 0 for problems still iterating; block 0 sets the while-condition
+__global__ void __launch_bounds__(RED_THREADS)
+bcg_direction(ChunkTable t, const double* __restrict__ r, double* __restrict__ d, double* __restrict__ h,
+              const double* __restrict__ inv_diag, const BState* ps, const int* __restrict__ pdone,
+              const BGlobal* gs, cudaGraphConditionalHandle cond, int use_cond) {
+  const int done = gs->done;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  if (pdone[prob]) return;
+  const double beta = ps[prob].beta;
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+    d[i] = zi + beta * d[i];
+    h[i] = 0.0;
+  }
+}
+
+// 1 on the boundary DOFs of one problem's node grid (concatenated numbering)
+__global__ void mark_boundary(int64_t Nx, int64_t Ny, int64_t Nz, int64_t dof_off, unsigned char* __restrict__ mask) {
+  const int64_t total = Nx * Ny * Nz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = t % Nx, y = (t / Nx) % Ny, z = t / (Nx * Ny);
+    if (x == 0 || y == 0 || z == 0 || x == Nx - 1 || y == Ny - 1 || z == Nz - 1) mask[dof_off + t] = 1;
+  }
+}
+
+}  // namespace fepa

@@ -6,6 +6,7 @@
 // mode) through short host-driven chunks of the same kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -21,6 +22,7 @@
 #include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
 #include "pa_tma_f32.cuh"
+#include "batch_kernels.cuh"
 
 using namespace fepa;
 
@@ -80,7 +82,8 @@ inline int grid_for(int64_t work, int threads, int cap) {
 // compiled kernel instances, indexed by p (1..8), q - p - 1 (0, 1), form (0, 1)
 // ---------------------------------------------------------------------------
 template <typename R>
-using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*);
+using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*, const int*,
+                         const int*);
 using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
@@ -257,7 +260,7 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
   const KernelSet& k = op->ks;
   const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
   k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x, y,
-                                                                    skip);
+                                                                    skip, nullptr, nullptr);
   LAUNCH_CHECK();
   return FEPA_OK;
 }
@@ -300,7 +303,7 @@ int launch_apply_nocount(fepa_op* op, const double* x, double* y, const int* ski
   const KernelSet& k = op->ks;
   const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
   k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x, y,
-                                                                    skip);
+                                                                    skip, nullptr, nullptr);
   BODY_CHECK();
   return FEPA_OK;
 }
@@ -748,7 +751,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   CREATE_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
   CREATE_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
   CREATE_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
-  build_gmap<<<grid_for(E * n * n * n, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, p, op->gmap);
+  build_gmap<<<grid_for(E * n * n * n, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, p, 0, op->gmap);
   g_launches.fetch_add(1);
   geom_qdata<<<grid_for(E * q3, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, q, op->verts, op->pts, op->wts,
                                                               form == FEPA_DIFFUSION, op->qd, op->flag);
@@ -1073,3 +1076,5 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
                 hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0);
   return FEPA_OK;
 }
+
+#include "batch_api.inc"

@@ -129,7 +129,7 @@ __global__ void qp_coords_kernel(int nx, int ny, int nz, int q, const double* __
 // ---------------------------------------------------------------------------
 // structured element -> DOF map and essential flags
 // ---------------------------------------------------------------------------
-__global__ void build_gmap(int nx, int ny, int nz, int p, int* __restrict__ gmap) {
+__global__ void build_gmap(int nx, int ny, int nz, int p, int dof_off, int* __restrict__ gmap) {
   const int n = p + 1, n3 = n * n * n;
   const int64_t Nx = (int64_t)p * nx + 1, Ny = (int64_t)p * ny + 1;
   const int64_t total = (int64_t)nx * ny * nz * n3;
@@ -138,7 +138,7 @@ __global__ void build_gmap(int nx, int ny, int nz, int p, int* __restrict__ gmap
     const int l = (int)(t - e * n3);
     const int a = l % n, b = (l / n) % n, c = l / (n * n);
     const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-    gmap[t] = (int)((p * ex + a) + Nx * ((p * ey + b) + Ny * (p * ez + c)));
+    gmap[t] = dof_off + (int)((p * ex + a) + Nx * ((p * ey + b) + Ny * (p * ez + c)));
   }
 }
 
@@ -189,7 +189,8 @@ struct PaShape {
 template <typename R, int P, int Q, bool DIFF>
 __global__ void __launch_bounds__(PaShape<R, P, Q, DIFF>::TPE * PaShape<R, P, Q, DIFF>::NE)
 pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R* __restrict__ Btab,
-         const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip) {
+         const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip,
+         const int* __restrict__ elem_prob, const int* __restrict__ prob_done) {
   using S = PaShape<R, P, Q, DIFF>;
   constexpr int n = S::N, T = S::TPE;
   if (skip && *skip) return;
@@ -202,7 +203,8 @@ pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R*
   R* S2 = S1 + S::NC1 * n * n * Q;
   const int tid = threadIdx.x;
   const int64_t e = (int64_t)blockIdx.x * S::NE + threadIdx.y;
-  const bool live = e < E;
+  // batched operators: elements of problems that have converged do nothing
+  const bool live = e < E && !(elem_prob && prob_done[elem_prob[e]]);
   const int* g = gmap + e * (n * n * n);
 
   for (int i = threadIdx.y * T + tid; i < Q * n; i += T * S::NE) {

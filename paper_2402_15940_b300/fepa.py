@@ -44,6 +44,15 @@ class RefineStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("max_iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dof_iterations", ctypes.c_double),
+                ("max_rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 CG_GRAPH, CG_STREAM = 0, 1
 
 SIGNATURES = [
@@ -78,6 +87,14 @@ SIGNATURES = [
     ("fepa_solve_refined", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
     ("fepa_solve_refined_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32,
                                                ctypes.POINTER(RefineStats)]),
+    ("fepa_batch_create", ctypes.c_int, [_I32, _P, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)]),
+    ("fepa_batch_destroy", None, [_P]),
+    ("fepa_batch_ndofs", _I64, [_P]),
+    ("fepa_batch_offsets", ctypes.c_int, [_P, _P]),
+    ("fepa_batch_groups", _I32, [_P]),
+    ("fepa_batch_set_stream", ctypes.c_int, [_P, _P]),
+    ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
     ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
 ]
 NOALLOC_MAX_DOFS = 131072
@@ -346,3 +363,70 @@ class Operator:
                                             _dev_ptr(x, torch.float64, self.N, "x"), int(iters),
                                             _PRECONDS[precond], ctypes.byref(st)))
         return st.as_dict()
+
+
+class Batch:
+    """Many independent problems solved together (block-diagonal batch operator).
+
+    problems: list of dicts with keys n=(nx, ny, nz), vertices (numpy), p, form."""
+
+    def __init__(self, problems, essential_boundary=True):
+        torch = _torch()
+        lib = load_library()
+        self._lib = lib
+        cnt = len(problems)
+        dims = np.ascontiguousarray([list(pr["n"]) for pr in problems], dtype=np.int32)
+        self._verts = [np.ascontiguousarray(pr["vertices"], dtype=np.float64) for pr in problems]
+        ptrs = (ctypes.c_void_p * cnt)(*[v.ctypes.data for v in self._verts])
+        orders = np.ascontiguousarray([pr["p"] for pr in problems], dtype=np.int32)
+        forms = np.ascontiguousarray([_FORMS[pr["form"]] for pr in problems], dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.fepa_batch_create(cnt, dims.ctypes.data_as(ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p),
+                                     orders.ctypes.data_as(ctypes.c_void_p), forms.ctypes.data_as(ctypes.c_void_p),
+                                     1 if essential_boundary else 0,
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.count = cnt
+        self.N = int(lib.fepa_batch_ndofs(h))
+        off = np.empty(cnt + 1, dtype=np.int64)
+        _check(lib.fepa_batch_offsets(h, off.ctypes.data_as(ctypes.c_void_p)))
+        self.offsets = off
+        self.groups = int(lib.fepa_batch_groups(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fepa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        torch = _torch()
+        _check(self._lib.fepa_batch_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def apply(self, x, out=None):
+        torch = _torch()
+        y = torch.empty(self.N, dtype=torch.float64, device="cuda") if out is None else out
+        self._sync_stream()
+        _check(self._lib.fepa_batch_apply(self._h, _dev_ptr(x, torch.float64, self.N, "x"),
+                                          _dev_ptr(y, torch.float64, self.N, "y")))
+        return y
+
+    def solve(self, b, x=None, rtol=1e-10, maxit=10000, precond="jacobi", raise_on_noconv=True):
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = BatchStats()
+        its = np.zeros(self.count, dtype=np.int32)
+        self._sync_stream()
+        rc = self._lib.fepa_batch_solve(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                        _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(maxit),
+                                        _PRECONDS[precond], ctypes.byref(st), its.ctypes.data_as(ctypes.c_void_p))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        d = st.as_dict()
+        d["iterations"] = its
+        return x, d
