@@ -433,6 +433,48 @@ def run_batch(args, rank, world, dist):
     return 0
 
 
+def run_serve(args, rank, world, dist):
+    """Served solve stream: for each arrival rate, `--requests` requests (mass or
+    diffusion, p uniform in 1..8, DOFs log-uniform in 1e3..5e6, FP64 or mixed with
+    refinement to 1e-10, seeded perturbed cubes, sine RHS) arrive as a Poisson process
+    and are served with continuous batching under an HBM budget."""
+    import torch
+
+    from paper_2402_15940_b300 import launch_count
+    from paper_2402_15940_b300.serve import GpuExecutor, Request, Server, poisson_arrivals
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    vf = lambda n, seed: FI.perturbed_cube_vertices(*n, seed=seed)  # noqa: E731
+    rates = [float(r) for r in args.rates.split(",")]
+    per_rate = []
+    l0 = launch_count()
+    with ClockSampler(local) as clk:
+        for k, rate in enumerate(rates):
+            spec = FI.serve_requests(args.requests, seed=100 * rank)   # same requests at every rate
+            reqs = [Request(rid=i, form=s["form"], p=s["p"], n=s["n"], mesh_seed=s["mesh_seed"],
+                            precision=s["precision"]) for i, s in enumerate(spec)]
+            poisson_arrivals(reqs, rate=rate, seed=k)
+            srv = Server(GpuExecutor(vf), hbm_budget=args.hbm_budget, tick_iters=args.tick_iters)
+            srv.run(reqs)
+            rep = srv.report()
+            rep["rate"] = rate
+            per_rate.append(rep)
+    if rank == 0:
+        top = max(per_rate, key=lambda r: r["solves_per_s"])
+        line = {"metric": "served solves/s, p50/p99 latency", "value": top["solves_per_s"], "unit": "solves/s",
+                "n_gpus": world, "steps": len(rates), "warmup": 0, "ms_per_step": 1e3 * top["makespan_s"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 | f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"{args.requests} requests per rate, Poisson arrivals, mass|diffusion, "
+                                       "p~U{1..8}, DOFs log-uniform 1e3..5e6, FP64 or mixed+refine (1/2 each) "
+                                       "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
+                           "tick_iters": args.tick_iters},
+                "per_rate": per_rate, "gpu_launches": launch_count() - l0, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,7 +493,11 @@ def main():
     ap.add_argument("--traffic-fp64", type=float, default=None, help="DRAM bytes per FP64 apply launch (ncu)")
     ap.add_argument("--traffic-fp32", type=float, default=None, help="DRAM bytes per FP32 apply launch (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bp3", "batch"], default="bp3")
+    ap.add_argument("--workload", choices=["bp3", "batch", "serve"], default="bp3")
+    ap.add_argument("--rates", default="10,100,1000,5000")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--hbm-budget", type=float, default=150e9)
+    ap.add_argument("--tick-iters", type=int, default=32)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -470,6 +516,8 @@ def main():
     try:
         if args.workload == "batch":
             return run_batch(args, rank, world, dist)
+        if args.workload == "serve":
+            return run_serve(args, rank, world, dist)
         return run_ours(args, rank, world, dist)
     finally:
         if dist is not None:

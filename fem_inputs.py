@@ -61,3 +61,21 @@ def problem_mix(count: int, seed: int = 0, p_range=(1, 6), n_range=(2, 24)) -> l
                     "mesh_seed": int(rng.integers(0, 2**31 - 1)),
                     "rhs_seed": int(rng.integers(0, 2**31 - 1))})
     return out
+
+
+def serve_requests(count: int, seed: int = 0, p_range=(1, 8), dofs_range=(1e3, 5e6), mixed_fraction: float = 0.5):
+    """A seeded stream of solve requests: form mass/diffusion with probability 1/2, order p
+    uniform in p_range, global DOF count log-uniform in dofs_range (a cube with
+    round((N^(1/3) - 1) / p) elements per direction, at least 1), precision 'mixed' with
+    probability mixed_fraction else 'fp64', and a mesh seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        form = "mass" if rng.uniform() < 0.5 else "diffusion"
+        p = int(rng.integers(p_range[0], p_range[1] + 1))
+        target = float(np.exp(rng.uniform(np.log(dofs_range[0]), np.log(dofs_range[1]))))
+        ne = max(1, int(round((target ** (1.0 / 3.0) - 1.0) / p)))
+        precision = "mixed" if rng.uniform() < mixed_fraction else "fp64"
+        out.append({"form": form, "p": p, "n": (ne, ne, ne), "precision": precision,
+                    "mesh_seed": int(rng.integers(0, 2**31 - 1))})
+    return out

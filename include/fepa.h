@@ -29,7 +29,8 @@
  *
  * Conventions:
  *   - Every int-returning call returns FEPA_OK (0) or a negative FEPA_ERR_* code and
- *     then fepa_last_error() holds a message (thread-local).  Nothing aborts or traps.
+ *     then fepa_last_error() holds a message (thread-local); fepa_solver_poll may also
+ *     return FEPA_BUSY (1).  Nothing aborts or traps.
  *   - "device" pointers are CUDA global-memory pointers of the op's device; "host"
  *     pointers are ordinary CPU memory.  The caller owns every buffer it passes in;
  *     the library owns the fepa_op handle and the device arrays inside it.
@@ -56,6 +57,8 @@ extern "C" {
 #define FEPA_ERR_NOCONV (-5)      /* CG reached maxit before the tolerance */
 #define FEPA_ERR_TIMEOUT (-6)     /* a kernel's bounded wait for staged data expired (no fault) */
 #define FEPA_ERR_UNSUPPORTED (-7) /* order / quadrature outside the compiled range */
+
+#define FEPA_BUSY 1               /* fepa_solver_poll: work still in flight */
 
 /* bilinear forms */
 #define FEPA_MASS 0       /* BP1: (u, v) */
@@ -250,6 +253,46 @@ int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int
 /* As fepa_solve_refined with HOST b and x (copies inside the call). */
 int fepa_solve_refined_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t max_outer,
                             double inner_rtol, int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats);
+
+/* ---------------------------------------------------------------------------
+ * Resumable solves, for schedulers that keep many problems resident and interleave
+ * their iterations (continuous batching): start a solve, enqueue bounded numbers of
+ * iterations on the op's stream, and poll for completion without blocking.  Each op
+ * runs at most one resumable solve at a time; b and x must stay valid until it ends.
+ * Results equal those of fepa_cg_solve / fepa_solve_refined on the same op.
+ * ------------------------------------------------------------------------- */
+#define FEPA_SOLVER_CG 0       /* FP64 (Jacobi-)PCG */
+#define FEPA_SOLVER_REFINED 1  /* FP64 iterative refinement around FP32 PCG */
+
+typedef struct fepa_solver_state {
+  int32_t done;              /* 1 once the solve has ended (x holds the result) */
+  int32_t status;            /* FEPA_OK or FEPA_ERR_NOCONV when done */
+  int32_t iterations;        /* CG iterations so far (inner FP32 ones for REFINED) */
+  int32_t outer_iterations;  /* corrections applied (REFINED) */
+  double rel_residual;       /* latest ||r|| / ||b|| (FP64 residual for REFINED) */
+} fepa_solver_state;
+
+/*
+ * Start a resumable solve on the op's stream (asynchronous).
+ *   kind        FEPA_SOLVER_CG or FEPA_SOLVER_REFINED
+ *   b, x        device, N doubles; x holds the initial guess and, once done, the solution
+ *   rtol        stopping rule (FP64 residual)
+ *   maxit       CG iteration limit (REFINED: per inner solve)
+ *   max_outer   REFINED: limit on corrections (ignored for CG)
+ *   inner_rtol  REFINED: inner relative tolerance in (0,1) (ignored for CG)
+ */
+int fepa_solver_start(fepa_op* op, int32_t kind, const double* b, double* x, double rtol, int32_t maxit,
+                      int32_t max_outer, double inner_rtol, int32_t precond);
+
+/* Enqueue up to `iterations` more CG iterations (asynchronous; no-op between phases). */
+int fepa_solver_advance(fepa_op* op, int32_t iterations);
+
+/*
+ * Check progress.  blocking = 0: returns FEPA_BUSY while the enqueued work is still in
+ * flight; otherwise fills *state, and for REFINED enqueues the next phase (correction
+ * and FP64 residual, or the next inner solve) when one has finished.
+ */
+int fepa_solver_poll(fepa_op* op, int32_t blocking, fepa_solver_state* state);
 
 /* ---------------------------------------------------------------------------
  * Batches of independent problems.  Each problem i is its own structured hex mesh,

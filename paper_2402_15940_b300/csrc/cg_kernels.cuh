@@ -23,8 +23,14 @@ struct CgState {
   int done;         // set when converged or maxit reached
   int converged;
   unsigned int ticket;
-  int pad;
+  int tick_limit;   // the graph loop pauses (without finishing) once iter reaches this
 };
+
+// Resumable solves: allow `k` more iterations before the graph loop pauses.
+__global__ void cg_set_tick(CgState* st, int k) {
+  const long long lim = (long long)st->iter + k;
+  st->tick_limit = lim > 0x7fffffff ? 0x7fffffff : (int)lim;
+}
 
 constexpr int RED_THREADS = 256;
 
@@ -115,6 +121,7 @@ cg_init(int64_t N, const double* __restrict__ b, double* __restrict__ r, double*
       st->converged = (tot[1] <= st->tol2) ? 1 : 0;
       st->done = st->converged;
       st->alpha = st->beta = 0.0;
+      st->tick_limit = 0x7fffffff;
       st->ticket = 0;
     }
   }
@@ -182,7 +189,8 @@ cg_direction(int64_t N, const double* __restrict__ r, double* __restrict__ d, do
              const double* __restrict__ inv_diag, const CgState* st, cudaGraphConditionalHandle cond,
              int use_cond) {
   const int done = st->done;
-  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
   if (done) return;
   const double beta = st->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -259,6 +267,7 @@ cg32_init(int64_t N, const float* __restrict__ b, float* __restrict__ x, float* 
       st->converged = (tot[1] <= st->tol2) ? 1 : 0;
       st->done = st->converged;
       st->alpha = st->beta = 0.0;
+      st->tick_limit = 0x7fffffff;
       st->ticket = 0;
     }
   }
@@ -323,7 +332,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, float* __restrict__ h,
                const float* __restrict__ inv_diag, const CgState* st, cudaGraphConditionalHandle cond, int use_cond) {
   const int done = st->done;
-  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
   if (done) return;
   const float beta = (float)st->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {

@@ -216,6 +216,14 @@ struct fepa_op {
   bool inv32_valid = false;
   CgState* st_host = nullptr;  // pinned
   int* st_host_flag = nullptr;  // pinned
+  // resumable solve (fepa_solver_*)
+  int sv_kind = -1, sv_phase = 0, sv_precond = 0, sv_outer = 0, sv_inner_total = 0, sv_maxit = 0, sv_max_outer = 0;
+  int sv_status = 0;
+  int sv_seen_iter = 0;  // iterations already counted in the launch counter
+  double sv_rtol = 0.0, sv_inner_rtol = 0.0, sv_rel = 0.0;
+  const double* sv_b = nullptr;
+  double* sv_x = nullptr;
+  cudaEvent_t sv_event = nullptr;
 };
 
 namespace {
@@ -240,6 +248,7 @@ void free_op(fepa_op* op) {
     if (p) cudaFree(p);
   if (op->st_host) cudaFreeHost(op->st_host);
   if (op->st_host_flag) cudaFreeHost(op->st_host_flag);
+  if (op->sv_event) cudaEventDestroy(op->sv_event);
   if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
   delete op;
 }
@@ -1078,3 +1087,4 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
 }
 
 #include "batch_api.inc"
+#include "solver_api.inc"

@@ -53,7 +53,17 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class SolverState(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 CG_GRAPH, CG_STREAM = 0, 1
+SOLVER_CG, SOLVER_REFINED = 0, 1
+BUSY = 1
 
 SIGNATURES = [
     ("fepa_version", ctypes.c_char_p, []),
@@ -87,6 +97,9 @@ SIGNATURES = [
     ("fepa_solve_refined", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
     ("fepa_solve_refined_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32,
                                                ctypes.POINTER(RefineStats)]),
+    ("fepa_solver_start", ctypes.c_int, [_P, _I32, _P, _P, _D, _I32, _I32, _D, _I32]),
+    ("fepa_solver_advance", ctypes.c_int, [_P, _I32]),
+    ("fepa_solver_poll", ctypes.c_int, [_P, _I32, ctypes.POINTER(SolverState)]),
     ("fepa_batch_create", ctypes.c_int, [_I32, _P, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)]),
     ("fepa_batch_destroy", None, [_P]),
     ("fepa_batch_ndofs", _I64, [_P]),
@@ -354,6 +367,28 @@ class Operator:
                                                  float(inner_rtol), int(inner_maxit), _PRECONDS[precond],
                                                  ctypes.byref(st)))
         return x, st.as_dict()
+
+    # -- resumable solve (continuous batching)
+    def solver_start(self, b, x, kind="cg", rtol=1e-10, maxit=20000, max_outer=50, inner_rtol=1e-4,
+                     precond="jacobi"):
+        torch = _torch()
+        self._sv_keep = (b, x)   # the buffers must outlive the solve
+        k = {"cg": SOLVER_CG, "refined": SOLVER_REFINED}.get(kind, kind)
+        _check(self._lib.fepa_solver_start(self._h, int(k), _dev_ptr(b, torch.float64, self.N, "b"),
+                                           _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(maxit),
+                                           int(max_outer), float(inner_rtol), _PRECONDS[precond]))
+
+    def solver_advance(self, iterations):
+        _check(self._lib.fepa_solver_advance(self._h, int(iterations)))
+
+    def solver_poll(self, blocking=False):
+        """None while work is in flight (non-blocking), else the state dict."""
+        st = SolverState()
+        rc = self._lib.fepa_solver_poll(self._h, 1 if blocking else 0, ctypes.byref(st))
+        if rc == BUSY:
+            return None
+        _check(rc)
+        return st.as_dict()
 
     def iterations(self, b, x, iters, precond="jacobi"):
         torch = _torch()

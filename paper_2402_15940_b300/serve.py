@@ -1,0 +1,241 @@
+"""Served solve stream with continuous batching.
+
+Requests (a mesh, order p, form, precision) arrive over time.  The scheduler keeps
+every admitted request resident on the device (its mesh, D factors and CG state, in a
+library op on a stream of its own), admits waiting requests in arrival order whenever
+the HBM budget allows, and on every tick advances each active request by a bounded
+number of CG iterations (fepa_solver_advance), so requests that arrive while others
+are running join at the next tick and their work overlaps on the device.  Finished
+requests leave at tick boundaries and release their memory.
+
+The scheduler is plain host logic; all device work goes through the C ABI of
+libfepa.so (GpuExecutor).  A FakeExecutor with the same interface drives the host
+logic in CPU tests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from collections import deque
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    form: str                 # "mass" | "diffusion"
+    p: int
+    n: tuple                  # elements per direction
+    mesh_seed: int
+    precision: str = "fp64"   # "fp64" | "mixed"
+    arrival: float = 0.0      # seconds after the start of the run
+    rtol: float = 1e-10
+
+    @property
+    def ndofs(self) -> int:
+        nx, ny, nz = self.n
+        return (self.p * nx + 1) * (self.p * ny + 1) * (self.p * nz + 1)
+
+    @property
+    def nelems(self) -> int:
+        nx, ny, nz = self.n
+        return nx * ny * nz
+
+
+def device_bytes(req: Request) -> int:
+    """Upper estimate of the device memory a resident request holds: vertices, element
+    map, FP64 D, FP32 D (mixed), the CG work vectors, right-hand side and solution."""
+    n, q, E, N = req.p + 1, req.p + 2, req.nelems, req.ndofs
+    ncomp = 6 if req.form == "diffusion" else 1
+    nv = (req.n[0] + 1) * (req.n[1] + 1) * (req.n[2] + 1)
+    by = 24 * nv + 4 * n ** 3 * E + 8 * ncomp * q ** 3 * E
+    by += 8 * N * 8                                   # b, x, r, d, h, 1/diag, copies
+    if req.precision == "mixed":
+        by += 4 * ncomp * (((q ** 3) + 3) & ~3) * E   # padded FP32 D
+        by += 4 * N * 6 + 8 * N                       # FP32 loop vectors, FP64 residual
+    return int(by * 1.05) + (1 << 20)
+
+
+@dataclasses.dataclass
+class Outcome:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    status: int
+    iterations: int
+    outer_iterations: int
+    rel_residual: float
+    ndofs: int
+    result: Optional[np.ndarray] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    """Continuous-batching scheduler over an executor (GpuExecutor or FakeExecutor)."""
+
+    def __init__(self, executor, hbm_budget: float = 150e9, tick_iters: int = 32, max_active: int = 256,
+                 keep_results: bool = False, clock: Callable[[], float] = time.perf_counter):
+        self.ex = executor
+        self.budget = float(hbm_budget)
+        self.tick_iters = int(tick_iters)
+        self.max_active = int(max_active)
+        self.keep_results = keep_results
+        self.clock = clock
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.pending: deque = deque()
+        self.active: dict = {}       # rid -> (request, handle, bytes, admitted)
+        self.done: list = []
+        self.rejected: list = []
+        self.ticks = 0
+        self.max_concurrent = 0
+
+    def _admit(self, now: float):
+        while self.pending and len(self.active) < self.max_active:
+            req = self.pending[0]
+            need = device_bytes(req)
+            if need > self.budget:             # can never fit: reject rather than block the queue
+                self.pending.popleft()
+                self.rejected.append(req.rid)
+                continue
+            if self.in_use + need > self.budget:
+                break                          # wait for memory to free up (arrival order kept)
+            self.pending.popleft()
+            handle = self.ex.start(req)
+            self.in_use += need
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            self.active[req.rid] = (req, handle, need, now)
+        self.max_concurrent = max(self.max_concurrent, len(self.active))
+
+    def _tick(self):
+        for rid, (req, h, need, adm) in self.active.items():
+            self.ex.advance(h, self.tick_iters)
+        self.ticks += 1
+        finished = []
+        for rid, (req, h, need, adm) in self.active.items():
+            st = self.ex.poll(h)
+            if st is not None and st["done"]:
+                finished.append(rid)
+                res = self.ex.result(h) if self.keep_results else None
+                self.done.append(Outcome(rid, req.arrival, adm, self.clock() - self.t0, st["status"],
+                                         st["iterations"], st["outer_iterations"], st["rel_residual"],
+                                         req.ndofs, res))
+        for rid in finished:
+            req, h, need, adm = self.active.pop(rid)
+            self.ex.release(h)
+            self.in_use -= need
+
+    def run(self, requests):
+        """Serve `requests` (arrival times relative to the start); returns the outcomes."""
+        arrivals = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        self.t0 = self.clock()
+        while arrivals or self.pending or self.active:
+            now = self.clock() - self.t0
+            while arrivals and arrivals[0].arrival <= now:
+                self.pending.append(arrivals.popleft())
+            self._admit(now)
+            if self.active:
+                self._tick()
+            elif arrivals and not self.pending:
+                wait = arrivals[0].arrival - (self.clock() - self.t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+        self.makespan = self.clock() - self.t0
+        return sorted(self.done, key=lambda o: o.rid)
+
+    def report(self):
+        lat = np.array([o.latency for o in self.done]) if self.done else np.zeros(1)
+        work = sum(o.ndofs * o.iterations for o in self.done)
+        return {"completed": len(self.done), "rejected": len(self.rejected), "makespan_s": self.makespan,
+                "solves_per_s": len(self.done) / self.makespan if self.makespan > 0 else 0.0,
+                "gdofs_per_cg_iter": work / self.makespan / 1e9 if self.makespan > 0 else 0.0,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "max_concurrent": self.max_concurrent, "peak_device_bytes": self.peak_in_use, "ticks": self.ticks}
+
+
+def poisson_arrivals(requests, rate: float, seed: int = 0):
+    """Assign Poisson arrival times (rate requests/s) in request order."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for r in requests:
+        t += rng.exponential(1.0 / rate)
+        r.arrival = t
+    return requests
+
+
+# ----------------------------------------------------------------------------- executors
+
+class GpuExecutor:
+    """Runs each request as a resident library op on its own CUDA stream."""
+
+    def __init__(self, vertices_fn, inner_rtol: float = 1e-4):
+        import torch
+        self.torch = torch
+        self.vertices_fn = vertices_fn      # (n, seed) -> vertex array
+        self.inner_rtol = inner_rtol
+
+    def start(self, req: Request):
+        from .fepa import Operator
+        torch = self.torch
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            op = Operator(*req.n, self.vertices_fn(req.n, req.mesh_seed), req.p, form=req.form)
+            if req.form == "diffusion":
+                op.set_essential(op.boundary_dofs())
+                b = op.rhs_sine(3 * math.pi ** 2)
+            else:
+                b = op.rhs_sine(1.0)
+            x = torch.zeros(op.N, dtype=torch.float64, device="cuda")
+            op.solver_start(b, x, kind="refined" if req.precision == "mixed" else "cg", rtol=req.rtol,
+                            inner_rtol=self.inner_rtol)
+        return {"op": op, "stream": stream, "b": b, "x": x}
+
+    def advance(self, h, iters: int):
+        with self.torch.cuda.stream(h["stream"]):
+            h["op"].solver_advance(iters)
+
+    def poll(self, h):
+        with self.torch.cuda.stream(h["stream"]):
+            return h["op"].solver_poll(blocking=False)
+
+    def result(self, h):
+        with self.torch.cuda.stream(h["stream"]):
+            return h["x"].cpu().numpy()
+
+    def release(self, h):
+        h["stream"].synchronize()
+        h["op"].close()
+        h.clear()
+
+
+class FakeExecutor:
+    """Host-only stand-in: a request needs `iters_fn(req)` iterations; every advance
+    performs up to the given number.  Used to test the scheduler without a GPU."""
+
+    def __init__(self, iters_fn):
+        self.iters_fn = iters_fn
+        self.log = []
+
+    def start(self, req):
+        self.log.append(("start", req.rid))
+        return {"req": req, "need": int(self.iters_fn(req)), "done": 0}
+
+    def advance(self, h, iters):
+        h["done"] = min(h["need"], h["done"] + iters)
+
+    def poll(self, h):
+        d = h["done"] >= h["need"]
+        return {"done": d, "status": 0, "iterations": h["done"], "outer_iterations": 0, "rel_residual": 0.0}
+
+    def result(self, h):
+        return None
+
+    def release(self, h):
+        self.log.append(("release", h["req"].rid))

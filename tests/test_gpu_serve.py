@@ -1,0 +1,100 @@
+"""GPU tests of resumable solves and of the continuous-batching server: every result
+is the same alone and in the mix (iteration counts within 1, solutions within 1e-9,
+the tolerance of the solver parity tests), and matches the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import fem_inputs as FI
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def F():
+    import paper_2402_15940_b300 as mod
+    return mod
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def make(n, p, form, seed):
+    op = F().Operator(*n, FI.perturbed_cube_vertices(*n, seed=seed), p, form=form)
+    if form == "diffusion":
+        op.set_essential(op.boundary_dofs())
+        b = op.rhs_sine(3 * math.pi ** 2)
+    else:
+        b = op.rhs_sine(1.0)
+    return op, b
+
+
+@pytest.mark.parametrize("kind", ["cg", "refined"])
+@pytest.mark.parametrize("step", [1, 7, 100000])
+def test_resumable_solve_equals_one_shot(kind, step):
+    op, b = make((4, 3, 4), 3, "diffusion", seed=2)
+    x1, s1 = (op.solve(b, rtol=1e-10) if kind == "cg" else op.solve_refined(b, rtol=1e-10))
+    x2 = torch.zeros_like(b)
+    op.solver_start(b, x2, kind=kind, rtol=1e-10)
+    st = None
+    for _ in range(100000):
+        op.solver_advance(step)
+        st = op.solver_poll(blocking=True)
+        if st["done"]:
+            break
+    assert st["done"] and st["status"] == 0 and st["rel_residual"] <= 1e-10
+    key = "iterations" if kind == "cg" else "inner_iterations"
+    assert abs(st["iterations"] - s1[key]) <= 1
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
+
+
+def test_nonblocking_poll_reports_busy_or_state():
+    op, b = make((6, 6, 6), 4, "diffusion", seed=3)
+    x = torch.zeros_like(b)
+    op.solver_start(b, x, kind="cg", rtol=1e-10)
+    seen_busy = False
+    for _ in range(1000000):
+        op.solver_advance(5)
+        st = op.solver_poll(blocking=False)
+        while st is None:
+            seen_busy = True
+            st = op.solver_poll(blocking=False)
+        if st["done"]:
+            break
+    assert st["done"] and st["status"] == 0
+    assert seen_busy or st["iterations"] > 0
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    from paper_2402_15940_b300.serve import GpuExecutor, Request, Server, poisson_arrivals
+    specs = [("diffusion", 2, (4, 4, 4), "fp64"), ("mass", 3, (3, 3, 3), "mixed"), ("diffusion", 4, (3, 3, 2), "mixed"),
+             ("diffusion", 1, (9, 8, 7), "fp64"), ("mass", 5, (2, 2, 2), "fp64"), ("diffusion", 6, (2, 2, 3), "mixed"),
+             ("diffusion", 3, (5, 5, 5), "fp64"), ("mass", 2, (6, 5, 4), "mixed")]
+    reqs = [Request(rid=i, form=f, p=p, n=n, mesh_seed=50 + i, precision=pr) for i, (f, p, n, pr) in enumerate(specs)]
+    poisson_arrivals(reqs, rate=500.0, seed=1)
+    vf = lambda n, seed: FI.perturbed_cube_vertices(*n, seed=seed)  # noqa: E731
+    srv = Server(GpuExecutor(vf), hbm_budget=2e9, tick_iters=4, keep_results=True)
+    out = srv.run(reqs)
+    assert len(out) == len(reqs) and all(o.status == 0 for o in out)
+    assert srv.max_concurrent >= 2
+    for o, r in zip(out, reqs):
+        op, b = make(r.n, r.p, r.form, r.mesh_seed)
+        if r.precision == "fp64":
+            xa, sa = op.solve(b, rtol=1e-10)
+            assert abs(sa["iterations"] - o.iterations) <= 1
+        else:
+            xa, sa = op.solve_refined(b, rtol=1e-10)
+            assert abs(sa["inner_iterations"] - o.iterations) <= 2
+        assert rel(o.result, xa.cpu().numpy()) <= 1e-9, r
+        # and the oracle's tight solution of the same problem
+        mesh = O.HexGridMesh(*r.n, FI.perturbed_cube_vertices(*r.n, seed=r.mesh_seed))
+        prob = O.Problem(mesh, r.p, None, r.form, assemble=r.p <= 5)
+        xo, _, _ = prob.solve(prob.sine_rhs(), rtol=1e-13)
+        assert rel(o.result, xo) <= 1e-8
+    rep = srv.report()
+    assert rep["completed"] == len(reqs) and rep["p99_latency_s"] >= rep["p50_latency_s"] > 0

@@ -1,0 +1,91 @@
+"""Host logic of the continuous-batching scheduler, with a fake executor and clock."""
+import numpy as np
+import pytest
+
+import fem_inputs as FI
+from paper_2402_15940_b300.serve import FakeExecutor, Request, Server, device_bytes, poisson_arrivals
+
+
+class FakeClock:
+    def __init__(self, dt=1.0):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def reqs(specs):
+    return [Request(rid=i, form=f, p=p, n=(n, n, n), mesh_seed=i, arrival=a) for i, (f, p, n, a) in enumerate(specs)]
+
+
+def test_device_bytes_grows_with_size_and_precision():
+    a = Request(0, "diffusion", 4, (8, 8, 8), 0)
+    b = Request(1, "diffusion", 4, (16, 16, 16), 0)
+    c = Request(2, "diffusion", 4, (16, 16, 16), 0, precision="mixed")
+    m = Request(3, "mass", 4, (16, 16, 16), 0)
+    assert device_bytes(a) < device_bytes(b) < device_bytes(c)
+    assert device_bytes(m) < device_bytes(b)
+    # FP64 D alone for p=4 diffusion: 48 q^3 bytes per element
+    assert device_bytes(b) > 48 * 216 * 16 ** 3
+
+
+def test_all_complete_and_budget_respected():
+    rs = reqs([("diffusion", (i % 6) + 1, 4 + i % 5, 0.0) for i in range(40)])
+    budget = 3 * max(device_bytes(r) for r in rs)
+    srv = Server(FakeExecutor(lambda r: 10 + 7 * r.rid), hbm_budget=budget, tick_iters=8, clock=FakeClock())
+    out = srv.run(rs)
+    assert [o.rid for o in out] == list(range(40))
+    assert all(o.iterations == 10 + 7 * o.rid for o in out)
+    assert srv.peak_in_use <= budget and srv.in_use == 0
+    assert srv.max_concurrent >= 2
+
+
+def test_late_short_request_overtakes_long_one():
+    # a long request is running when a short one arrives: the short one is admitted at the
+    # next tick boundary and finishes first (continuous batching, not a queue)
+    rs = reqs([("diffusion", 2, 4, 0.0), ("mass", 2, 4, 5.0)])
+    need = {0: 1000, 1: 16}
+    srv = Server(FakeExecutor(lambda r: need[r.rid]), hbm_budget=1e12, tick_iters=8, clock=FakeClock())
+    out = {o.rid: o for o in srv.run(rs)}
+    assert out[1].admitted < out[0].finished
+    assert out[1].finished < out[0].finished
+    assert srv.max_concurrent == 2
+
+
+def test_fifo_admission_under_memory_pressure():
+    rs = reqs([("diffusion", 3, 10, 0.0), ("diffusion", 3, 10, 0.0), ("mass", 1, 2, 0.0), ("diffusion", 3, 10, 0.0)])
+    budget = device_bytes(rs[0]) * 1.5   # one big request at a time
+    ex = FakeExecutor(lambda r: 20)
+    srv = Server(ex, hbm_budget=budget, tick_iters=4, clock=FakeClock())
+    srv.run(rs)
+    starts = [rid for kind, rid in ex.log if kind == "start"]
+    assert starts == [0, 1, 2, 3]          # the small one does not jump the queue
+    assert srv.peak_in_use <= budget
+
+
+def test_oversize_request_rejected_not_blocking():
+    rs = reqs([("diffusion", 8, 60, 0.0), ("mass", 1, 2, 0.0)])
+    srv = Server(FakeExecutor(lambda r: 5), hbm_budget=device_bytes(rs[1]) * 4, clock=FakeClock())
+    out = srv.run(rs)
+    assert srv.rejected == [0] and [o.rid for o in out] == [1]
+
+
+def test_report_percentiles_and_poisson_arrivals():
+    rs = reqs([("mass", 1, 2, 0.0) for _ in range(200)])
+    poisson_arrivals(rs, rate=50.0, seed=3)
+    gaps = np.diff([0.0] + [r.arrival for r in rs])
+    assert abs(gaps.mean() - 1 / 50.0) < 0.2 / 50.0
+    srv = Server(FakeExecutor(lambda r: 3), hbm_budget=1e12, tick_iters=1, clock=FakeClock(dt=0.001))
+    srv.run(rs)
+    rep = srv.report()
+    assert rep["completed"] == 200 and rep["p50_latency_s"] <= rep["p99_latency_s"]
+
+
+def test_serve_request_generator():
+    r = FI.serve_requests(500, seed=1)
+    assert {x["form"] for x in r} == {"mass", "diffusion"}
+    assert min(x["p"] for x in r) == 1 and max(x["p"] for x in r) == 8
+    n = np.array([(x["p"] * x["n"][0] + 1) ** 3 for x in r])
+    assert n.min() >= 8 and n.max() < 1.5e7
+    assert 0.35 < np.mean([x["precision"] == "mixed" for x in r]) < 0.65
