@@ -20,6 +20,7 @@ __all__ = [
     "perturbed_cube_vertices",
     "uniform_vector",
     "problem_mix",
+    "serve_requests",
 ]
 
 
