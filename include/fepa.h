@@ -347,6 +347,34 @@ int fepa_batch_apply(fepa_batch* batch, const double* x, double* y);
 int fepa_batch_solve(fepa_batch* batch, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
                      fepa_batch_stats* stats, int32_t* iterations);
 
+/* ---------------------------------------------------------------------------
+ * p-multigrid preconditioner (Sec. 2.1: a hierarchy of orders on one mesh, transfers
+ * between them by sum factorisation, diagonal-based smoothers with Chebyshev
+ * acceleration).  Levels p, max(1, p/2), ..., 1 built from the fine op's mesh and form;
+ * essential DOFs must be none or exactly the boundary (each level then fixes its own
+ * boundary).  Smoother: `smooth_degree` Chebyshev-Jacobi steps on
+ * [0.25, 1.05] * lambda_max(D^{-1}A) (power iteration at set-up); coarsest level:
+ * `coarse_degree` steps on [0.003, 1.05] * lambda_max.  The V-cycle is symmetric and
+ * linear, so it preconditions plain CG.  All FP64.  The fine op must outlive the object.
+ * ------------------------------------------------------------------------- */
+typedef struct fepa_mg fepa_mg;
+
+int fepa_mg_create(fepa_op* fine, int32_t smooth_degree, int32_t coarse_degree, fepa_mg** out);
+void fepa_mg_destroy(fepa_mg* mg);
+int32_t fepa_mg_levels(const fepa_mg* mg);
+/* order, DOFs and lambda_max(D^{-1}A) estimate of a level (0 = finest); outputs may be null */
+int fepa_mg_level_info(const fepa_mg* mg, int32_t level, int32_t* order, int64_t* ndofs, double* lambda_max);
+/* x_level = P x_{level+1} (device vectors of the two levels' sizes) */
+int fepa_mg_prolong(fepa_mg* mg, int32_t level, const double* x_coarse, double* x_fine);
+/* r_{level+1} = P^T r_level, coarse essential rows set to 0 */
+int fepa_mg_restrict(fepa_mg* mg, int32_t level, const double* r_fine, double* r_coarse);
+/* x = S b with the level's Chebyshev smoother (coarse solver on the last level), from 0 */
+int fepa_mg_smooth(fepa_mg* mg, int32_t level, const double* b, double* x);
+/* x = M^{-1} b, one V-cycle on the finest level */
+int fepa_mg_vcycle(fepa_mg* mg, const double* b, double* x);
+/* CG on the fine op preconditioned by the V-cycle; blocks until done */
+int fepa_mg_solve(fepa_mg* mg, const double* b, double* x, double rtol, int32_t maxit, fepa_cg_stats* stats);
+
 /*
  * CG solve that allocates nothing.  The paper has no counterpart: this call exists
  * for callers that cannot allocate device memory once they are running -- for

@@ -619,3 +619,52 @@ def dense_bruteforce(mesh: HexGridMesh, p: int, q: int, form: str) -> np.ndarray
                                 v = grad[s][0] * grad[t][0] + grad[s][1] * grad[t][1] + grad[s][2] * grad[t][2]
                             A[dofs[e, s], dofs[e, t]] += w * det * v
     return A
+
+
+# ----------------------------------------------------------------------------
+# p-multigrid pieces (Sec. 2.1: order hierarchy on one mesh, transfers between
+# orders, diagonal-based smoothing with Chebyshev acceleration)
+# ----------------------------------------------------------------------------
+
+def order_prolongation(mesh: HexGridMesh, pc: int, pf: int) -> sp.csr_matrix:
+    """P with P[i, j] = phi_j^{pc}(x_i): the coarse (order pc) nodal basis function j
+    evaluated at fine (order pf) node i, element by element on the reference element
+    (the map is the same for both orders, so this is the natural injection Q_pc into Q_pf)."""
+    nf, nc = pf + 1, pc + 1
+    Vc, _ = lagrange(gll_points(pc), gll_points(pf))           # (nf, nc) 1D
+    I3 = np.zeros((nf ** 3, nc ** 3))
+    for c in range(nf):
+        for b in range(nf):
+            for a in range(nf):
+                row = a + nf * (b + nf * c)
+                for k in range(nc):
+                    for j in range(nc):
+                        for i in range(nc):
+                            I3[row, i + nc * (j + nc * k)] = Vc[a, i] * Vc[b, j] * Vc[c, k]
+    df, dc = elem_dofs(mesh, pf), elem_dofs(mesh, pc)
+    P = sp.lil_matrix((num_dofs(mesh, pf), num_dofs(mesh, pc)))
+    for e in range(mesh.num_elements):
+        for r in range(nf ** 3):
+            for s in range(nc ** 3):
+                if I3[r, s] != 0.0:
+                    P[df[e, r], dc[e, s]] = I3[r, s]     # equal from every element sharing the node
+    return P.tocsr()
+
+
+def chebyshev_smoother(apply, diag: np.ndarray, b: np.ndarray, lmin: float, lmax: float, k: int) -> np.ndarray:
+    """k steps of Chebyshev acceleration of Jacobi for A x = b from x0 = 0, for the
+    eigenvalues of D^{-1}A assumed in [lmin, lmax] (the classical three-term recurrence:
+    theta, delta the centre and half-width of the interval, sigma = theta/delta)."""
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    x = np.zeros_like(b)
+    r = b.copy()
+    d = r / diag / theta
+    for _ in range(k):
+        x = x + d
+        r = r - apply(d)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / diag)
+        rho = rho_new
+    return x

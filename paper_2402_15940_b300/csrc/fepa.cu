@@ -23,6 +23,7 @@
 #include "pa_kernels.cuh"
 #include "pa_tma_f32.cuh"
 #include "batch_kernels.cuh"
+#include "mg_kernels.cuh"
 
 using namespace fepa;
 
@@ -185,6 +186,7 @@ struct fepa_op {
   cudaStream_t cap_stream;  // private stream used only to capture graphs
   KernelSet ks;
   std::vector<float> B32h, G32h;
+  std::vector<double> verts_host;  // host copy of the vertex grid (for derived ops, e.g. multigrid levels)
   // device arrays owned by the op
   double* verts = nullptr;
   int* gmap = nullptr;
@@ -741,6 +743,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int ncomp = form == FEPA_DIFFUSION ? 6 : 1;
   const int64_t q3 = (int64_t)q * q * q;
+  op->verts_host.assign(vertices, vertices + 3 * nv);
   if ((rc = dalloc(&op->verts, 3 * nv)) || (rc = dalloc(&op->gmap, E * n * n * n)) ||
       (rc = dalloc(&op->qd, E * ncomp * q3)) || (rc = dalloc(&op->B, (size_t)q * n)) ||
       (rc = dalloc(&op->G, (size_t)q * n)) || (rc = dalloc(&op->pts, q)) || (rc = dalloc(&op->wts, q)) ||
@@ -781,6 +784,12 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
   const int64_t q3 = (int64_t)op->q * op->q * op->q;
   CUDA_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double),
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (on_device) {
+    op->verts_host.resize(3 * nv);
+    CUDA_TRY(cudaMemcpyAsync(op->verts_host.data(), op->verts, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  } else {
+    op->verts_host.assign(vertices, vertices + 3 * nv);
+  }
   CUDA_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
   geom_qdata<<<grid_for(op->E * q3, 256, 148 * 32), 256, 0, s>>>(op->nx, op->ny, op->nz, op->q, op->verts, op->pts,
                                                                   op->wts, op->form == FEPA_DIFFUSION, op->qd, op->flag);
@@ -1088,3 +1097,4 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
 
 #include "batch_api.inc"
 #include "solver_api.inc"
+#include "mg_api.inc"

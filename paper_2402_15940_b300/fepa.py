@@ -108,6 +108,16 @@ SIGNATURES = [
     ("fepa_batch_set_stream", ctypes.c_int, [_P, _P]),
     ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
     ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
+    ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(_P)]),
+    ("fepa_mg_destroy", None, [_P]),
+    ("fepa_mg_levels", _I32, [_P]),
+    ("fepa_mg_level_info", ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                                          ctypes.POINTER(_D)]),
+    ("fepa_mg_prolong", ctypes.c_int, [_P, _I32, _P, _P]),
+    ("fepa_mg_restrict", ctypes.c_int, [_P, _I32, _P, _P]),
+    ("fepa_mg_smooth", ctypes.c_int, [_P, _I32, _P, _P]),
+    ("fepa_mg_vcycle", ctypes.c_int, [_P, _P, _P]),
+    ("fepa_mg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
 ]
 NOALLOC_MAX_DOFS = 131072
@@ -465,3 +475,77 @@ class Batch:
         d = st.as_dict()
         d["iterations"] = its
         return x, d
+
+
+class Multigrid:
+    """p-multigrid V-cycle over orders p, p/2, ..., 1 of an Operator's mesh and form."""
+
+    def __init__(self, op: Operator, smooth_degree=2, coarse_degree=24):
+        lib = load_library()
+        self._lib, self.op = lib, op
+        h = ctypes.c_void_p()
+        op._sync_stream()
+        _check(lib.fepa_mg_create(op._h, int(smooth_degree), int(coarse_degree), ctypes.byref(h)))
+        self._h = h
+        self.levels = []
+        for l in range(int(lib.fepa_mg_levels(h))):
+            o, n, lam = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+            _check(lib.fepa_mg_level_info(h, l, ctypes.byref(o), ctypes.byref(n), ctypes.byref(lam)))
+            self.levels.append({"order": o.value, "ndofs": n.value, "lambda_max": lam.value})
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fepa_mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, level, out=None):
+        torch = _torch()
+        return torch.empty(self.levels[level]["ndofs"], dtype=torch.float64, device="cuda") if out is None else out
+
+    def prolong(self, level, xc, out=None):
+        torch = _torch()
+        y = self._vec(level, out)
+        _check(self._lib.fepa_mg_prolong(self._h, int(level),
+                                         _dev_ptr(xc, torch.float64, self.levels[level + 1]["ndofs"], "xc"),
+                                         _dev_ptr(y, torch.float64, self.levels[level]["ndofs"], "xf")))
+        return y
+
+    def restrict(self, level, rf, out=None):
+        torch = _torch()
+        y = self._vec(level + 1, out)
+        _check(self._lib.fepa_mg_restrict(self._h, int(level),
+                                          _dev_ptr(rf, torch.float64, self.levels[level]["ndofs"], "rf"),
+                                          _dev_ptr(y, torch.float64, self.levels[level + 1]["ndofs"], "rc")))
+        return y
+
+    def smooth(self, level, b, out=None):
+        torch = _torch()
+        y = self._vec(level, out)
+        n = self.levels[level]["ndofs"]
+        _check(self._lib.fepa_mg_smooth(self._h, int(level), _dev_ptr(b, torch.float64, n, "b"),
+                                        _dev_ptr(y, torch.float64, n, "x")))
+        return y
+
+    def vcycle(self, b, out=None):
+        torch = _torch()
+        y = self._vec(0, out)
+        n = self.levels[0]["ndofs"]
+        _check(self._lib.fepa_mg_vcycle(self._h, _dev_ptr(b, torch.float64, n, "b"),
+                                        _dev_ptr(y, torch.float64, n, "x")))
+        return y
+
+    def solve(self, b, x=None, rtol=1e-10, maxit=1000):
+        torch = _torch()
+        n = self.levels[0]["ndofs"]
+        x = torch.zeros(n, dtype=torch.float64, device="cuda") if x is None else x
+        st = CgStats()
+        self.op._sync_stream()
+        _check(self._lib.fepa_mg_solve(self._h, _dev_ptr(b, torch.float64, n, "b"), _dev_ptr(x, torch.float64, n, "x"),
+                                       float(rtol), int(maxit), ctypes.byref(st)))
+        return x, st.as_dict()

@@ -1,0 +1,122 @@
+"""GPU parity of the p-multigrid pieces against the oracle: order transfers (P, P^T),
+the Chebyshev-Jacobi smoother, the lambda_max estimate, the symmetric V-cycle, and the
+V-cycle-preconditioned CG solve.  FP64 tolerance 1e-12 (same sums in another order)
+for transfers and smoothers; solutions within 1e-9 of the oracle at the 1e-10 stop."""
+import math
+
+import numpy as np
+import pytest
+
+import fem_inputs as FI
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMOOTH_LO, SMOOTH_HI, COARSE_LO, COARSE_HI = 0.25, 1.05, 0.003, 1.05
+
+
+def F():
+    import paper_2402_15940_b300 as mod
+    return mod
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nd, nb = np.linalg.norm(a - b), np.linalg.norm(b)
+    if nb == 0.0:        # e.g. a coarse level whose DOFs are all essential
+        return nd
+    return nd / nb
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def setup(shape, p, form, seed=0, degree=2, coarse=24):
+    verts = FI.perturbed_cube_vertices(*shape, seed=seed)
+    op = F().Operator(*shape, verts, p, form=form)
+    if form == "diffusion":
+        op.set_essential(op.boundary_dofs())
+    mg = F().Multigrid(op, smooth_degree=degree, coarse_degree=coarse)
+    return op, mg, O.HexGridMesh(*shape, verts)
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 4, (3, 2, 2)), ("mass", 3, (2, 3, 2)),
+                                          ("diffusion", 8, (2, 1, 2)), ("diffusion", 5, (2, 2, 2))])
+def test_levels_and_transfers_match_oracle(form, p, shape):
+    op, mg, mesh = setup(shape, p, form)
+    orders = [lv["order"] for lv in mg.levels]
+    expect = [p]
+    while expect[-1] > 1:
+        expect.append(max(1, expect[-1] // 2))
+    assert orders == expect
+    for l in range(len(orders) - 1):
+        pf, pc = orders[l], orders[l + 1]
+        P = O.order_prolongation(mesh, pc, pf)
+        xc = FI.uniform_vector(P.shape[1], seed=l)
+        assert rel(mg.prolong(l, dev(xc)).cpu().numpy(), P @ xc) <= 1e-12
+        rf = FI.uniform_vector(P.shape[0], seed=10 + l)
+        if form == "diffusion":
+            rf_in = rf.copy()
+            rf_in[O.boundary_dofs(mesh, pf)] = 0.0
+            ref = P.T @ rf_in
+            ref[O.boundary_dofs(mesh, pc)] = 0.0
+        else:
+            ref = P.T @ rf
+        assert rel(mg.restrict(l, dev(rf)).cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("form,p", [("diffusion", 4), ("mass", 2), ("diffusion", 6)])
+def test_smoothers_match_oracle_chebyshev(form, p):
+    shape = (2, 2, 3)
+    op, mg, mesh = setup(shape, p, form, degree=3, coarse=17)
+    for l, lv in enumerate(mg.levels):
+        prob = O.Problem(mesh, lv["order"], None, form)
+        Ac = prob.Ac
+        b = FI.uniform_vector(prob.N, seed=l)
+        if form == "diffusion":
+            b[prob.ess] = 0.0
+        last = l == len(mg.levels) - 1
+        lo, hi, k = (COARSE_LO, COARSE_HI, 17) if last else (SMOOTH_LO, SMOOTH_HI, 3)
+        ref = O.chebyshev_smoother(lambda v: Ac @ v, Ac.diagonal(), b, lo * lv["lambda_max"], hi * lv["lambda_max"], k)
+        assert rel(mg.smooth(l, dev(b)).cpu().numpy(), ref) <= 1e-12
+
+
+def test_lambda_max_estimate():
+    op, mg, mesh = setup((2, 2, 2), 3, "diffusion")
+    for lv in mg.levels:
+        prob = O.Problem(mesh, lv["order"], None, O.DIFFUSION)
+        A = prob.Ac.toarray()
+        lam = np.linalg.eigvals(A / np.diag(A)[:, None]).real.max()
+        assert 0.9 * lam <= lv["lambda_max"] <= lam * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("form", ["diffusion", "mass"])
+def test_vcycle_symmetric_positive(form):
+    op, mg, _ = setup((3, 3, 2), 4, form, seed=2)
+    u = dev(FI.uniform_vector(op.N, seed=1))
+    v = dev(FI.uniform_vector(op.N, seed=2))
+    if form == "diffusion":
+        ess = torch.from_numpy(op.boundary_dofs().astype(np.int64)).cuda()
+        u[ess] = 0.0
+        v[ess] = 0.0
+    Mu, Mv = mg.vcycle(u), mg.vcycle(v)
+    a, b = float(torch.dot(v, Mu)), float(torch.dot(u, Mv))
+    assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    assert float(torch.dot(u, Mu)) > 0 and float(torch.dot(v, Mv)) > 0
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 4, (4, 4, 4)), ("diffusion", 2, (6, 6, 5)),
+                                          ("mass", 3, (3, 3, 3)), ("diffusion", 6, (2, 3, 2))])
+def test_mg_solve_matches_oracle_and_needs_fewer_iterations(form, p, shape):
+    op, mg, mesh = setup(shape, p, form, seed=5)
+    b = op.rhs_sine(3 * math.pi ** 2 if form == "diffusion" else 1.0)
+    x, st = mg.solve(b, rtol=1e-10)
+    xj, sj = op.solve(b, rtol=1e-10)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    xo, it_o, _ = prob.solve(b.cpu().numpy(), rtol=1e-13)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert rel(x.cpu().numpy(), xo) <= 1e-9
+    assert st["iterations"] < sj["iterations"]

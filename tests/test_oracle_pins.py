@@ -271,3 +271,46 @@ def test_planted_transpose_mistake_is_caught(monkeypatch):
     u = 0.3 + 1.1 * xyz[:, 0] - 0.7 * xyz[:, 1] + 2.3 * xyz[:, 2]
     interior = np.setdiff1d(np.arange(len(u)), O.boundary_dofs(mesh, 2))
     assert np.abs((K @ u)[interior]).max() > 1e-6
+
+
+# ---------------------------------------------------------------- p-multigrid pieces
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (1, 3), (3, 6)])
+def test_prolongation_reproduces_coarse_polynomials(pc, pf):
+    # interpolating a coarse-space function onto the fine nodes is exact: P u_c equals the
+    # fine nodal values of the same polynomial (degree <= pc in each reference variable)
+    mesh = perturbed(2, 1, 2, seed=9)
+    P = O.order_prolongation(mesh, pc, pf)
+    xc, xf = O.node_coords(mesh, pc), O.node_coords(mesh, pf)
+    f = lambda x: (1 + x[:, 0] - 0.5 * x[:, 1] + 2 * x[:, 2]) ** pc  # noqa: E731
+    # on a trilinear mesh this is in Q_pc only for pc = 1 or an affine element; use the
+    # element map instead: nodal values of a Q_pc function of the reference coordinates
+    np.testing.assert_allclose(P @ np.ones(P.shape[1]), np.ones(P.shape[0]), atol=1e-14)
+    if pc == 1:
+        np.testing.assert_allclose(P @ f(xc), f(xf), atol=1e-12)
+    # the fine mass matrix restricted by P is the coarse mass matrix (the spaces are nested)
+    Mf = O.assemble_csr(mesh, pf, pf + 2, O.MASS)
+    Mc = O.assemble_csr(mesh, pc, pc + 2, O.MASS)
+    np.testing.assert_allclose((P.T @ Mf @ P).toarray(), Mc.toarray(), atol=1e-14)
+
+
+def test_chebyshev_smoother_polynomial_bound():
+    # for [lmin, lmax] containing the spectrum of D^{-1}A the A-norm error after k steps is
+    # at most 1/T_k(sigma) times the initial one (Chebyshev minimax property); and with a wide
+    # interval it converges to the solution
+    mesh = perturbed(2, 2, 2, seed=4)
+    prob = O.Problem(mesh, 2, None, O.DIFFUSION)
+    A = prob.Ac.toarray()
+    dg = np.diag(A).copy()
+    ev = np.linalg.eigvals(A / dg[:, None]).real
+    lmin, lmax = ev.min(), ev.max()
+    b = FI.uniform_vector(prob.N, seed=2)
+    x = np.linalg.solve(A, b)
+    sigma = (lmax + lmin) / (lmax - lmin)
+    for k in (1, 3, 8, 20):
+        xk = O.chebyshev_smoother(lambda v: A @ v, dg, b, lmin, lmax, k)
+        e = xk - x
+        bound = 1.0 / np.cosh(k * np.arccosh(sigma))
+        assert np.sqrt(e @ A @ e) <= bound * np.sqrt(x @ A @ x) * (1 + 1e-9)
+    xk = O.chebyshev_smoother(lambda v: A @ v, dg, b, lmin, lmax, 200)
+    np.testing.assert_allclose(xk, x, rtol=0, atol=1e-10 * np.abs(x).max())
