@@ -353,26 +353,36 @@ int fepa_batch_solve(fepa_batch* batch, const double* b, double* x, double rtol,
  * acceleration).  Levels p, max(1, p/2), ..., 1 built from the fine op's mesh and form;
  * essential DOFs must be none or exactly the boundary (each level then fixes its own
  * boundary).  Smoother: `smooth_degree` Chebyshev-Jacobi steps on
- * [0.25, 1.05] * lambda_max(D^{-1}A) (power iteration at set-up); coarsest level:
- * `coarse_degree` steps on [0.003, 1.05] * lambda_max.  The V-cycle is symmetric and
- * linear, so it preconditions plain CG.  All FP64.  The fine op must outlive the object.
+ * [0.25, 1.1] * lambda_max(D^{-1}A) (power iteration at set-up); coarsest level:
+ * `coarse_degree` steps on [0.003, 1.2] * lambda_max.  The V-cycle is symmetric and
+ * linear, so it preconditions plain CG.  precision: FEPA_MG_FP64, or FEPA_MG_FP32 for an
+ * FP32 V-cycle (FP32 operators, smoothers and transfers on every level) inside the FP64
+ * CG (whose operator action, dot products and scalars stay FP64).  The fine op must
+ * outlive the object.
  * ------------------------------------------------------------------------- */
 typedef struct fepa_mg fepa_mg;
+#define FEPA_MG_FP64 0
+#define FEPA_MG_FP32 1
 
-int fepa_mg_create(fepa_op* fine, int32_t smooth_degree, int32_t coarse_degree, fepa_mg** out);
+int fepa_mg_create(fepa_op* fine, int32_t smooth_degree, int32_t coarse_degree, int32_t precision, fepa_mg** out);
+/* After fepa_op_set_vertices on the fine op: move every level's mesh and rebuild its
+ * diagonal and lambda_max (no allocation). */
+int fepa_mg_update(fepa_mg* mg);
 void fepa_mg_destroy(fepa_mg* mg);
 int32_t fepa_mg_levels(const fepa_mg* mg);
 /* order, DOFs and lambda_max(D^{-1}A) estimate of a level (0 = finest); outputs may be null */
 int fepa_mg_level_info(const fepa_mg* mg, int32_t level, int32_t* order, int64_t* ndofs, double* lambda_max);
-/* x_level = P x_{level+1} (device vectors of the two levels' sizes) */
+/* x_level = P x_{level+1} (device vectors of the two levels' sizes); FP64 V-cycle only */
 int fepa_mg_prolong(fepa_mg* mg, int32_t level, const double* x_coarse, double* x_fine);
-/* r_{level+1} = P^T r_level, coarse essential rows set to 0 */
+/* r_{level+1} = P^T r_level, coarse essential rows set to 0; FP64 V-cycle only */
 int fepa_mg_restrict(fepa_mg* mg, int32_t level, const double* r_fine, double* r_coarse);
-/* x = S b with the level's Chebyshev smoother (coarse solver on the last level), from 0 */
+/* x = S b with the level's Chebyshev smoother (coarse solver on the last level), from 0;
+ * FP64 V-cycle only */
 int fepa_mg_smooth(fepa_mg* mg, int32_t level, const double* b, double* x);
-/* x = M^{-1} b, one V-cycle on the finest level */
+/* x = M^{-1} b, one V-cycle on the finest level (FP64 b, x in either precision mode) */
 int fepa_mg_vcycle(fepa_mg* mg, const double* b, double* x);
-/* CG on the fine op preconditioned by the V-cycle; blocks until done */
+/* CG on the fine op preconditioned by the V-cycle (flexible Polak-Ribiere beta, equal to
+ * the standard one for an exact fixed preconditioner); blocks until done */
 int fepa_mg_solve(fepa_mg* mg, const double* b, double* x, double rtol, int32_t maxit, fepa_cg_stats* stats);
 
 /*

@@ -668,3 +668,25 @@ def chebyshev_smoother(apply, diag: np.ndarray, b: np.ndarray, lmin: float, lmax
         d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / diag)
         rho = rho_new
     return x
+
+
+def pmg_vcycle(As, diags, Ps, lmax, degree, coarse_degree, b, smooth=(0.25, 1.1), coarse=(0.003, 1.2), ess=None):
+    """One symmetric V-cycle over levels 0 (finest) .. L (coarsest): Chebyshev-Jacobi
+    pre-smoothing from 0, residual, restriction by P^T (essential rows of the coarser level
+    set to 0), recursion, prolongation by P, residual, post-smoothing, correction; the
+    coarsest level applies a higher-degree Chebyshev polynomial.  As[l] are the (constrained)
+    level matrices, Ps[l] maps level l+1 to level l, ess[l] the essential rows of level l."""
+    def rec(l, rhs):
+        A = As[l]
+        app = lambda v: A @ v  # noqa: E731
+        if l == len(As) - 1:
+            return chebyshev_smoother(app, diags[l], rhs, coarse[0] * lmax[l], coarse[1] * lmax[l], coarse_degree)
+        x = chebyshev_smoother(app, diags[l], rhs, smooth[0] * lmax[l], smooth[1] * lmax[l], degree)
+        r = rhs - A @ x
+        rc = Ps[l].T @ (r if ess is None or ess[l] is None else np.where(np.isin(np.arange(len(r)), ess[l]), 0.0, r))
+        if ess is not None and ess[l + 1] is not None:
+            rc[ess[l + 1]] = 0.0
+        x = x + Ps[l] @ rec(l + 1, rc)
+        r = rhs - A @ x
+        return x + chebyshev_smoother(app, diags[l], r, smooth[0] * lmax[l], smooth[1] * lmax[l], degree)
+    return rec(0, np.asarray(b, dtype=np.float64))

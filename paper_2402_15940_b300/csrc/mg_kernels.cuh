@@ -16,37 +16,38 @@ constexpr int MG_MAXN = FEPA_MAX_ORDER + 1;
 // xf = P xc: interpolate coarse nodal values to the fine nodes of every element;
 // I[a][i] = coarse basis i at fine node a (nf x nc).  Shared fine nodes get the same
 // value from every element that holds them (plain stores).  One element per block.
+template <typename T>
 __global__ void mg_prolong(int E, int nf, int nc, const int* __restrict__ gf, const int* __restrict__ gc,
-                           const double* __restrict__ I, const double* __restrict__ xc, double* __restrict__ xf) {
-  __shared__ double sI[MG_MAXN * MG_MAXN];
-  __shared__ double s0[MG_MAXN * MG_MAXN * MG_MAXN];
-  __shared__ double s1[MG_MAXN * MG_MAXN * MG_MAXN];
+                           const T* __restrict__ I, const T* __restrict__ xc, T* __restrict__ xf) {
+  __shared__ T sI[MG_MAXN * MG_MAXN];
+  __shared__ T s0[MG_MAXN * MG_MAXN * MG_MAXN];
+  __shared__ T s1[MG_MAXN * MG_MAXN * MG_MAXN];
   const int64_t e = blockIdx.x;
-  const int t = threadIdx.x, T = blockDim.x;
+  const int t = threadIdx.x, NT = blockDim.x;
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
-  for (int k = t; k < nf * nc; k += T) sI[k] = I[k];
-  for (int k = t; k < nc3; k += T) s0[k] = xc[gmap_dof(gc[e * nc3 + k])];
+  for (int k = t; k < nf * nc; k += NT) sI[k] = I[k];
+  for (int k = t; k < nc3; k += NT) s0[k] = xc[gmap_dof(gc[e * nc3 + k])];
   __syncthreads();
   // x: [c][b][a'] over coarse c, b
-  for (int w = t; w < nf * nc * nc; w += T) {
+  for (int w = t; w < nf * nc * nc; w += NT) {
     const int a = w % nf, cb = w / nf;
-    double s = 0.0;
+    T s = T(0);
     for (int i = 0; i < nc; ++i) s += sI[a * nc + i] * s0[cb * nc + i];
     s1[w] = s;
   }
   __syncthreads();
   // y: [c][b'][a']
-  for (int w = t; w < nf * nf * nc; w += T) {
+  for (int w = t; w < nf * nf * nc; w += NT) {
     const int a = w % nf, b = (w / nf) % nf, c = w / (nf * nf);
-    double s = 0.0;
+    T s = T(0);
     for (int j = 0; j < nc; ++j) s += sI[b * nc + j] * s1[(c * nc + j) * nf + a];
     s0[w] = s;
   }
   __syncthreads();
   // z: [c'][b'][a'] -> fine DOFs
-  for (int w = t; w < nf3; w += T) {
+  for (int w = t; w < nf3; w += NT) {
     const int ab = w % (nf * nf), c = w / (nf * nf);
-    double s = 0.0;
+    T s = T(0);
     for (int k = 0; k < nc; ++k) s += sI[c * nc + k] * s0[k * nf * nf + ab];
     xf[gmap_dof(gf[e * nf3 + w])] = s;
   }
@@ -55,48 +56,50 @@ __global__ void mg_prolong(int E, int nf, int nc, const int* __restrict__ gf, co
 // rc += P^T rf: every fine DOF counted once (its value divided by the number of elements
 // holding it), transposed interpolation, scatter-add to the coarse DOFs.  Fine essential
 // entries are read as 0.
+template <typename T>
 __global__ void mg_restrict(int E, int nf, int nc, const int* __restrict__ gf, const int* __restrict__ gc,
-                            const double* __restrict__ I, const double* __restrict__ inv_mult,
-                            const double* __restrict__ rf, double* __restrict__ rc) {
-  __shared__ double sI[MG_MAXN * MG_MAXN];
-  __shared__ double s0[MG_MAXN * MG_MAXN * MG_MAXN];
-  __shared__ double s1[MG_MAXN * MG_MAXN * MG_MAXN];
+                            const T* __restrict__ I, const T* __restrict__ inv_mult, const T* __restrict__ rf,
+                            T* __restrict__ rc) {
+  __shared__ T sI[MG_MAXN * MG_MAXN];
+  __shared__ T s0[MG_MAXN * MG_MAXN * MG_MAXN];
+  __shared__ T s1[MG_MAXN * MG_MAXN * MG_MAXN];
   const int64_t e = blockIdx.x;
-  const int t = threadIdx.x, T = blockDim.x;
+  const int t = threadIdx.x, NT = blockDim.x;
   const int nc3 = nc * nc * nc, nf3 = nf * nf * nf;
-  for (int k = t; k < nf * nc; k += T) sI[k] = I[k];
-  for (int k = t; k < nf3; k += T) {
+  for (int k = t; k < nf * nc; k += NT) sI[k] = I[k];
+  for (int k = t; k < nf3; k += NT) {
     const int g = gf[e * nf3 + k];
-    s0[k] = g >= 0 ? rf[g] * inv_mult[g] : 0.0;
+    s0[k] = g >= 0 ? rf[g] * inv_mult[g] : T(0);
   }
   __syncthreads();
   // z^T: [k][b'][a'] = sum_c' I[c'][k] s0[c'][b'][a']
-  for (int w = t; w < nc * nf * nf; w += T) {
+  for (int w = t; w < nc * nf * nf; w += NT) {
     const int ab = w % (nf * nf), k = w / (nf * nf);
-    double s = 0.0;
+    T s = T(0);
     for (int c = 0; c < nf; ++c) s += sI[c * nc + k] * s0[c * nf * nf + ab];
     s1[w] = s;
   }
   __syncthreads();
   // y^T: [k][j][a'] = sum_b' I[b'][j] s1[k][b'][a']
-  for (int w = t; w < nc * nc * nf; w += T) {
+  for (int w = t; w < nc * nc * nf; w += NT) {
     const int a = w % nf, j = (w / nf) % nc, k = w / (nf * nc);
-    double s = 0.0;
+    T s = T(0);
     for (int b = 0; b < nf; ++b) s += sI[b * nc + j] * s1[(k * nf + b) * nf + a];
     s0[w] = s;
   }
   __syncthreads();
   // x^T: [k][j][i] = sum_a' I[a'][i] s0[k][j][a'] -> coarse DOFs
-  for (int w = t; w < nc3; w += T) {
+  for (int w = t; w < nc3; w += NT) {
     const int i = w % nc, kj = w / nc;
-    double s = 0.0;
+    T s = T(0);
     for (int a = 0; a < nf; ++a) s += sI[a * nc + i] * s0[kj * nf + a];
     atomicAdd(rc + gmap_dof(gc[e * nc3 + w]), s);
   }
 }
 
 // 1 / (number of elements holding each DOF) on a structured node grid
-__global__ void mg_inv_multiplicity(int nx, int ny, int nz, int p, double* __restrict__ out) {
+template <typename T>
+__global__ void mg_inv_multiplicity(int nx, int ny, int nz, int p, T* __restrict__ out) {
   const int64_t Nx = (int64_t)p * nx + 1, Ny = (int64_t)p * ny + 1, Nz = (int64_t)p * nz + 1;
   const int64_t total = Nx * Ny * Nz;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -105,67 +108,85 @@ __global__ void mg_inv_multiplicity(int nx, int ny, int nz, int p, double* __res
     int m = 1;
     for (int d = 0; d < 3; ++d)
       if (g[d] % p == 0 && g[d] > 0 && g[d] < lim[d]) m *= 2;
-    out[t] = 1.0 / m;
+    out[t] = T(1) / T(m);
   }
 }
 
 // Chebyshev-accelerated Jacobi, from x = 0: start x = 0, r = b, d = D^{-1} b / theta, h = 0
-__global__ void cheb_start(int64_t N, const double* __restrict__ b, const double* __restrict__ invd, double inv_theta,
-                           double* __restrict__ x, double* __restrict__ r, double* __restrict__ d,
-                           double* __restrict__ h) {
+template <typename T>
+__global__ void cheb_start(int64_t N, const T* __restrict__ b, const T* __restrict__ invd, T inv_theta,
+                           T* __restrict__ x, T* __restrict__ r, T* __restrict__ d, T* __restrict__ h) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double bi = b[i];
-    x[i] = 0.0;
+    const T bi = b[i];
+    x[i] = T(0);
     r[i] = bi;
     d[i] = inv_theta * invd[i] * bi;
-    h[i] = 0.0;
+    h[i] = T(0);
   }
 }
 
 // one step after h = A d: x += d; r -= h; d = c1 d + c2 D^{-1} r; h = 0
-__global__ void cheb_step(int64_t N, double c1, double c2, const double* __restrict__ invd, double* __restrict__ x,
-                          double* __restrict__ r, double* __restrict__ d, double* __restrict__ h) {
+template <typename T>
+__global__ void cheb_step(int64_t N, T c1, T c2, const T* __restrict__ invd, T* __restrict__ x, T* __restrict__ r,
+                          T* __restrict__ d, T* __restrict__ h) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double di = d[i];
+    const T di = d[i];
     x[i] += di;
-    const double ri = r[i] - h[i];
+    const T ri = r[i] - h[i];
     r[i] = ri;
     d[i] = c1 * di + c2 * invd[i] * ri;
-    h[i] = 0.0;
+    h[i] = T(0);
   }
 }
 
+// v[rows] = 0 (essential rows of a coarse level)
+template <typename T>
+__global__ void zero_rows(int64_t count, const int* __restrict__ rows, T* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    v[rows[i]] = T(0);
+}
+
 // y = a*x + y, and r = b - h (helpers of the V-cycle)
-__global__ void axpy(int64_t N, double a, const double* __restrict__ x, double* __restrict__ y) {
+template <typename T>
+__global__ void axpy(int64_t N, T a, const T* __restrict__ x, T* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
 }
 
-__global__ void sub_to(int64_t N, const double* __restrict__ b, const double* __restrict__ h, double* __restrict__ r) {
+template <typename T>
+__global__ void sub_to(int64_t N, const T* __restrict__ b, const T* __restrict__ h, T* __restrict__ r) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     r[i] = b[i] - h[i];
 }
 
+// out = in converted (FP64 <-> FP32 at the boundary of an FP32 V-cycle)
+template <typename A, typename B>
+__global__ void convert(int64_t N, const A* __restrict__ in, B* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
 // deterministic pseudo-random start vector for the power iteration (splitmix64 of the index)
-__global__ void hash_fill(int64_t N, double* __restrict__ v) {
+template <typename T>
+__global__ void hash_fill(int64_t N, T* __restrict__ v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5;
+    v[i] = (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5);
   }
 }
 
 // out[0] += (a, b), out[1] += (a, D a) with D = 1/w (w may be null: (a, a)): power iteration
+template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
-dot2(int64_t N, const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ w,
-     double* __restrict__ out) {
+dot2(int64_t N, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ w, double* __restrict__ out) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ai = a[i];
-    v[0] += ai * b[i];
-    v[1] += w ? ai * ai / w[i] : ai * ai;   // w = 1/diag: (a, D a)
+    const double ai = (double)a[i];
+    v[0] += ai * (double)b[i];
+    v[1] += w ? ai * ai / (double)w[i] : ai * ai;   // w = 1/diag: (a, D a)
   }
   double blk[2];
   block_sum<2>(v, blk);
@@ -176,8 +197,8 @@ dot2(int64_t N, const double* __restrict__ a, const double* __restrict__ b, cons
 }
 
 // v = s * D^{-1} h
-__global__ void scaled_jacobi(int64_t N, double s, const double* __restrict__ invd, const double* __restrict__ h,
-                              double* __restrict__ v) {
+template <typename T>
+__global__ void scaled_jacobi(int64_t N, T s, const T* __restrict__ invd, const T* __restrict__ h, T* __restrict__ v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = s * invd[i] * h[i];
 }
@@ -185,15 +206,16 @@ __global__ void scaled_jacobi(int64_t N, double s, const double* __restrict__ in
 // ---------------------------------------------------------------------------
 // CG preconditioned by a V-cycle: scalars on the device as in cg_kernels.cuh
 // ---------------------------------------------------------------------------
-// r = b - h; rr = (r,r), bb = (b,b); h = 0
+// r = b - h; rr = (r,r), bb = (b,b); h = 0; d = 0
 __global__ void __launch_bounds__(RED_THREADS)
-pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ h, CgState* st,
-          double rtol2, int maxit, double* partials) {
+pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ h,
+          double* __restrict__ d, CgState* st, double rtol2, int maxit, double* partials) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = b[i], ri = bi - h[i];
     r[i] = ri;
     h[i] = 0.0;
+    d[i] = 0.0;
     v[0] += ri * ri;
     v[1] += bi * bi;
   }
@@ -218,19 +240,26 @@ pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, doubl
   }
 }
 
-// rho_new = (z, r); first: d = z and beta = 0, else beta = rho_new / rho; d = z + beta d
+// rho_new = (z, r) and beta in the flexible (Polak-Ribiere) form
+//   beta = (z_new, r_new - r_old) / rho_old = -alpha (z_new, h) / rho_old,  h = A d_old,
+// which equals rho_new / rho_old for a fixed symmetric preconditioner and stays robust
+// when the preconditioner is applied in lower precision; beta = 0 on the first step.
 __global__ void __launch_bounds__(RED_THREADS)
-pcg_rho(int64_t N, const double* __restrict__ z, const double* __restrict__ r, CgState* st, double* partials) {
-  double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    v[0] += z[i] * r[i];
-  double blk[1];
-  block_sum<1>(v, blk);
-  if (publish_partials<1>(blk, partials, &st->ticket)) {
-    double tot[1];
-    final_sums<1>(partials, tot);
+pcg_rho(int64_t N, const double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ h,
+        CgState* st, double* partials) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    v[0] += zi * r[i];
+    v[1] += zi * h[i];
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
     if (threadIdx.x == 0) {
-      st->beta = st->iter == 0 ? 0.0 : tot[0] / st->rho;
+      st->beta = st->iter == 0 ? 0.0 : -st->alpha * tot[1] / st->rho;
       st->rho = tot[0];
       st->ticket = 0;
     }
@@ -241,7 +270,7 @@ __global__ void pcg_direction(int64_t N, const double* __restrict__ z, double* _
                               const CgState* st) {
   const double beta = st->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    d[i] = z[i] + beta * d[i];
+    d[i] = beta == 0.0 ? z[i] : z[i] + beta * d[i];
     h[i] = 0.0;
   }
 }

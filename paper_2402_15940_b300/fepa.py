@@ -108,7 +108,8 @@ SIGNATURES = [
     ("fepa_batch_set_stream", ctypes.c_int, [_P, _P]),
     ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
     ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
-    ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(_P)]),
+    ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    ("fepa_mg_update", ctypes.c_int, [_P]),
     ("fepa_mg_destroy", None, [_P]),
     ("fepa_mg_levels", _I32, [_P]),
     ("fepa_mg_level_info", ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I64),
@@ -480,18 +481,31 @@ class Batch:
 class Multigrid:
     """p-multigrid V-cycle over orders p, p/2, ..., 1 of an Operator's mesh and form."""
 
-    def __init__(self, op: Operator, smooth_degree=2, coarse_degree=24):
+    def __init__(self, op: Operator, smooth_degree=2, coarse_degree=24, precision="fp64"):
         lib = load_library()
         self._lib, self.op = lib, op
         h = ctypes.c_void_p()
         op._sync_stream()
-        _check(lib.fepa_mg_create(op._h, int(smooth_degree), int(coarse_degree), ctypes.byref(h)))
+        self.precision = precision
+        _check(lib.fepa_mg_create(op._h, int(smooth_degree), int(coarse_degree),
+                                  {"fp64": 0, "fp32": 1}[precision], ctypes.byref(h)))
         self._h = h
+        self._info()
+
+    def _info(self):
+        lib, h = self._lib, self._h
         self.levels = []
         for l in range(int(lib.fepa_mg_levels(h))):
             o, n, lam = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
             _check(lib.fepa_mg_level_info(h, l, ctypes.byref(o), ctypes.byref(n), ctypes.byref(lam)))
             self.levels.append({"order": o.value, "ndofs": n.value, "lambda_max": lam.value})
+
+    def update(self):
+        """Follow the fine op after set_vertices: move every level's mesh, rebuild diagonals
+        and eigenvalue bounds."""
+        self.op._sync_stream()
+        _check(self._lib.fepa_mg_update(self._h))
+        self._info()
 
     def close(self):
         if getattr(self, "_h", None):

@@ -13,7 +13,7 @@ import oracle as O
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SMOOTH_LO, SMOOTH_HI, COARSE_LO, COARSE_HI = 0.25, 1.05, 0.003, 1.05
+SMOOTH_LO, SMOOTH_HI, COARSE_LO, COARSE_HI = 0.25, 1.1, 0.003, 1.2
 
 
 def F():
@@ -120,3 +120,69 @@ def test_mg_solve_matches_oracle_and_needs_fewer_iterations(form, p, shape):
     assert st["status"] == 0 and st["rel_residual"] <= 1e-10
     assert rel(x.cpu().numpy(), xo) <= 1e-9
     assert st["iterations"] < sj["iterations"]
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 4, (4, 4, 4)), ("diffusion", 8, (2, 2, 2)),
+                                          ("mass", 2, (5, 4, 4))])
+def test_fp32_vcycle_solve_matches_oracle(form, p, shape):
+    """FP32 V-cycle inside the FP64 CG: the preconditioner is FP32, the operator action,
+    dot products and scalars FP64, so the solution meets the FP64 tolerance."""
+    verts = FI.perturbed_cube_vertices(*shape, seed=6)
+    op = F().Operator(*shape, verts, p, form=form)
+    if form == "diffusion":
+        op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    mg64 = F().Multigrid(op, precision="fp64")
+    x64, s64 = mg64.solve(b, rtol=1e-10)
+    mg32 = F().Multigrid(op, precision="fp32")
+    x32, s32 = mg32.solve(b, rtol=1e-10)
+    prob = O.Problem(O.HexGridMesh(*shape, verts), p, None, form, assemble=p <= 5)
+    xo, _, _ = prob.solve(b.cpu().numpy(), rtol=1e-13)
+    assert s32["status"] == 0 and s32["rel_residual"] <= 1e-10
+    assert rel(x32.cpu().numpy(), xo) <= 1e-9
+    assert s32["iterations"] <= s64["iterations"] + 2
+    for a, c in zip(mg32.levels, mg64.levels):
+        assert abs(a["lambda_max"] / c["lambda_max"] - 1) < 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_update_follows_moved_mesh(precision):
+    shape, p = (3, 3, 3), 4
+    op = F().Operator(*shape, FI.perturbed_cube_vertices(*shape, seed=1), p, form="diffusion")
+    op.set_essential(op.boundary_dofs())
+    mg = F().Multigrid(op, precision=precision)
+    verts2 = FI.perturbed_cube_vertices(*shape, seed=2)
+    op.set_vertices(verts2)
+    mg.update()
+    b = op.rhs_sine(1.0)
+    x1, s1 = mg.solve(b, rtol=1e-10)
+    op2 = F().Operator(*shape, verts2, p, form="diffusion")
+    op2.set_essential(op2.boundary_dofs())
+    mg2 = F().Multigrid(op2, precision=precision)
+    x2, s2 = mg2.solve(op2.rhs_sine(1.0), rtol=1e-10)
+    assert abs(s1["iterations"] - s2["iterations"]) <= 1   # atomic summation order may move the stop
+    assert rel(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-9
+    tol = 1e-9 if precision == "fp64" else 1e-5   # FP32 atomics reorder the power iteration's sums
+    for a, c in zip(mg.levels, mg2.levels):
+        assert abs(a["lambda_max"] / c["lambda_max"] - 1) < tol
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 4, (3, 3, 3)), ("mass", 4, (2, 3, 2)),
+                                          ("diffusion", 6, (2, 2, 3))])
+def test_vcycle_matches_oracle_and_is_deterministic(form, p, shape):
+    """The GPU V-cycle equals the oracle's V-cycle built from the level matrices and
+    prolongations with the same eigenvalue bounds, and repeated cycles agree."""
+    op, mg, mesh = setup(shape, p, form, seed=3)
+    orders = [lv["order"] for lv in mg.levels]
+    probs = [O.Problem(mesh, o, None, form) for o in orders]
+    As = [pr.Ac for pr in probs]
+    Ps = [O.order_prolongation(mesh, orders[l + 1], orders[l]) for l in range(len(orders) - 1)]
+    ess = [pr.ess if form == "diffusion" else None for pr in probs]
+    b = FI.uniform_vector(op.N, seed=9)
+    if form == "diffusion":
+        b[probs[0].ess] = 0.0
+    ref = O.pmg_vcycle(As, [A.diagonal() for A in As], Ps, [lv["lambda_max"] for lv in mg.levels], 2, 24, b, ess=ess)
+    z1 = mg.vcycle(dev(b)).cpu().numpy()
+    z2 = mg.vcycle(dev(b)).cpu().numpy()
+    assert rel(z1, ref) <= 1e-11
+    assert rel(z1, z2) <= 1e-13

@@ -314,3 +314,23 @@ def test_chebyshev_smoother_polynomial_bound():
         assert np.sqrt(e @ A @ e) <= bound * np.sqrt(x @ A @ x) * (1 + 1e-9)
     xk = O.chebyshev_smoother(lambda v: A @ v, dg, b, lmin, lmax, 200)
     np.testing.assert_allclose(xk, x, rtol=0, atol=1e-10 * np.abs(x).max())
+
+
+def test_pmg_vcycle_two_levels_reduces_error_and_is_symmetric():
+    # a symmetric V-cycle is a symmetric operator and, with a convergent smoother and an
+    # accurate coarse solve, a good preconditioner: kappa(M A) far below kappa(D^{-1} A)
+    mesh = perturbed(3, 3, 3, seed=8)
+    pf, pc = 4, 2
+    prf, prc = O.Problem(mesh, pf, None, O.DIFFUSION), O.Problem(mesh, pc, None, O.DIFFUSION)
+    As = [prf.Ac, prc.Ac]
+    P = O.order_prolongation(mesh, pc, pf)
+    lam = [np.linalg.eigvals(A.toarray() / A.diagonal()[:, None]).real.max() for A in As]
+    M = np.stack([O.pmg_vcycle(As, [A.diagonal() for A in As], [P], lam, 2, 40, e, ess=[prf.ess, prc.ess])
+                  for e in np.eye(prf.N)], axis=1)
+    interior = np.setdiff1d(np.arange(prf.N), prf.ess)
+    Mi = M[np.ix_(interior, interior)]
+    np.testing.assert_allclose(Mi, Mi.T, atol=1e-10 * np.abs(Mi).max())
+    Ai = As[0].toarray()[np.ix_(interior, interior)]
+    ev = np.sort(np.linalg.eigvals(Mi @ Ai).real)
+    evj = np.sort(np.linalg.eigvals(Ai / np.diag(Ai)[:, None]).real)
+    assert ev[0] > 0 and ev[-1] / ev[0] < 0.1 * evj[-1] / evj[0]
