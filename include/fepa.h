@@ -195,6 +195,22 @@ int fepa_op_set_f32_variant(fepa_op* op, int32_t variant);
 int32_t fepa_op_f32_variant(const fepa_op* op);          /* -1 until chosen */
 const char* fepa_f32_variant_name(int32_t variant);
 
+/*
+ * Arithmetic of the FP64 action (fepa_op_apply and every FP64 solve on this op).
+ * Variants: 0 = native FP64 (DFMA), 1 = double-float: each value is split into two
+ * floats (hi + lo) as it is read, every contraction step is an accurate dot-product
+ * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative
+ * error), and the element result is recombined in FP64 -- same inputs, outputs and
+ * memory traffic, error far inside the FP64 action's tolerance.  This library's own
+ * design for a GPU whose FP64 rate is a small fraction of its FP32 rate; the paper's
+ * FP64 kernels have no counterpart.  By default (-1) the first FP64 use times both on
+ * this op's mesh and keeps the faster; cached per device and (p, q, form).  The
+ * allocation-free solve never times: it uses the chosen or forced variant, else 0.
+ */
+int fepa_op_set_f64_variant(fepa_op* op, int32_t variant);
+int32_t fepa_op_f64_variant(const fepa_op* op);          /* -1 until chosen */
+const char* fepa_f64_variant_name(int32_t variant);
+
 /* diag(A) (of the constrained operator: 1 on essential rows), computed without
  * assembling A by sum factorisation (Sec. 2.1).  diag: device, N doubles. */
 int fepa_op_diagonal(fepa_op* op, double* diag);

@@ -23,6 +23,7 @@
 #include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
 #include "pa_tma_f32.cuh"
+#include "pa_df64.cuh"
 #include "batch_kernels.cuh"
 #include "mg_kernels.cuh"
 
@@ -89,6 +90,8 @@ using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*
 using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
+constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
+using ApplyDfFn = void (*)(int, const int*, const double*, const double*, double*, const int*);
 
 struct Apply32Variant {
   Apply32Fn fn;
@@ -98,6 +101,8 @@ struct Apply32Variant {
 
 struct KernelSet {
   ApplyFn<double> apply;
+  ApplyDfFn apply_df;
+  int df_smem, df_ne;
   Apply32Variant v32[N32_VARIANTS];
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   void (*rhs)(int, int, const double*, const int*, const double*, const double*, const double*, const double*,
@@ -111,6 +116,9 @@ template <int P, int Q, bool DIFF>
 KernelSet make_set() {
   KernelSet k;
   k.apply = pa_apply<double, P, Q, DIFF>;
+  k.apply_df = pa_apply_df<P, Q, DIFF>;
+  k.df_smem = DfShape<P, Q, DIFF>::SMEM;
+  k.df_ne = DfShape<P, Q, DIFF>::NE;
   k.v32[0] = {pa_apply_f32_tma<P, Q, DIFF, true, 1>, TmaShape<P, Q, DIFF, true, 1>::SMEM,
               TmaShape<P, Q, DIFF, true, 1>::NE, TmaShape<P, Q, DIFF, true, 1>::NE, false};
   k.v32[1] = {pa_apply_f32_tma<P, Q, DIFF, false, 1>, TmaShape<P, Q, DIFF, false, 1>::SMEM,
@@ -173,7 +181,7 @@ struct CgLoop {
   int red_blocks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int graph_precond = -1;
+  int graph_key = -1;  // preconditioner and kernel variants the cached graph was captured with
 };
 
 }  // namespace
@@ -205,6 +213,8 @@ struct fepa_op {
   int v32 = -1;        // FP32 kernel variant in use (-1: not chosen yet)
   int v32_grid[4] = {0, 0, 0, 0};  // launch grid per variant (persistent: SMs x resident blocks)
   int v32_forced = -1; // variant set by the caller (-1: autotune)
+  int v64 = -1;        // FP64 action variant in use (-1: not chosen yet)
+  int v64_forced = -1; // variant set by the caller (-1: autotune)
   int* err = nullptr;  // device word set by kernels whose bounded waits expired
   // CG workspace (allocated on first solve)
   double* inv_diag = nullptr;
@@ -267,13 +277,37 @@ int dalloc(T** p, size_t count) {
   return FEPA_OK;
 }
 
+// y += A x in FP64 with variant v (launch only; not counted)
+int launch_apply64_variant(fepa_op* op, int v, const double* x, double* y, const int* skip, cudaStream_t s) {
+  const KernelSet& k = op->ks;
+  if (v == 1) {
+    const int grid = (int)((op->E + k.df_ne - 1) / k.df_ne);
+    k.apply_df<<<grid, dim3(k.apply_tpe, k.df_ne), k.df_smem, s>>>((int)op->E, op->gmap, op->qd, x, y, skip);
+  } else {
+    const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
+    k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x,
+                                                                      y, skip, nullptr, nullptr);
+  }
+  BODY_CHECK();
+  return FEPA_OK;
+}
+
+int ensure_v64(fepa_op* op);
+
+// y += A x in FP64 without choosing a variant (no timing, no allocation): the chosen or
+// forced variant, else the DFMA kernel (counted)
+int launch_apply_untuned(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
+  const int v = op->v64 >= 0 ? op->v64 : (op->v64_forced >= 0 ? op->v64_forced : 0);
+  TRY(launch_apply64_variant(op, v, x, y, skip, s));
+  g_launches.fetch_add(1);
+  return FEPA_OK;
+}
+
 // y += A x in FP64 (launch only; counted)
 int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
-  const KernelSet& k = op->ks;
-  const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
-  k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x, y,
-                                                                    skip, nullptr, nullptr);
-  LAUNCH_CHECK();
+  TRY(ensure_v64(op));
+  TRY(launch_apply64_variant(op, op->v64, x, y, skip, s));
+  g_launches.fetch_add(1);
   return FEPA_OK;
 }
 
@@ -311,13 +345,9 @@ int launch_apply32_nocount(fepa_op* op, const float* x, float* y, const int* ski
   return launch_apply32_variant(op, op->v32, x, y, skip, s);
 }
 
+// (the variant is chosen before any capture: ensure_v64 runs in run_loop)
 int launch_apply_nocount(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
-  const KernelSet& k = op->ks;
-  const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
-  k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x, y,
-                                                                    skip, nullptr, nullptr);
-  BODY_CHECK();
-  return FEPA_OK;
+  return launch_apply64_variant(op, op->v64 < 0 ? 0 : op->v64, x, y, skip, s);
 }
 
 int ensure_host_state(fepa_op* op) {
@@ -375,7 +405,18 @@ int ensure_inv_diag(fepa_op* op) {
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mutex;
 int g_tuned[64][FEPA_MAX_ORDER + 1][2][2];
+int g_tuned64[64][FEPA_MAX_ORDER + 1][2][2];
 bool g_tuned_init = false;
+
+void init_tuned() {
+  if (g_tuned_init) return;
+  for (auto* t : {&g_tuned, &g_tuned64})
+    for (auto& a : *t)
+      for (auto& b : a)
+        for (auto& c : b)
+          for (int& d : c) d = -1;
+  g_tuned_init = true;
+}
 
 int time_variants32(fepa_op* op, int* best) {
   cudaStream_t s = op->stream;
@@ -423,13 +464,7 @@ int choose_variant32(fepa_op* op) {
   }
   const int dev = op->device < 64 ? op->device : 63;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  if (!g_tuned_init) {
-    for (auto& a : g_tuned)
-      for (auto& b : a)
-        for (auto& c : b)
-          for (int& d : c) d = -1;
-    g_tuned_init = true;
-  }
+  init_tuned();
   int& slot = g_tuned[dev][op->p][op->q - op->p - 1][op->form];
   if (slot < 0) {
     int best = 0;
@@ -437,6 +472,66 @@ int choose_variant32(fepa_op* op) {
     slot = best;
   }
   op->v32 = slot;
+  return FEPA_OK;
+}
+
+// Time the FP64 action variants on this op (2 warm-up + 5 timed launches each).
+int time_variants64(fepa_op* op, int* best) {
+  cudaStream_t s = op->stream;
+  double *x = nullptr, *y = nullptr;
+  TRY(dalloc(&x, op->N));
+  int rc = dalloc(&y, op->N);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best_ms = 1e30f;
+  *best = 0;
+  if (rc == FEPA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(FEPA_ERR_CUDA, "event creation failed");
+  if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(double), s) != cudaSuccess)
+    rc = fail(FEPA_ERR_CUDA, "memset failed");
+  for (int v = 0; rc == FEPA_OK && v < N64_VARIANTS; ++v) {
+    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply64_variant(op, v, x, y, nullptr, s);
+    if (rc != FEPA_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = launch_apply64_variant(op, v, x, y, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (rc != FEPA_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = fail(FEPA_ERR_CUDA, "autotune timing failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    g_launches.fetch_add(7);
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = v;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x);
+  if (y) cudaFree(y);
+  return rc;
+}
+
+// FP64 action variant: the caller's, else the fastest one measured for this device, p, q
+// and form (both meet the FP64 tolerance; timed once per process)
+int ensure_v64(fepa_op* op) {
+  if (op->v64 >= 0) return FEPA_OK;
+  if (op->v64_forced >= 0) {
+    op->v64 = op->v64_forced;
+    return FEPA_OK;
+  }
+  const int dev = op->device < 64 ? op->device : 63;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  init_tuned();
+  int& slot = g_tuned64[dev][op->p][op->q - op->p - 1][op->form];
+  if (slot < 0) {
+    int best = 0;
+    TRY(time_variants64(op, &best));
+    slot = best;
+  }
+  op->v64 = slot;
   return FEPA_OK;
 }
 
@@ -510,7 +605,9 @@ constexpr int STREAM_CHUNK = 8;
 // Capture one iteration into the body of a while-node (once per loop and precond).
 template <typename Body>
 int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
-  if (L.exec && L.graph_precond == precond) return FEPA_OK;
+  TRY(ensure_v64(op));
+  const int key = precond + 16 * (op->v32 + 1) + 256 * (op->v64 + 1);
+  if (L.exec && L.graph_key == key) return FEPA_OK;
   if (L.exec) { cudaGraphExecDestroy(L.exec); L.exec = nullptr; }
   if (L.graph) { cudaGraphDestroy(L.graph); L.graph = nullptr; }
   CUDA_TRY(cudaGraphCreate(&L.graph, 0));
@@ -530,7 +627,7 @@ int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
   if (rc != FEPA_OK) return rc;
   if (ce != cudaSuccess) return fail(FEPA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
   CUDA_TRY(cudaGraphInstantiate(&L.exec, L.graph, 0));
-  L.graph_precond = precond;
+  L.graph_key = key;
   return FEPA_OK;
 }
 
@@ -538,6 +635,7 @@ int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
 template <typename Body>
 int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
   cudaStream_t s = op->stream;
+  TRY(ensure_v64(op));
   if (op->cg_mode == FEPA_CG_GRAPH) {
     TRY(build_while_graph(op, L, precond, body));
     CUDA_TRY(cudaGraphLaunch(L.exec, s));
@@ -727,6 +825,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
     return bail(fail(FEPA_ERR_CUDA, "stream creation failed"));
   int rc;
   if ((rc = allow_smem((const void*)op->ks.apply, op->ks.apply_smem)) ||
+      (rc = allow_smem((const void*)op->ks.apply_df, op->ks.df_smem)) ||
       (rc = allow_smem((const void*)op->ks.diag, op->ks.diag_smem)) ||
       (rc = allow_smem((const void*)op->ks.rhs, op->ks.rhs_smem)))
     return bail(rc);
@@ -759,6 +858,20 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   CREATE_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->B, Bh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->G, Gh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  {
+    // (hi, lo) float pairs of the FP64 tables for the double-float action (slot of this p, q)
+    std::vector<float> tdf(2 * TAB_SLOT, 0.f);
+    for (int k = 0; k < q * n; ++k) {
+      const float bh = (float)Bh[k], gh = (float)Gh[k];
+      tdf[2 * k] = bh;
+      tdf[2 * k + 1] = (float)(Bh[k] - (double)bh);
+      tdf[2 * (100 + k)] = gh;
+      tdf[2 * (100 + k) + 1] = (float)(Gh[k] - (double)gh);
+    }
+    const size_t slot = (size_t)((p - 1) * 2 + (q - p - 1)) * TAB_SLOT * 2;
+    CREATE_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float), slot * sizeof(float),
+                                       cudaMemcpyHostToDevice, s));
+  }
   CREATE_TRY(cudaMemcpyAsync(op->pts, ph.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
@@ -924,6 +1037,22 @@ int fepa_op_set_f32_variant(fepa_op* op, int32_t variant) {
 
 int32_t fepa_op_f32_variant(const fepa_op* op) { return op ? op->v32 : -1; }
 
+int fepa_op_set_f64_variant(fepa_op* op, int32_t variant) {
+  if (!op) return fail(FEPA_ERR_ARG, "op is null");
+  if (variant < -1 || variant >= N64_VARIANTS) return fail(FEPA_ERR_ARG, "variant %d outside -1..%d", variant,
+                                                            N64_VARIANTS - 1);
+  op->v64_forced = variant;
+  op->v64 = variant;  // -1: choose again at next use
+  return FEPA_OK;
+}
+
+int32_t fepa_op_f64_variant(const fepa_op* op) { return op ? op->v64 : -1; }
+
+const char* fepa_f64_variant_name(int32_t variant) {
+  static const char* names[N64_VARIANTS] = {"FP64 pipe (DFMA)", "double-float on the FP32 pipe"};
+  return (variant >= 0 && variant < N64_VARIANTS) ? names[variant] : "unknown";
+}
+
 const char* fepa_f32_variant_name(int32_t variant) {
   static const char* names[N32_VARIANTS] = {"tma-staged D", "direct D", "direct D, half block",
                                              "persistent pipeline (TMA D, cp.async gather)"};
@@ -1063,7 +1192,7 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
   }
   const double* pinv = precond ? invd : nullptr;
   CUDA_TRY(cudaMemsetAsync(h, 0, N * sizeof(double), s));
-  TRY(launch_apply(op, x, h, nullptr, s));
+  TRY(launch_apply_untuned(op, x, h, nullptr, s));
   cg_init<<<rb, RED_THREADS, 0, s>>>(N, b, r, d, h, pinv, st, rtol * rtol, maxit, partials);
   LAUNCH_CHECK();
   // host-driven loop in chunks; every kernel returns at once after the device sets done
@@ -1071,7 +1200,7 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
   CgState hs;
   for (;;) {
     for (int k = 0; k < CHUNK; ++k) {
-      TRY(launch_apply(op, d, h, &st->done, s));
+      TRY(launch_apply_untuned(op, d, h, &st->done, s));
       cg_dot_dh<<<rb, RED_THREADS, 0, s>>>(N, d, h, st, partials);
       LAUNCH_CHECK();
       cg_update<<<rb, RED_THREADS, 0, s>>>(N, x, r, d, h, pinv, st, partials);

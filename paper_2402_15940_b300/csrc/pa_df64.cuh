@@ -1,0 +1,291 @@
+// FP64-accurate partial-assembly action evaluated on the FP32 pipe (the operator
+// y = G^T B^T D B G x of Fig. fig_feod, arXiv 2402.15940).
+//
+// On this GPU the FP64 pipe issues 2 DFMA per cycle per SM against 128 FFMA, so the FP64
+// operator is bound by the FP64 pipe (the native kernel keeps it ~93 % busy).  Here every
+// value is an unevaluated sum of two floats (hi + lo, about 48 significant bits) and every
+// multiply-add of the contractions is an accurate dot-product step: the product of the
+// high parts is split exactly by an FMA, the cross terms are added by FMAs, and the
+// running sum is kept exact by TwoSum with the rounding errors collected in the low word
+// (the "Dot2" scheme of Ogita, Rump and Oishi).  That is ~12 FP32 instructions per FP64-
+// accurate multiply-add, several times the DFMA throughput, with a relative error of
+// about 2^-48 per contraction -- far inside the 1e-12 parity bound of the FP64 action.
+// x, y and D stay FP64 in memory: x and D are split into (hi, lo) as they are read,
+// the element result is recombined in FP64 and scattered with FP64 atomics, so the
+// kernel needs no data beyond the FP64 operator's and moves the same bytes.
+// Stage order and thread mapping follow the FP32 kernel (pa_tma_f32.cuh, variant 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pa_tma_f32.cuh"
+
+namespace fepa {
+
+struct __align__(8) dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_from(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfl df_zero() { return {0.f, 0.f}; }
+
+// acc += t * x, accurately (TwoProd by FMA for the high parts, cross terms by FMA,
+// TwoSum for the running sum, errors into the low word)
+__device__ __forceinline__ void df_fma(dfl& acc, dfl t, dfl x) {
+  const float p = __fmul_rn(t.h, x.h);
+  float e = __fmaf_rn(t.h, x.h, -p);
+  e = __fmaf_rn(t.h, x.l, e);
+  e = __fmaf_rn(t.l, x.h, e);
+  const float s = __fadd_rn(acc.h, p);
+  const float bv = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
+// renormalise so that |lo| <= ulp(hi)/2 (Fast2Sum; valid as |lo| is far below |hi|)
+__device__ __forceinline__ dfl df_norm(dfl a) {
+  const float s = __fadd_rn(a.h, a.l);
+  return {s, __fsub_rn(a.l, __fsub_rn(s, a.h))};
+}
+
+// tables of every compiled (P, Q) as (hi, lo) pairs: slot as in c_tab32
+__constant__ float c_tabdf[TAB_SLOT * TAB_SLOTS * 2];
+
+template <int P, int Q>
+struct TabDf {
+  static constexpr int OFF = ((P - 1) * 2 + (Q - P - 1)) * TAB_SLOT * 2;
+  static __device__ __forceinline__ dfl B(int i, int a) {
+    const int k = OFF + 2 * (i * (P + 1) + a);
+    return {c_tabdf[k], c_tabdf[k + 1]};
+  }
+  static __device__ __forceinline__ dfl G(int i, int a) {
+    const int k = OFF + 2 * (100 + i * (P + 1) + a);
+    return {c_tabdf[k], c_tabdf[k + 1]};
+  }
+};
+
+// one element group per block (as many elements as fill ~256 threads), D read directly
+template <int P, int Q, bool DIFF>
+struct DfShape {
+  using L = F32Layout<P, Q, DIFF>;
+  static constexpr int N = P + 1, TPE = Q * Q;
+  static constexpr int NE = L::NE0;
+  static constexpr int SMEM = NE * (L::XSZ + L::WORK) * 8;
+};
+
+template <int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE)
+pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, const double* __restrict__ x,
+            double* __restrict__ y, const int* __restrict__ skip) {
+  using S = DfShape<P, Q, DIFF>;
+  using L = typename S::L;
+  using T = TabDf<P, Q>;
+  constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_df[];
+  dfl* sXall = reinterpret_cast<dfl*>(smem_df);
+  dfl* sWall = sXall + NE * L::XSZ;
+  const int tid = threadIdx.x, el = threadIdx.y;
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+  const bool live = el < ne;
+  dfl* sX = sXall + el * L::XSZ;
+  dfl* S1 = sWall + el * L::WORK;
+  dfl* S2 = S1 + L::NC1 * L::S1C;
+  const int* g = gmap + (e0 + el) * (n * n * n);
+  if (live)
+    for (int l = tid; l < n * n * n; l += TPE) {
+      const int gi = g[l];
+      sX[(l / n) * L::XL + l % n] = gi >= 0 ? df_from(x[gi]) : df_zero();
+    }
+  __syncthreads();
+
+  // stage 1 (x): line (b,c) -> S1[m][c][b][i]
+  if (live && tid < n * n) {
+    dfl xv[n];
+#pragma unroll
+    for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      dfl sb = df_zero(), sg = df_zero();
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        df_fma(sb, T::B(i, a), xv[a]);
+        if (DIFF) df_fma(sg, T::G(i, a), xv[a]);
+      }
+      S1[tid * L::Q1 + i] = df_norm(sb);
+      if (DIFF) S1[L::S1C + tid * L::Q1 + i] = df_norm(sg);
+    }
+  }
+  __syncthreads();
+
+  // stage 2 (y): line (i,c) -> S2[m][c][j][i]
+  if (live && tid < Q * n) {
+    const int i = tid % Q, c = tid / Q;
+    dfl vb[n], vg[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      vb[b] = S1[(b + n * c) * L::Q1 + i];
+      if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * L::Q1 + i];
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      dfl bb = df_zero(), bg = df_zero(), gb = df_zero();
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        df_fma(bb, T::B(j, b), vb[b]);
+        if (DIFF) {
+          df_fma(bg, T::G(j, b), vb[b]);
+          df_fma(gb, T::B(j, b), vg[b]);
+        }
+      }
+      const int o = c * L::P2 + j * Q + i;
+      if (DIFF) {
+        S2[o] = df_norm(gb);
+        S2[L::S2C + o] = df_norm(bg);
+        S2[2 * L::S2C + o] = df_norm(bb);
+      } else {
+        S2[o] = df_norm(bb);
+      }
+    }
+  }
+  __syncthreads();
+
+  // stage 3 (z) + D + stage 3^T per (i,j) column, in registers
+  if (live) {
+    dfl c0[n], c1[n], c2[n], a0[n], a1[n], a2[n];
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+      c0[c] = S2[c * L::P2 + tid];
+      if (DIFF) {
+        c1[c] = S2[L::S2C + c * L::P2 + tid];
+        c2[c] = S2[2 * L::S2C + c * L::P2 + tid];
+      }
+      a0[c] = df_zero();
+      if (DIFF) a1[c] = a2[c] = df_zero();
+    }
+    const double* dE = qd + (e0 + el) * (L::NC * L::Q3) + tid;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const double* dk = dE + k * Q * Q;
+      if (DIFF) {
+        dfl u0 = df_zero(), u1 = df_zero(), u2 = df_zero();
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          df_fma(u0, T::B(k, c), c0[c]);
+          df_fma(u1, T::B(k, c), c1[c]);
+          df_fma(u2, T::G(k, c), c2[c]);
+        }
+        u0 = df_norm(u0);
+        u1 = df_norm(u1);
+        u2 = df_norm(u2);
+        const dfl d00 = df_from(__ldg(dk)), d01 = df_from(__ldg(dk + L::Q3)), d02 = df_from(__ldg(dk + 2 * L::Q3)),
+                  d11 = df_from(__ldg(dk + 3 * L::Q3)), d12 = df_from(__ldg(dk + 4 * L::Q3)),
+                  d22 = df_from(__ldg(dk + 5 * L::Q3));
+        dfl v0 = df_zero(), v1 = df_zero(), v2 = df_zero();
+        df_fma(v0, d00, u0);
+        df_fma(v0, d01, u1);
+        df_fma(v0, d02, u2);
+        df_fma(v1, d01, u0);
+        df_fma(v1, d11, u1);
+        df_fma(v1, d12, u2);
+        df_fma(v2, d02, u0);
+        df_fma(v2, d12, u1);
+        df_fma(v2, d22, u2);
+        v0 = df_norm(v0);
+        v1 = df_norm(v1);
+        v2 = df_norm(v2);
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          df_fma(a0[c], T::B(k, c), v0);
+          df_fma(a1[c], T::B(k, c), v1);
+          df_fma(a2[c], T::G(k, c), v2);
+        }
+      } else {
+        dfl u = df_zero();
+#pragma unroll
+        for (int c = 0; c < n; ++c) df_fma(u, T::B(k, c), c0[c]);
+        u = df_norm(u);
+        dfl v = df_zero();
+        df_fma(v, df_from(__ldg(dk)), u);
+        v = df_norm(v);
+#pragma unroll
+        for (int c = 0; c < n; ++c) df_fma(a0[c], T::B(k, c), v);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+      S2[c * L::P2 + tid] = df_norm(a0[c]);
+      if (DIFF) {
+        S2[L::S2C + c * L::P2 + tid] = df_norm(a1[c]);
+        S2[2 * L::S2C + c * L::P2 + tid] = df_norm(a2[c]);
+      }
+    }
+  }
+  __syncthreads();
+
+  // stage 2^T (y)
+  if (live && tid < Q * n) {
+    const int i = tid % Q, c = tid / Q;
+    dfl v0[Q], v1[Q], v2[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      v0[j] = S2[c * L::P2 + j * Q + i];
+      if (DIFF) {
+        v1[j] = S2[L::S2C + c * L::P2 + j * Q + i];
+        v2[j] = S2[2 * L::S2C + c * L::P2 + j * Q + i];
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      dfl t0 = df_zero(), t1 = df_zero();
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        df_fma(t0, T::B(j, b), v0[j]);
+        if (DIFF) {
+          df_fma(t1, T::G(j, b), v1[j]);
+          df_fma(t1, T::B(j, b), v2[j]);
+        }
+      }
+      S1[(b + n * c) * L::Q1 + i] = df_norm(t0);
+      if (DIFF) S1[L::S1C + (b + n * c) * L::Q1 + i] = df_norm(t1);
+    }
+  }
+  __syncthreads();
+
+  // stage 1^T (x) and G^T (FP64 atomics)
+  if (live && tid < n * n) {
+    dfl t0[Q], t1[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      t0[i] = S1[tid * L::Q1 + i];
+      if (DIFF) t1[i] = S1[L::S1C + tid * L::Q1 + i];
+    }
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      dfl s = df_zero();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (DIFF) {
+          df_fma(s, T::G(i, a), t0[i]);
+          df_fma(s, T::B(i, a), t1[i]);
+        } else {
+          df_fma(s, T::B(i, a), t0[i]);
+        }
+      }
+      const int gi = g[a + n * tid];
+      if (gi >= 0) {
+        atomicAdd(y + gi, df_to(s));
+      } else if (!((~gi) & ESS_SKIP)) {
+        atomicAdd(y + (~gi), x[~gi]);
+      }
+    }
+  }
+}
+
+}  // namespace fepa

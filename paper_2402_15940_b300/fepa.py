@@ -88,6 +88,9 @@ SIGNATURES = [
     ("fepa_op_set_f32_variant", ctypes.c_int, [_P, _I32]),
     ("fepa_op_f32_variant", _I32, [_P]),
     ("fepa_f32_variant_name", ctypes.c_char_p, [_I32]),
+    ("fepa_op_set_f64_variant", ctypes.c_int, [_P, _I32]),
+    ("fepa_op_f64_variant", _I32, [_P]),
+    ("fepa_f64_variant_name", ctypes.c_char_p, [_I32]),
     ("fepa_op_diagonal", ctypes.c_int, [_P, _P]),
     ("fepa_op_rhs", ctypes.c_int, [_P, _P, _P]),
     ("fepa_op_rhs_sine", ctypes.c_int, [_P, _D, _P]),
@@ -297,6 +300,14 @@ class Operator:
     def f32_variant(self):
         v = int(self._lib.fepa_op_f32_variant(self._h))
         return v, self._lib.fepa_f32_variant_name(v).decode()
+
+    def set_f64_variant(self, variant):
+        """-1: autotune at next FP64 use; 0: FP64 pipe; 1: double-float on the FP32 pipe."""
+        _check(self._lib.fepa_op_set_f64_variant(self._h, int(variant)))
+
+    def f64_variant(self):
+        v = int(self._lib.fepa_op_f64_variant(self._h))
+        return v, self._lib.fepa_f64_variant_name(v).decode()
 
     def set_cg_mode(self, mode):
         _check(self._lib.fepa_op_set_cg_mode(self._h, {"graph": CG_GRAPH, "stream": CG_STREAM}.get(mode, mode)))

@@ -1,0 +1,177 @@
+"""GPU parity of the double-float FP64 action (variant 1: every value split into two
+floats, contractions by exact FMA products and TwoSum accumulation on the FP32 pipe)
+against the oracle, at the FP64 action's tolerance (relative l2 <= 1e-12), and against
+the DFMA kernel; CG and multigrid solves on it; the full-size sampled rows."""
+import math
+
+import numpy as np
+import pytest
+
+import fem_inputs as FI
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+# elements per block is 256 // (q*q): several blocks and a ragged tail for each p
+SHAPES = {1: (5, 4, 3), 2: (4, 3, 3), 3: (3, 3, 3), 4: (3, 3, 2), 5: (3, 2, 2), 6: (3, 2, 1), 7: (2, 2, 2),
+          8: (3, 1, 1)}
+
+
+def F():
+    import paper_2402_15940_b300 as mod
+    return mod
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def make(shape, p, form, seed=0, q=None, variant=1):
+    verts = FI.perturbed_cube_vertices(*shape, seed=seed)
+    op = F().Operator(*shape, verts, p, form=form, q=0 if q is None else q)
+    op.set_f64_variant(variant)
+    return op, O.HexGridMesh(*shape, verts)
+
+
+def oracle_action(mesh, p, q, form, x, ess=None):
+    if p <= 5:
+        A = O.assemble_csr(mesh, p, q, form)
+        if ess is not None:
+            A = O.constrain(A, ess)
+        return A @ x
+    return O.action_elementwise(mesh, p, q, form, x, ess=ess)
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", list(range(1, 9)))
+def test_df_apply_matches_oracle(p, form):
+    op, mesh = make(SHAPES[p], p, form, seed=p)
+    assert op.f64_variant()[0] == 1
+    x = FI.uniform_vector(op.N, seed=100 + p)
+    y = host(op.apply(dev(x)))
+    ref = oracle_action(mesh, p, p + 2, form, x)
+    assert rel(y, ref) <= TOL
+    assert np.max(np.abs(y - ref)) <= 10 * TOL * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", [1, 3, 5, 8])
+def test_df_apply_q_equals_p_plus_1(p, form):
+    op, mesh = make(SHAPES[p], p, form, seed=p, q=p + 1)
+    x = FI.uniform_vector(op.N, seed=7)
+    assert rel(host(op.apply(dev(x))), oracle_action(mesh, p, p + 1, form, x)) <= TOL
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_df_apply_constrained_matches_oracle(p, form):
+    op, mesh = make(SHAPES[p], p, form, seed=11)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    x = FI.uniform_vector(op.N, seed=12)
+    y = host(op.apply(dev(x)))
+    assert rel(y, oracle_action(mesh, p, p + 2, form, x, ess=ess.astype(np.int64))) <= TOL
+    # essential rows return x exactly (the owner occurrence adds x in FP64)
+    assert np.array_equal(y[ess], x[ess])
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_df_agrees_with_dfma_kernel(p, form):
+    shape = (5, 4, 4)
+    op64, _ = make(shape, p, form, seed=5, variant=0)
+    opdf, _ = make(shape, p, form, seed=5, variant=1)
+    x = dev(FI.uniform_vector(op64.N, seed=6))
+    y64, ydf = host(op64.apply(x)), host(opdf.apply(x))
+    e = rel(ydf, y64)
+    assert e <= TOL
+    # far from FP32 (~1e-7): the low words carry the extra 24 bits
+    assert e <= 1e-13
+
+
+def test_df_scale_and_linearity():
+    """A(a x + b z) = a A x + b A z to double-float accuracy, and A(2^k x) = 2^k A x
+    for moderate k (scaling by a power of two is exact in both words; only the order
+    of the FP64 atomic sums differs between launches)."""
+    op, _ = make((4, 3, 3), 3, "diffusion", seed=8)
+    x = FI.uniform_vector(op.N, seed=1)
+    z = FI.uniform_vector(op.N, seed=2)
+    Ax, Az = host(op.apply(dev(x))), host(op.apply(dev(z)))
+    lin = host(op.apply(dev(0.75 * x - 1.5 * z)))
+    assert rel(lin, 0.75 * Ax - 1.5 * Az) <= 1e-13
+    for k in (-20, 17):
+        assert rel(host(op.apply(dev(np.ldexp(x, k)))), np.ldexp(Ax, k)) <= 1e-15
+
+
+@pytest.mark.parametrize("form,p,shape", [("mass", 3, (3, 3, 2)), ("diffusion", 5, (2, 3, 2)),
+                                          ("diffusion", 8, (2, 1, 2)), ("diffusion", 2, (6, 5, 4))])
+def test_df_cg_solve_matches_oracle(form, p, shape):
+    op, mesh = make(shape, p, form, seed=23)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    if form == "diffusion":
+        op.set_essential(prob.ess.astype(np.int32))
+    b = FI.uniform_vector(op.N, seed=24)
+    b[prob.ess] = 0.0
+    x, st = op.solve(dev(b), rtol=1e-10, maxit=5000)
+    xo, it_o, _ = prob.solve(b, rtol=1e-10)
+    assert abs(st["iterations"] - it_o) <= 1
+    assert rel(host(x), xo) <= 1e-8
+
+
+def test_variant_switch_rebuilds_graph_and_autotune_picks_one():
+    op, _ = make((4, 4, 4), 4, "diffusion", seed=3, variant=0)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(3 * math.pi ** 2)
+    x0, s0 = op.solve(b, rtol=1e-10)
+    op.set_f64_variant(1)
+    x1, s1 = op.solve(b, rtol=1e-10)
+    assert op.f64_variant()[0] == 1
+    assert abs(s0["iterations"] - s1["iterations"]) <= 1
+    assert rel(host(x1), host(x0)) <= 1e-9
+    op.set_f64_variant(-1)
+    x2, s2 = op.solve(b, rtol=1e-10)
+    assert op.f64_variant()[0] in (0, 1)
+    assert rel(host(x2), host(x0)) <= 1e-9
+
+
+def test_df_multigrid_solve():
+    shape, p = (4, 4, 4), 4
+    op, mesh = make(shape, p, "diffusion", seed=5)
+    op.set_essential(op.boundary_dofs())
+    mg = F().Multigrid(op, precision="fp32")
+    b = op.rhs_sine(3 * math.pi ** 2)
+    x, st = mg.solve(b, rtol=1e-10)
+    prob = O.Problem(mesh, p, None, "diffusion")
+    xo, _, _ = prob.solve(host(b), rtol=1e-13)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert rel(host(x), xo) <= 1e-9
+
+
+def test_df_full_size_bp3_p4_sampled():
+    """Diffusion, p=4 on 64^3 perturbed hexes (257^3 DOFs): sampled rows of the
+    constrained double-float action against the oracle, one by one."""
+    shape, p = (64, 64, 64), 4
+    op, mesh = make(shape, p, "diffusion", seed=0)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    x = FI.uniform_vector(op.N, seed=0)
+    y = host(op.apply(dev(x)))
+    rng = np.random.default_rng(42)
+    rows = np.concatenate([rng.choice(op.N, 48, replace=False), ess[rng.choice(len(ess), 8, replace=False)],
+                           [0, op.N - 1, op.N // 2]])
+    ref = O.action_rows(mesh, p, p + 2, O.DIFFUSION, x, rows, ess=ess.astype(np.int64))
+    assert np.max(np.abs(y[rows] - ref)) <= 1e-12 * np.max(np.abs(ref))
