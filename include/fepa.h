@@ -351,6 +351,11 @@ int fepa_batch_offsets(const fepa_batch* batch, int64_t* offsets);   /* host, co
 int32_t fepa_batch_groups(const fepa_batch* batch);                  /* distinct (p, form) */
 int fepa_batch_set_stream(fepa_batch* batch, void* stream);
 
+/* FP64 action variant of every group (as fepa_op_set_f64_variant: 0 DFMA, 1 double-float,
+ * -1 = the process-wide choice for the group's (p, q, form) if one was measured, else
+ * the faster of the two timed on the group at the next apply or solve). */
+int fepa_batch_set_f64_variant(fepa_batch* batch, int32_t variant);
+
 /* y = A x for every problem at once (x, y: device, total DOFs). */
 int fepa_batch_apply(fepa_batch* batch, const double* x, double* y);
 

@@ -91,7 +91,8 @@ using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, 
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
 constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
-using ApplyDfFn = void (*)(int, const int*, const double*, const double*, double*, const int*);
+using ApplyDfFn = void (*)(int, const int*, const float2*, const double*, double*, const int*, const int*,
+                          const int*);
 
 struct Apply32Variant {
   Apply32Fn fn;
@@ -166,6 +167,24 @@ const KernelTable& kernels() {
   return table;
 }
 
+// (hi, lo) float pairs of the FP64 1D tables for the double-float action, into the
+// constant-memory slot of (p, q)
+int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vector<double>& Gh, cudaStream_t s) {
+  const int n = p + 1;
+  std::vector<float> tdf(2 * TAB_SLOT, 0.f);
+  for (int k = 0; k < q * n; ++k) {
+    const float bh = (float)Bh[k], gh = (float)Gh[k];
+    tdf[2 * k] = bh;
+    tdf[2 * k + 1] = (float)(Bh[k] - (double)bh);
+    tdf[2 * (100 + k)] = gh;
+    tdf[2 * (100 + k) + 1] = (float)(Gh[k] - (double)gh);
+  }
+  const size_t slot = (size_t)((p - 1) * 2 + (q - p - 1)) * TAB_SLOT * 2;
+  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float), slot * sizeof(float),
+                                   cudaMemcpyHostToDevice, s));
+  return FEPA_OK;
+}
+
 int allow_smem(const void* fn, int bytes) {
   if (bytes > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return FEPA_OK;
@@ -210,6 +229,9 @@ struct fepa_op {
   // FP32 operator data (built on first use): padded FP32 D; tables in constant memory
   float* qd32 = nullptr;
   bool qd32_valid = false;
+  // double-float action data (built when that variant is in use): D as (hi, lo) floats
+  float2* qddf = nullptr;
+  bool qddf_valid = false;
   int v32 = -1;        // FP32 kernel variant in use (-1: not chosen yet)
   int v32_grid[4] = {0, 0, 0, 0};  // launch grid per variant (persistent: SMs x resident blocks)
   int v32_forced = -1; // variant set by the caller (-1: autotune)
@@ -255,7 +277,7 @@ void free_op(fepa_op* op) {
   free_loop(op->cg64);
   free_loop(op->cg32);
   for (void* p : {(void*)op->verts, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
-                  (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->err,
+                  (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->qddf, (void*)op->err,
                   (void*)op->inv_diag, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->h64,
                   (void*)op->st_ref, (void*)op->partials_ref})
     if (p) cudaFree(p);
@@ -282,7 +304,8 @@ int launch_apply64_variant(fepa_op* op, int v, const double* x, double* y, const
   const KernelSet& k = op->ks;
   if (v == 1) {
     const int grid = (int)((op->E + k.df_ne - 1) / k.df_ne);
-    k.apply_df<<<grid, dim3(k.apply_tpe, k.df_ne), k.df_smem, s>>>((int)op->E, op->gmap, op->qd, x, y, skip);
+    k.apply_df<<<grid, dim3(k.apply_tpe, k.df_ne), k.df_smem, s>>>((int)op->E, op->gmap, op->qddf, x, y, skip,
+                                                                   nullptr, nullptr);
   } else {
     const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
     k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x,
@@ -292,12 +315,13 @@ int launch_apply64_variant(fepa_op* op, int v, const double* x, double* y, const
   return FEPA_OK;
 }
 
-int ensure_v64(fepa_op* op);
+int prepare_f64(fepa_op* op);
 
 // y += A x in FP64 without choosing a variant (no timing, no allocation): the chosen or
 // forced variant, else the DFMA kernel (counted)
 int launch_apply_untuned(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
-  const int v = op->v64 >= 0 ? op->v64 : (op->v64_forced >= 0 ? op->v64_forced : 0);
+  int v = op->v64 >= 0 ? op->v64 : (op->v64_forced >= 0 ? op->v64_forced : 0);
+  if (v == 1 && !op->qddf_valid) v = 0;  // its D copy would need an allocation
   TRY(launch_apply64_variant(op, v, x, y, skip, s));
   g_launches.fetch_add(1);
   return FEPA_OK;
@@ -305,7 +329,7 @@ int launch_apply_untuned(fepa_op* op, const double* x, double* y, const int* ski
 
 // y += A x in FP64 (launch only; counted)
 int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
-  TRY(ensure_v64(op));
+  TRY(prepare_f64(op));
   TRY(launch_apply64_variant(op, op->v64, x, y, skip, s));
   g_launches.fetch_add(1);
   return FEPA_OK;
@@ -345,7 +369,7 @@ int launch_apply32_nocount(fepa_op* op, const float* x, float* y, const int* ski
   return launch_apply32_variant(op, op->v32, x, y, skip, s);
 }
 
-// (the variant is chosen before any capture: ensure_v64 runs in run_loop)
+// (the variant and its data are prepared before any capture: prepare_f64 runs in run_loop)
 int launch_apply_nocount(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
   return launch_apply64_variant(op, op->v64 < 0 ? 0 : op->v64, x, y, skip, s);
 }
@@ -475,6 +499,17 @@ int choose_variant32(fepa_op* op) {
   return FEPA_OK;
 }
 
+// (hi, lo) copy of D for the double-float action (allocated once, rebuilt after the mesh moves)
+int ensure_df(fepa_op* op) {
+  if (op->qddf_valid) return FEPA_OK;
+  const int64_t count = op->E * (op->form == FEPA_DIFFUSION ? 6 : 1) * (int64_t)op->q * op->q * op->q;
+  if (!op->qddf) TRY(dalloc(&op->qddf, count));
+  split_to_df<<<grid_for(count, 256, 148 * 32), 256, 0, op->stream>>>(count, op->qd, op->qddf);
+  LAUNCH_CHECK();
+  op->qddf_valid = true;
+  return FEPA_OK;
+}
+
 // Time the FP64 action variants on this op (2 warm-up + 5 timed launches each).
 int time_variants64(fepa_op* op, int* best) {
   cudaStream_t s = op->stream;
@@ -488,6 +523,7 @@ int time_variants64(fepa_op* op, int* best) {
     rc = fail(FEPA_ERR_CUDA, "event creation failed");
   if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(double), s) != cudaSuccess)
     rc = fail(FEPA_ERR_CUDA, "memset failed");
+  if (rc == FEPA_OK) rc = ensure_df(op);
   for (int v = 0; rc == FEPA_OK && v < N64_VARIANTS; ++v) {
     for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply64_variant(op, v, x, y, nullptr, s);
     if (rc != FEPA_OK) break;
@@ -514,6 +550,13 @@ int time_variants64(fepa_op* op, int* best) {
   return rc;
 }
 
+// Cached FP64 variant choice for (device, p, q, form), -1 if none yet (caller holds no lock)
+int tuned64_lookup(int device, int p, int q, int form) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  init_tuned();
+  return g_tuned64[device < 64 ? device : 63][p][q - p - 1][form];
+}
+
 // FP64 action variant: the caller's, else the fastest one measured for this device, p, q
 // and form (both meet the FP64 tolerance; timed once per process)
 int ensure_v64(fepa_op* op) {
@@ -532,6 +575,19 @@ int ensure_v64(fepa_op* op) {
     slot = best;
   }
   op->v64 = slot;
+  if (op->v64 != 1 && op->qddf) {  // the timing built a D copy the chosen kernel does not read
+    cudaStreamSynchronize(op->stream);
+    cudaFree(op->qddf);
+    op->qddf = nullptr;
+    op->qddf_valid = false;
+  }
+  return FEPA_OK;
+}
+
+// variant chosen and its data current (call outside graph capture, before launches)
+int prepare_f64(fepa_op* op) {
+  TRY(ensure_v64(op));
+  if (op->v64 == 1) TRY(ensure_df(op));
   return FEPA_OK;
 }
 
@@ -605,7 +661,7 @@ constexpr int STREAM_CHUNK = 8;
 // Capture one iteration into the body of a while-node (once per loop and precond).
 template <typename Body>
 int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
-  TRY(ensure_v64(op));
+  TRY(prepare_f64(op));
   const int key = precond + 16 * (op->v32 + 1) + 256 * (op->v64 + 1);
   if (L.exec && L.graph_key == key) return FEPA_OK;
   if (L.exec) { cudaGraphExecDestroy(L.exec); L.exec = nullptr; }
@@ -635,7 +691,7 @@ int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
 template <typename Body>
 int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
   cudaStream_t s = op->stream;
-  TRY(ensure_v64(op));
+  TRY(prepare_f64(op));
   if (op->cg_mode == FEPA_CG_GRAPH) {
     TRY(build_while_graph(op, L, precond, body));
     CUDA_TRY(cudaGraphLaunch(L.exec, s));
@@ -858,20 +914,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   CREATE_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->B, Bh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->G, Gh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
-  {
-    // (hi, lo) float pairs of the FP64 tables for the double-float action (slot of this p, q)
-    std::vector<float> tdf(2 * TAB_SLOT, 0.f);
-    for (int k = 0; k < q * n; ++k) {
-      const float bh = (float)Bh[k], gh = (float)Gh[k];
-      tdf[2 * k] = bh;
-      tdf[2 * k + 1] = (float)(Bh[k] - (double)bh);
-      tdf[2 * (100 + k)] = gh;
-      tdf[2 * (100 + k) + 1] = (float)(Gh[k] - (double)gh);
-    }
-    const size_t slot = (size_t)((p - 1) * 2 + (q - p - 1)) * TAB_SLOT * 2;
-    CREATE_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float), slot * sizeof(float),
-                                       cudaMemcpyHostToDevice, s));
-  }
+  if ((rc = upload_df_tables(p, q, Bh, Gh, s))) return bail(rc);
   CREATE_TRY(cudaMemcpyAsync(op->pts, ph.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CREATE_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
@@ -911,6 +954,7 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
   op->inv_diag_valid = false;
   op->inv32_valid = false;
   op->qd32_valid = false;
+  op->qddf_valid = false;
   CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");

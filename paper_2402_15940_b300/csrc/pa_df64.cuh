@@ -10,9 +10,11 @@
 // (the "Dot2" scheme of Ogita, Rump and Oishi).  That is ~12 FP32 instructions per FP64-
 // accurate multiply-add, several times the DFMA throughput, with a relative error of
 // about 2^-48 per contraction -- far inside the 1e-12 parity bound of the FP64 action.
-// x, y and D stay FP64 in memory: x and D are split into (hi, lo) as they are read,
-// the element result is recombined in FP64 and scattered with FP64 atomics, so the
-// kernel needs no data beyond the FP64 operator's and moves the same bytes.
+// x and y stay FP64 in memory: x is split into (hi, lo) as it is gathered and the element
+// result is recombined in FP64 and scattered with FP64 atomics.  D is read as (hi, lo)
+// float pairs (8 bytes per value, as FP64) split once from the FP64 D by split_to_df:
+// converting D in the hot loop would put ~4 FP64-pipe instructions per stored value on
+// the very pipe this kernel exists to avoid.
 // Stage order and thread mapping follow the FP32 kernel (pa_tma_f32.cuh, variant 1).
 #pragma once
 #include <cuda_runtime.h>
@@ -32,6 +34,10 @@ __device__ __forceinline__ dfl df_from(double d) {
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ dfl df_zero() { return {0.f, 0.f}; }
+__device__ __forceinline__ dfl df_ld(const float2* p) {
+  const float2 v = __ldg(p);
+  return {v.x, v.y};
+}
 
 // acc += t * x, accurately (TwoProd by FMA for the high parts, cross terms by FMA,
 // TwoSum for the running sum, errors into the low word)
@@ -78,10 +84,25 @@ struct DfShape {
   static constexpr int SMEM = NE * (L::XSZ + L::WORK) * 8;
 };
 
+// MINB: resident blocks per SM the register allocation must allow (0: no constraint);
+// KU: unroll of the stage-3 quadrature loop (Q = fully unrolled).  Measured on B300:
+// for diffusion from p = 4 on, a fully unrolled stage 3 holds 100-255 registers and one
+// or two blocks per SM; with the loop rolled (tables read per k from constant memory)
+// and two blocks per SM guaranteed, p = 4 runs 1.08x, p = 6 2.7x and p = 8 2.2x faster.
+// Lower orders and the mass form are fastest with no constraint (an explicit minimum
+// of 1 lets the allocator take up to 255 registers: 1.1-2x slower); the mass form rolls
+// its (short) stage-3 loop from p = 6 on.
 template <int P, int Q, bool DIFF>
-__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE)
-pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, const double* __restrict__ x,
-            double* __restrict__ y, const int* __restrict__ skip) {
+struct DfTune {
+  static constexpr int MINB = (DIFF && P >= 4) ? 2 : 0;
+  static constexpr int KU = (P >= (DIFF ? 4 : 6)) ? 1 : Q;
+};
+
+template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 0>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
+pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
+            double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
+            const int* __restrict__ prob_done) {
   using S = DfShape<P, Q, DIFF>;
   using L = typename S::L;
   using T = TabDf<P, Q>;
@@ -93,7 +114,11 @@ pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
-  const bool live = el < ne;
+  // batched problems: the elements of a converged problem do no work
+  if (PF > 0 && tid == 0 && el == 0)
+    prefetch_group<PF>(qd + e0 * (L::NC * L::Q3), (size_t)ne * L::NC * L::Q3 * 8u, gmap + e0 * (n * n * n),
+                       ne * n * n * n);
+  const bool live = el < ne && !(elem_prob && prob_done[elem_prob[e0 + el]]);
   dfl* sX = sXall + el * L::XSZ;
   dfl* S1 = sWall + el * L::WORK;
   dfl* S2 = S1 + L::NC1 * L::S1C;
@@ -169,10 +194,10 @@ pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
       a0[c] = df_zero();
       if (DIFF) a1[c] = a2[c] = df_zero();
     }
-    const double* dE = qd + (e0 + el) * (L::NC * L::Q3) + tid;
-#pragma unroll
+    const float2* dE = qd + (e0 + el) * (L::NC * L::Q3) + tid;
+#pragma unroll KU
     for (int k = 0; k < Q; ++k) {
-      const double* dk = dE + k * Q * Q;
+      const float2* dk = dE + k * Q * Q;
       if (DIFF) {
         dfl u0 = df_zero(), u1 = df_zero(), u2 = df_zero();
 #pragma unroll
@@ -184,9 +209,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
         u0 = df_norm(u0);
         u1 = df_norm(u1);
         u2 = df_norm(u2);
-        const dfl d00 = df_from(__ldg(dk)), d01 = df_from(__ldg(dk + L::Q3)), d02 = df_from(__ldg(dk + 2 * L::Q3)),
-                  d11 = df_from(__ldg(dk + 3 * L::Q3)), d12 = df_from(__ldg(dk + 4 * L::Q3)),
-                  d22 = df_from(__ldg(dk + 5 * L::Q3));
+        const dfl d00 = df_ld(dk), d01 = df_ld(dk + L::Q3), d02 = df_ld(dk + 2 * L::Q3), d11 = df_ld(dk + 3 * L::Q3),
+                  d12 = df_ld(dk + 4 * L::Q3), d22 = df_ld(dk + 5 * L::Q3);
         dfl v0 = df_zero(), v1 = df_zero(), v2 = df_zero();
         df_fma(v0, d00, u0);
         df_fma(v0, d01, u1);
@@ -212,7 +236,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
         for (int c = 0; c < n; ++c) df_fma(u, T::B(k, c), c0[c]);
         u = df_norm(u);
         dfl v = df_zero();
-        df_fma(v, df_from(__ldg(dk)), u);
+        df_fma(v, df_ld(dk), u);
         v = df_norm(v);
 #pragma unroll
         for (int c = 0; c < n; ++c) df_fma(a0[c], T::B(k, c), v);
@@ -285,6 +309,14 @@ pa_apply_df(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
         atomicAdd(y + (~gi), x[~gi]);
       }
     }
+  }
+}
+
+// FP64 D -> (hi, lo) float pairs, same layout [e][comp][q^3]
+__global__ void split_to_df(int64_t count, const double* __restrict__ qd, float2* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const dfl v = df_from(qd[t]);
+    out[t] = make_float2(v.h, v.l);
   }
 }
 

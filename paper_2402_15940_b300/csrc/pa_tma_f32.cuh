@@ -124,6 +124,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+// one thread asks the TMA engine to pull [p, p + bytes) into L2 (p and bytes multiples of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of [p, p + bytes) widened to 16-byte boundaries (every allocation of this
+// library is 256-byte aligned and carries 16 bytes of slack past its end)
+__device__ __forceinline__ void prefetch_range(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = a & ~(uintptr_t)15, hi = (a + bytes + 15) & ~(uintptr_t)15;
+  bulk_prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
+}
+
+// L2 prefetch of an element group's D block (PF >= 1) and map entries (PF >= 2), issued
+// by one thread when the block starts so the later loads hit L2
+template <int PF>
+__device__ __forceinline__ void prefetch_group(const void* d, size_t dbytes, const int* g, int nidx) {
+  if (PF >= 1) prefetch_range(d, dbytes);
+  if (PF >= 2) prefetch_range(g, 4u * (size_t)nidx);
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -321,7 +342,7 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 // ---------------------------------------------------------------------------
 // variants 0-2: one element group per block
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV>
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 0>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
@@ -336,6 +357,8 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+  if (!STAGE_D && PF > 0 && tid == 0 && el == 0)
+    prefetch_group<PF>(qd32 + e0 * S::DELEM, (size_t)ne * S::DELEM * 4u, gmap + e0 * (n * n * n), ne * n * n * n);
   if (STAGE_D && tid == 0 && el == 0) {
     mbar_init(mbar, 1);
     const uint32_t bytes = (uint32_t)ne * S::DELEM * 4u;

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("fepa_batch_offsets", ctypes.c_int, [_P, _P]),
     ("fepa_batch_groups", _I32, [_P]),
     ("fepa_batch_set_stream", ctypes.c_int, [_P, _P]),
+    ("fepa_batch_set_f64_variant", ctypes.c_int, [_P, _I32]),
     ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
     ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
     ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
@@ -464,6 +465,10 @@ class Batch:
     def _sync_stream(self):
         torch = _torch()
         _check(self._lib.fepa_batch_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def set_f64_variant(self, variant):
+        """-1: measured choice per group; 0: FP64 pipe; 1: double-float on the FP32 pipe."""
+        _check(self._lib.fepa_batch_set_f64_variant(self._h, int(variant)))
 
     def apply(self, x, out=None):
         torch = _torch()

@@ -47,11 +47,12 @@ class Request:
 
 def device_bytes(req: Request) -> int:
     """Upper estimate of the device memory a resident request holds: vertices, element
-    map, FP64 D, FP32 D (mixed), the CG work vectors, right-hand side and solution."""
+    map, FP64 D and its (hi, lo) float copy for the double-float action, FP32 D (mixed),
+    the CG work vectors, right-hand side and solution."""
     n, q, E, N = req.p + 1, req.p + 2, req.nelems, req.ndofs
     ncomp = 6 if req.form == "diffusion" else 1
     nv = (req.n[0] + 1) * (req.n[1] + 1) * (req.n[2] + 1)
-    by = 24 * nv + 4 * n ** 3 * E + 8 * ncomp * q ** 3 * E
+    by = 24 * nv + 4 * n ** 3 * E + 2 * 8 * ncomp * q ** 3 * E
     by += 8 * N * 8                                   # b, x, r, d, h, 1/diag, copies
     if req.precision == "mixed":
         by += 4 * ncomp * (((q ** 3) + 3) & ~3) * E   # padded FP32 D

@@ -60,9 +60,12 @@ def test_batch_layout_and_groups():
     assert bt.groups == len({(pr["p"], pr["form"]) for pr in probs})
 
 
-def test_batch_apply_matches_oracle():
+@pytest.mark.parametrize("variant", [-1, 0, 1])
+def test_batch_apply_matches_oracle(variant):
+    """Both FP64 action kernels (DFMA, double-float) and the measured choice."""
     probs = small_mix(seed=1)
     bt = F().Batch(probs)
+    bt.set_f64_variant(variant)
     x = FI.uniform_vector(bt.N, seed=3)
     y = bt.apply(torch.from_numpy(x).cuda()).cpu().numpy()
     for i, pr in enumerate(probs):
@@ -71,9 +74,11 @@ def test_batch_apply_matches_oracle():
         assert rel(y[sl], op.apply(x[sl], constrained=True)) <= 1e-12, i
 
 
-def test_batch_solve_matches_oracle_and_alone():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batch_solve_matches_oracle_and_alone(variant):
     probs = small_mix(seed=2, count=12)
     bt = F().Batch(probs)
+    bt.set_f64_variant(variant)
     b = rhs_for(probs, bt.offsets)
     x, st = bt.solve(torch.from_numpy(b).cuda(), rtol=1e-10)
     x = x.cpu().numpy()
