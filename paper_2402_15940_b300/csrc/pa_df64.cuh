@@ -84,6 +84,7 @@ struct DfShape {
   static constexpr int SMEM = NE * (L::XSZ + L::WORK) * 8;
 };
 
+// PF: L2 prefetch of the group's D and map at block start (as in pa_tma_f32.cuh; 4-9 %).
 // MINB: resident blocks per SM the register allocation must allow (0: no constraint);
 // KU: unroll of the stage-3 quadrature loop (Q = fully unrolled).  Measured on B300:
 // for diffusion from p = 4 on, a fully unrolled stage 3 holds 100-255 registers and one
@@ -98,7 +99,7 @@ struct DfTune {
   static constexpr int KU = (P >= (DIFF ? 4 : 6)) ? 1 : Q;
 };
 
-template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 0>
+template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
 __global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
 pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
             double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
@@ -114,10 +115,13 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
-  // batched problems: the elements of a converged problem do no work
-  if (PF > 0 && tid == 0 && el == 0)
+  // L2 prefetch of the group's D and map (batched problems: not when the problems of the
+  // group's first and last elements have converged)
+  if (PF > 0 && tid == 0 && el == 0 &&
+      !(elem_prob && prob_done[elem_prob[e0]] && prob_done[elem_prob[e0 + ne - 1]]))
     prefetch_group<PF>(qd + e0 * (L::NC * L::Q3), (size_t)ne * L::NC * L::Q3 * 8u, gmap + e0 * (n * n * n),
                        ne * n * n * n);
+  // batched problems: the elements of a converged problem do no work
   const bool live = el < ne && !(elem_prob && prob_done[elem_prob[e0 + el]]);
   dfl* sX = sXall + el * L::XSZ;
   dfl* S1 = sWall + el * L::WORK;

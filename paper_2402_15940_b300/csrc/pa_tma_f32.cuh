@@ -149,9 +149,27 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// stages (called by every thread of the block; `tid` is the thread's index within
-// its element, `live` whether its element exists)
+// stages (called by every thread of the block; `tid` is the work item's line within
+// its element, `live` whether its element exists).  Stages 1, 2, 2^T and 1^T have
+// fewer lines per element (n^2, Q n) than the element has threads (Q^2).  FLAT: the
+// block deals their lines out over all its threads, so idle lanes gather in the last
+// warps, which then skip the stage, instead of sitting in every warp.  Measured on
+// B300 (with the L2 prefetch): p=2 8 %, p=4 2 % faster; p=6, 8 10-19 % slower
+// (no warp is saved there and the straddled elements cost more), so p <= 4 only.
 // ---------------------------------------------------------------------------
+
+// work item of a stage with W lines per element: (element, line) of thread (tid, el)
+template <bool FLAT, int W, int TPE>
+__device__ __forceinline__ void stage_item(int tid, int el, int& e, int& line) {
+  if (FLAT) {
+    const int f = el * TPE + tid;
+    e = f / W;
+    line = f - e * W;
+  } else {
+    e = el;
+    line = tid;  // lines >= W: the stage's own check leaves them idle
+  }
+}
 
 // stage 1 (x): line (b,c) -> S1[m][c][b][i] for all i
 template <int P, int Q, bool DIFF>
@@ -342,7 +360,9 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 // ---------------------------------------------------------------------------
 // variants 0-2: one element group per block
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 0>
+// PF: L2 prefetch at block start (TMA engine, one thread): 1 = the group's D (unless staged),
+// 2 = also its map entries.  Measured on B300: 4-11 % faster for p = 2..8 (PF 2 best).
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4)>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
@@ -357,8 +377,10 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
-  if (!STAGE_D && PF > 0 && tid == 0 && el == 0)
-    prefetch_group<PF>(qd32 + e0 * S::DELEM, (size_t)ne * S::DELEM * 4u, gmap + e0 * (n * n * n), ne * n * n * n);
+  if (PF > 0 && tid == 0 && el == 0) {
+    if (!STAGE_D) prefetch_range(qd32 + e0 * S::DELEM, (size_t)ne * S::DELEM * 4u);
+    if (PF >= 2) prefetch_range(gmap + e0 * (n * n * n), 4u * (size_t)ne * n * n * n);
+  }
   if (STAGE_D && tid == 0 && el == 0) {
     mbar_init(mbar, 1);
     const uint32_t bytes = (uint32_t)ne * S::DELEM * 4u;
@@ -376,9 +398,18 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
       sX[(l / n) * S::XL + l % n] = gi >= 0 ? x[gi] : 0.f;
     }
   __syncthreads();
-  f32_stage1<P, Q, DIFF>(tid, live, sX, S1);
+  {
+    int e, ln;
+    stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
+    f32_stage1<P, Q, DIFF>(ln, e < ne, sXall + e * S::XSZ, sWall + e * S::WORK);
+  }
   __syncthreads();
-  f32_stage2<P, Q, DIFF>(tid, live, S1, S2);
+  {
+    int e, ln;
+    stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
+    float* S1e = sWall + e * S::WORK;
+    f32_stage2<P, Q, DIFF>(ln, e < ne, S1e, S1e + S::NC1 * S::S1C);
+  }
   if (STAGE_D) {
     // D must have landed before stage 3; every thread observes the barrier (bounded)
     const bool ok = mbar_wait_bounded(mbar);
@@ -395,15 +426,24 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
   f32_stage3<P, Q, DIFF>(tid, live, S2, dE);
   __syncthreads();
-  f32_stage2t<P, Q, DIFF>(tid, live, S2, S1);
+  {
+    int e, ln;
+    stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
+    float* S1e = sWall + e * S::WORK;
+    f32_stage2t<P, Q, DIFF>(ln, e < ne, S1e + S::NC1 * S::S1C, S1e);
+  }
   __syncthreads();
-  f32_stage1t<P, Q, DIFF>(tid, live, S1, g, x, y);
+  {
+    int e, ln;
+    stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
+    f32_stage1t<P, Q, DIFF>(ln, e < ne, sWall + e * S::WORK, gmap + (e0 + e) * (n * n * n), x, y);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // variant 3: persistent, software-pipelined over element groups
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool DIFF>
+template <int P, int Q, bool DIFF, bool FLAT = (P <= 4)>
 __global__ void __launch_bounds__(PipeShape<P, Q, DIFF>::T)
 pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                   float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
@@ -485,10 +525,20 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
     cp_async_wait_all();
     __syncthreads();
     const int64_t e0 = (int64_t)g * NE;
-    const bool live = e0 + el < E;
-    f32_stage1<P, Q, DIFF>(tid, live, sX + cur * NE * S::XSZ + el * S::XSZ, S1);
+    const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+    const bool live = el < ne;
+    {
+      int e, ln;
+      stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
+      f32_stage1<P, Q, DIFF>(ln, e < ne, sX + cur * NE * S::XSZ + e * S::XSZ, sW + e * S::WORK);
+    }
     __syncthreads();
-    f32_stage2<P, Q, DIFF>(tid, live, S1, S2);
+    {
+      int e, ln;
+      stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
+      float* S1e = sW + e * S::WORK;
+      f32_stage2<P, Q, DIFF>(ln, e < ne, S1e, S1e + S::NC1 * S::S1C);
+    }
     if (has_next) gather(gn, nxt, r);
     const uint32_t pc = cur ? ph1 : ph0, pn = cur ? ph0 : ph1;
     const bool ok = mbar_wait_bounded(&mbar[cur], pc);
@@ -504,9 +554,18 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
     }
     f32_stage3<P, Q, DIFF>(tid, live, S2, sD + cur * NE * S::DELEM + el * S::DELEM + tid);
     __syncthreads();
-    f32_stage2t<P, Q, DIFF>(tid, live, S2, S1);
+    {
+      int e, ln;
+      stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
+      float* S1e = sW + e * S::WORK;
+      f32_stage2t<P, Q, DIFF>(ln, e < ne, S1e + S::NC1 * S::S1C, S1e);
+    }
     __syncthreads();
-    f32_stage1t<P, Q, DIFF>(tid, live, S1, sI + cur * S::IDX + el * n3, x, y);
+    {
+      int e, ln;
+      stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
+      f32_stage1t<P, Q, DIFF>(ln, e < ne, sW + e * S::WORK, sI + cur * S::IDX + e * n3, x, y);
+    }
     __syncthreads();
     cur = nxt;
   }
