@@ -6,7 +6,9 @@ manufactured solution, matrix-free diagonal, and the solve to a relative FP64
 residual of 1e-10 (every CG iteration applies the fused G^T B^T D B G kernel).
 Two forms of the solve are timed on the same problem: the mixed-precision one (FP64
 iterative refinement around an FP32 Jacobi-PCG; the headline `value`) and the plain
-FP64 Jacobi-PCG (`fp64_plain`).
+FP64 Jacobi-PCG (`fp64_plain`); beside them the same solve by mixed-precision CG with reliable
+updates (`mixed_reliable`) and by FP64 CG preconditioned with an FP32 p-multigrid V-cycle
+(`mg_pcg_fp32_vcycle`).
 value = N * (CG iterations) / step time, summed over ranks (independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -229,6 +231,9 @@ def run_ours(args, rank, world, dist):
         if prec == "mg":
             _, st = mg["mg"].solve(b, x, rtol=args.rtol, maxit=args.maxit)
             return st["iterations"], st
+        if prec == "reliable":
+            _, st = op.solve_reliable(b, x, rtol=args.rtol, delta=args.delta)
+            return st["inner_iterations"], st
         _, st = op.solve_refined(b, x, rtol=args.rtol, inner_rtol=args.inner_rtol)
         return st["inner_iterations"], st
 
@@ -316,6 +321,8 @@ def run_ours(args, rank, world, dist):
     results = {}
     if args.multigrid:
         results["mg"] = timed("mg")
+    if args.reliable:
+        results["reliable"] = timed("reliable")
     for prec in ("mixed", "fp64"):
         if args.precision not in (prec, "both"):
             continue
@@ -398,6 +405,17 @@ def run_ours(args, rank, world, dist):
                 "gdofs_per_cg_iter": m["value"], "gpu_launches": m["gpu_launches"]}
             if "fp64" in results:
                 line["mg_pcg_fp32_vcycle"]["time_to_solution_speedup_vs_fp64"] = (
+                    results["fp64"]["ms_per_step"] / m["ms_per_step"])
+        if "reliable" in results:
+            m = results["reliable"]
+            line["mixed_reliable"] = {
+                "solver": f"one FP32 Jacobi-PCG recurrence, residual replaced by the FP64 residual each time it "
+                          f"falls by {args.delta} (reliable updates; direction and scalars kept)",
+                "ms_per_step": m["ms_per_step"], "iterations_per_step": m["iterations_per_step"],
+                "gdofs_per_cg_iter": m["value"], "gpu_launches": m["gpu_launches"],
+                "replacements": m["stats"]["outer_iterations"], "rel_residual": m["stats"]["rel_residual"]}
+            if "fp64" in results:
+                line["mixed_reliable"]["time_to_solution_speedup_vs_fp64"] = (
                     results["fp64"]["ms_per_step"] / m["ms_per_step"])
         if mixed and "fp64" in results:
             f64 = results["fp64"]
@@ -535,6 +553,9 @@ def main():
     ap.add_argument("--cg-mode", choices=["graph", "stream"], default="graph",
                     help="graph: CG loop in one CUDA graph (default); stream: plain launches (for profiling)")
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--delta", type=float, default=0.03, help="reliable-update replacement factor")
+    ap.add_argument("--no-reliable", dest="reliable", action="store_false",
+                    help="skip the reliable-update mixed solve")
     ap.add_argument("--no-multigrid", dest="multigrid", action="store_false",
                     help="skip the p-multigrid preconditioned form")
     ap.add_argument("--traffic-fp64", type=float, default=None, help="DRAM bytes per FP64 apply launch (ncu)")

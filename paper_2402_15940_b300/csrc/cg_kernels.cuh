@@ -369,6 +369,42 @@ refine_residual(int64_t N, const double* __restrict__ b, const double* __restric
   }
 }
 
+// Residual replacement for the reliable-update solve: the FP32 loop stopped after its
+// residual fell by delta; x has absorbed e, r holds the FP64 residual b - A x rounded to
+// FP32.  Here: e = 0; rho = (z, r), rr = (r, r) of the replaced residual; beta so that
+// the following direction kernel gives d = z + (rho / rho_prev) d_prev, continuing the
+// same Krylov recurrence (rho_prev = rho_last / beta_last); stop the next segment at
+// rr <= max(delta2 rr, floor2).
+__global__ void __launch_bounds__(RED_THREADS)
+cg32_replace(int64_t N, const float* __restrict__ r, float* __restrict__ e, const float* __restrict__ inv_diag,
+             CgState* st, double delta2, double floor2, double* partials) {
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = r[i];
+    const float zi = inv_diag ? ri * inv_diag[i] : ri;
+    e[i] = 0.f;
+    f2_add_prod(zr_h, zr_l, zi, ri);
+    f2_add_prod(rr_h, rr_l, ri, ri);
+  }
+  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
+    if (threadIdx.x == 0) {
+      // (no step taken since the last start: beta 0 restarts the direction at d = z)
+      st->beta = st->beta != 0.0 ? tot[0] / (st->rho / st->beta) : 0.0;
+      st->rho = tot[0];
+      st->rr = tot[1];
+      st->tol2 = delta2 * tot[1] > floor2 ? delta2 * tot[1] : floor2;
+      st->converged = 0;
+      st->done = 0;
+      st->ticket = 0;
+    }
+  }
+}
+
 // x += e (FP64 accumulation of the FP32 correction)
 __global__ void refine_correct(int64_t N, double* __restrict__ x, const float* __restrict__ e) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)

@@ -755,6 +755,13 @@ int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int 
 }
 
 // Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG.
+// Inner tolerance of a refinement step at outer residual rel: inner_rtol, relaxed when
+// less is enough to reach rtol (the last correction: 0.25 rtol / rel, at most 0.5)
+double inner_tol(double inner_rtol, double rtol, double rel) {
+  const double need = rel > 0.0 ? 0.25 * rtol / rel : inner_rtol;
+  return need > inner_rtol ? (need < 0.5 ? need : 0.5) : inner_rtol;
+}
+
 int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_outer, double inner_rtol,
                 int inner_maxit, int precond, fepa_refine_stats* stats) {
   TRY(check_solve_args(op, b, x, rtol, max_outer, precond));
@@ -798,10 +805,10 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     bnorm = sqrt(href.bb);
     rel = href.bb > 0 ? sqrt(href.rr / href.bb) : 0.0;
     if (rel <= rtol || outer >= max_outer) break;
-    // FP32 correction: A e = r with relative tolerance inner_rtol
+    // FP32 correction: A e = r with relative tolerance inner_rtol (relaxed on the last step)
+    const double tol = inner_tol(inner_rtol, rtol, rel);
     cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
-                                                    (float*)L.h, invd, L.st, inner_rtol * inner_rtol, inner_maxit,
-                                                    L.partials);
+                                                    (float*)L.h, invd, L.st, tol * tol, inner_maxit, L.partials);
     LAUNCH_CHECK();
     CgState hin;
     TRY(run_loop(op, L, precond, body, &hin));
@@ -821,6 +828,90 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
   if (rel > rtol)
     return fail(FEPA_ERR_NOCONV, "refinement did not reach rtol %.3g in %d outer steps (rel. residual %.3e)", rtol,
                 outer, rel);
+  return FEPA_OK;
+}
+
+// Mixed-precision CG with reliable updates (residual replacement): one FP32 Jacobi-PCG
+// recurrence whose residual is replaced by the FP64 residual b - A x each time it has
+// fallen by delta, the FP32 iterate being added to the FP64 x first.  Unlike the
+// restarted refinement, the direction and the scalars carry over (cg32_replace), so the
+// Krylov space is not thrown away at each correction.
+int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double delta, int maxit, int precond,
+                 fepa_refine_stats* stats) {
+  TRY(check_solve_args(op, b, x, rtol, maxit, precond));
+  if (!(delta > 0.0 && delta < 1.0)) return fail(FEPA_ERR_ARG, "delta must be in (0, 1)");
+  CgLoop& L = op->cg32;
+  TRY(ensure_loop<float>(op, L, true));
+  TRY(ensure_f32(op));
+  if (!op->h64) {
+    TRY(dalloc(&op->h64, op->N));
+    TRY(dalloc(&op->st_ref, 1));
+    TRY(dalloc(&op->partials_ref, 2 * (size_t)L.red_blocks));
+    CUDA_TRY(cudaMemsetAsync(op->st_ref, 0, sizeof(CgState), op->stream));
+  }
+  cudaStream_t s = op->stream;
+  if (precond) {
+    TRY(ensure_inv_diag(op));
+    if (!op->inv32_valid) {
+      to_f32<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, op->inv_diag, (float*)L.invd);
+      LAUNCH_CHECK();
+      op->inv32_valid = true;
+    }
+  }
+  const float* invd = precond ? (const float*)L.invd : nullptr;
+  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond, int use_cond) {
+    return body32(op, L, invd, bs, cond, use_cond);
+  };
+  auto residual = [&](double* rel, double* bb) -> int {  // FP64 r = b - A x into the FP32 loop's r
+    CUDA_TRY(cudaMemsetAsync(op->h64, 0, op->N * sizeof(double), s));
+    TRY(launch_apply(op, x, op->h64, nullptr, s));
+    refine_residual<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, b, op->h64, (float*)L.r, op->st_ref,
+                                                          op->partials_ref);
+    LAUNCH_CHECK();
+    CUDA_TRY(cudaMemcpyAsync(op->st_host, op->st_ref, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *bb = op->st_host->bb;
+    *rel = op->st_host->bb > 0 ? sqrt(op->st_host->rr / op->st_host->bb) : 0.0;
+    return FEPA_OK;
+  };
+  double rel = 0.0, bb = 0.0;
+  TRY(residual(&rel, &bb));
+  const double rr0 = rel * rel * bb;
+  const double floor2 = 0.25 * rtol * rtol * bb;  // a segment need not go below half the target
+  int replacements = 0, iters = 0;
+  if (rel > rtol) {
+    const double first = rr0 > 0.0 && floor2 / rr0 > delta * delta ? floor2 / rr0 : delta * delta;
+    cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
+                                                    (float*)L.h, invd, L.st, first, maxit, L.partials);
+    LAUNCH_CHECK();
+    for (;;) {
+      CgState hin;
+      TRY(run_loop(op, L, precond, body, &hin));
+      iters = hin.iter;
+      refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
+      LAUNCH_CHECK();
+      TRY(residual(&rel, &bb));
+      if (rel <= rtol || iters >= maxit) break;
+      cg32_replace<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, invd, L.st,
+                                                         delta * delta, floor2, L.partials);
+      LAUNCH_CHECK();
+      cg32_direction<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.d, (float*)L.h, invd,
+                                                          L.st, 0, 0);
+      LAUNCH_CHECK();
+      ++replacements;
+    }
+  }
+  TRY(check_err(op));
+  if (stats) {
+    stats->outer_iterations = replacements;
+    stats->inner_iterations = iters;
+    stats->rel_residual = rel;
+    stats->b_norm = sqrt(bb);
+    stats->status = rel <= rtol ? FEPA_OK : FEPA_ERR_NOCONV;
+  }
+  if (rel > rtol)
+    return fail(FEPA_ERR_NOCONV, "reliable-update CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)",
+                rtol, iters, rel);
   return FEPA_OK;
 }
 
@@ -1152,6 +1243,18 @@ int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, i
 int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int32_t max_outer, double inner_rtol,
                        int32_t inner_maxit, int32_t precond, fepa_refine_stats* stats) {
   return run_refined(op, b, x, rtol, max_outer, inner_rtol, inner_maxit, precond, stats);
+}
+
+int fepa_solve_reliable(fepa_op* op, const double* b, double* x, double rtol, double delta, int32_t maxit,
+                        int32_t precond, fepa_refine_stats* stats) {
+  return run_reliable(op, b, x, rtol, delta, maxit, precond, stats);
+}
+
+int fepa_solve_reliable_host(fepa_op* op, const double* b_host, double* x_host, double rtol, double delta,
+                             int32_t maxit, int32_t precond, fepa_refine_stats* stats) {
+  return host_solve(op, b_host, x_host, [&](const double* b, double* x) {
+    return run_reliable(op, b, x, rtol, delta, maxit, precond, stats);
+  });
 }
 
 int fepa_solve_refined_host(fepa_op* op, const double* b_host, double* x_host, double rtol, int32_t max_outer,

@@ -97,6 +97,110 @@ __global__ void mg_restrict(int E, int nf, int nc, const int* __restrict__ gf, c
   }
 }
 
+// Compiled transfers for one (fine, coarse) node count pair: several elements per block
+// (NF^2 threads each), sizes known at compile time so every contraction unrolls.
+template <int NF, int NC>
+struct XferShape {
+  static constexpr int TPE = NF * NF;
+  static constexpr int NEB = (256 / TPE) > 0 ? (256 / TPE) : 1;
+  static constexpr int THREADS = NEB * TPE;
+};
+
+// xf = P xc (as mg_prolong), elements blockIdx.x * NEB + threadIdx.x / NF^2
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(XferShape<NF, NC>::THREADS)
+mg_prolong_t(int E, const int* __restrict__ gf, const int* __restrict__ gc, const T* __restrict__ I,
+             const T* __restrict__ xc, T* __restrict__ xf) {
+  using S = XferShape<NF, NC>;
+  constexpr int TPE = S::TPE, NEB = S::NEB, NC3 = NC * NC * NC, NF3 = NF * NF * NF;
+  __shared__ T sI[NF * NC];
+  __shared__ T s0[NEB][NF3];
+  __shared__ T s1[NEB][NF * NC * NC];
+  const int el = threadIdx.x / TPE, t = threadIdx.x - el * TPE;
+  const int64_t e = (int64_t)blockIdx.x * NEB + el;
+  const bool live = e < E;
+  for (int k = threadIdx.x; k < NF * NC; k += S::THREADS) sI[k] = I[k];
+  if (live)
+    for (int k = t; k < NC3; k += TPE) s0[el][k] = xc[gmap_dof(gc[e * NC3 + k])];
+  __syncthreads();
+  if (live)
+    for (int w = t; w < NF * NC * NC; w += TPE) {  // x: [c][b][a']
+      const int a = w % NF, cb = w / NF;
+      T v = T(0);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) v += sI[a * NC + i] * s0[el][cb * NC + i];
+      s1[el][w] = v;
+    }
+  __syncthreads();
+  if (live)
+    for (int w = t; w < NF * NF * NC; w += TPE) {  // y: [c][b'][a']
+      const int a = w % NF, b = (w / NF) % NF, c = w / (NF * NF);
+      T v = T(0);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) v += sI[b * NC + j] * s1[el][(c * NC + j) * NF + a];
+      s0[el][w] = v;
+    }
+  __syncthreads();
+  if (live)
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {  // z: thread (a', b') writes its column
+      T v = T(0);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) v += sI[c * NC + k] * s0[el][k * NF * NF + t];
+      xf[gmap_dof(gf[e * NF3 + c * NF * NF + t])] = v;
+    }
+}
+
+// rc += P^T rf (as mg_restrict)
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(XferShape<NF, NC>::THREADS)
+mg_restrict_t(int E, const int* __restrict__ gf, const int* __restrict__ gc, const T* __restrict__ I,
+              const T* __restrict__ inv_mult, const T* __restrict__ rf, T* __restrict__ rc) {
+  using S = XferShape<NF, NC>;
+  constexpr int TPE = S::TPE, NEB = S::NEB, NC3 = NC * NC * NC, NF3 = NF * NF * NF;
+  __shared__ T sI[NF * NC];
+  __shared__ T s0[NEB][NF * NF * NC];
+  __shared__ T s1[NEB][NF * NC * NC];
+  const int el = threadIdx.x / TPE, t = threadIdx.x - el * TPE;
+  const int64_t e = (int64_t)blockIdx.x * NEB + el;
+  const bool live = e < E;
+  for (int k = threadIdx.x; k < NF * NC; k += S::THREADS) sI[k] = I[k];
+  __syncthreads();
+  if (live) {  // z^T straight from the fine values: thread (a', b') reads its column
+    T col[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+      const int g = gf[e * NF3 + c * NF * NF + t];
+      col[c] = g >= 0 ? rf[g] * inv_mult[g] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      T v = T(0);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) v += sI[c * NC + k] * col[c];
+      s0[el][k * NF * NF + t] = v;
+    }
+  }
+  __syncthreads();
+  if (live)
+    for (int w = t; w < NC * NC * NF; w += TPE) {  // y^T: [k][j][a']
+      const int a = w % NF, j = (w / NF) % NC, k = w / (NF * NC);
+      T v = T(0);
+#pragma unroll
+      for (int b = 0; b < NF; ++b) v += sI[b * NC + j] * s0[el][(k * NF + b) * NF + a];
+      s1[el][w] = v;
+    }
+  __syncthreads();
+  if (live)
+    for (int w = t; w < NC3; w += TPE) {  // x^T: [k][j][i] -> coarse DOFs
+      const int i = w % NC, kj = w / NC;
+      T v = T(0);
+#pragma unroll
+      for (int a = 0; a < NF; ++a) v += sI[a * NC + i] * s1[el][kj * NF + a];
+      atomicAdd(rc + gmap_dof(gc[e * NC3 + w]), v);
+    }
+}
+
 // 1 / (number of elements holding each DOF) on a structured node grid
 template <typename T>
 __global__ void mg_inv_multiplicity(int nx, int ny, int nz, int p, T* __restrict__ out) {
@@ -182,12 +286,15 @@ __global__ void hash_fill(int64_t N, T* __restrict__ v) {
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
 dot2(int64_t N, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ w, double* __restrict__ out) {
-  double v[2] = {0.0, 0.0};
+  // per-thread partial sums in T (FP32 for an FP32 V-cycle: the eigenvalue estimate needs
+  // a few digits, and FP64 products would run on the slow FP64 pipe), block sums in FP64
+  T p0 = T(0), p1 = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ai = (double)a[i];
-    v[0] += ai * (double)b[i];
-    v[1] += w ? ai * ai / (double)w[i] : ai * ai;   // w = 1/diag: (a, D a)
+    const T ai = a[i];
+    p0 += ai * b[i];
+    p1 += w ? ai * ai / w[i] : ai * ai;   // w = 1/diag: (a, D a)
   }
+  double v[2] = {(double)p0, (double)p1};
   double blk[2];
   block_sum<2>(v, blk);
   if (threadIdx.x == 0) {
@@ -201,6 +308,20 @@ template <typename T>
 __global__ void scaled_jacobi(int64_t N, T s, const T* __restrict__ invd, const T* __restrict__ h, T* __restrict__ v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = s * invd[i] * h[i];
+}
+
+// Power-iteration step without a host round trip: lambda = dots[0] / dots[1] (the
+// Rayleigh quotient just reduced), v = D^{-1} h / lambda, h = 0 for the next product,
+// and the other dot pair cleared for the next reduction.
+template <typename T>
+__global__ void power_step(int64_t N, const double* __restrict__ dots, double* __restrict__ next,
+                           const T* __restrict__ invd, T* __restrict__ h, T* __restrict__ v) {
+  const T s = (T)(dots[1] / dots[0]);
+  if (blockIdx.x == 0 && threadIdx.x < 2) next[threadIdx.x] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    v[i] = s * invd[i] * h[i];
+    h[i] = T(0);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -98,6 +98,8 @@ SIGNATURES = [
     ("fepa_cg_solve_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_iterations", ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_solve_refined", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
+    ("fepa_solve_reliable", ctypes.c_int, [_P, _P, _P, _D, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
+    ("fepa_solve_reliable_host", ctypes.c_int, [_P, _P, _P, _D, _D, _I32, _I32, ctypes.POINTER(RefineStats)]),
     ("fepa_solve_refined_host", ctypes.c_int, [_P, _P, _P, _D, _I32, _D, _I32, _I32,
                                                ctypes.POINTER(RefineStats)]),
     ("fepa_solver_start", ctypes.c_int, [_P, _I32, _P, _P, _D, _I32, _I32, _D, _I32]),
@@ -389,6 +391,33 @@ class Operator:
                                                  x.ctypes.data_as(ctypes.c_void_p), float(rtol), int(max_outer),
                                                  float(inner_rtol), int(inner_maxit), _PRECONDS[precond],
                                                  ctypes.byref(st)))
+        return x, st.as_dict()
+
+    def solve_reliable(self, b, x=None, rtol=1e-10, delta=0.03, maxit=20000, precond="jacobi",
+                       raise_on_noconv=True):
+        """Mixed-precision CG with reliable updates: one FP32 recurrence, its residual
+        replaced by the FP64 residual each time it falls by delta (Krylov space kept)."""
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = RefineStats()
+        self._sync_stream()
+        rc = self._lib.fepa_solve_reliable(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                           _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), float(delta),
+                                           int(maxit), _PRECONDS[precond], ctypes.byref(st))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        return x, st.as_dict()
+
+    def solve_reliable_host(self, b, x=None, rtol=1e-10, delta=0.03, maxit=20000, precond="jacobi"):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.N) if x is None else x
+        if b.shape != (self.N,) or x.shape != (self.N,) or x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("b and x must be contiguous float64 arrays of length N")
+        st = RefineStats()
+        self._sync_stream()
+        _check(self._lib.fepa_solve_reliable_host(self._h, b.ctypes.data_as(ctypes.c_void_p),
+                                                  x.ctypes.data_as(ctypes.c_void_p), float(rtol), float(delta),
+                                                  int(maxit), _PRECONDS[precond], ctypes.byref(st)))
         return x, st.as_dict()
 
     # -- resumable solve (continuous batching)

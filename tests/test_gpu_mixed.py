@@ -182,3 +182,52 @@ def test_refined_full_size_sampled(p, n):
     assert np.max(np.abs(bh[rows] - Ax)) <= 1e-10 * np.linalg.norm(bh)
     x64, s64 = op.solve(b, rtol=1e-12, maxit=20000)
     assert rel(xh, x64.cpu().numpy()) <= 1e-9
+
+
+# ---------------------------------------------------------------- reliable updates
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 2, (4, 4, 4)), ("diffusion", 4, (3, 3, 3)),
+                                          ("diffusion", 6, (2, 2, 2)), ("mass", 3, (3, 4, 2)),
+                                          ("diffusion", 8, (2, 1, 2))])
+def test_reliable_solution_matches_oracle(form, p, shape):
+    op, mesh = make(shape, p, form, seed=41)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    if form == "diffusion":
+        op.set_essential(prob.ess.astype(np.int32))
+        b = op.rhs_sine(3 * math.pi ** 2)
+        bo = prob.sine_rhs()
+    else:
+        bo = FI.uniform_vector(op.N, seed=42)
+        b = torch.from_numpy(bo).cuda()
+    x, st = op.solve_reliable(b, rtol=1e-12, delta=0.1)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-12
+    xo, _, _ = prob.solve(bo, rtol=1e-14)
+    assert rel(x.cpu().numpy(), xo) <= 1e-10
+
+
+@pytest.mark.parametrize("delta", [0.3, 0.1, 0.01])
+def test_reliable_keeps_the_krylov_space(delta):
+    """With the direction carried over each replacement, the FP32 iteration count stays
+    near the FP64 CG's (the restarted refinement needs several times more here)."""
+    op, _ = make((8, 8, 8), 3, "diffusion", seed=46)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(3 * math.pi ** 2)
+    x64, s64 = op.solve(b, rtol=1e-10)
+    x, st = op.solve_reliable(b, rtol=1e-10, delta=delta)
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-10 and st["outer_iterations"] >= 1
+    assert st["inner_iterations"] <= 1.3 * s64["iterations"] + 10
+    assert rel(x.cpu().numpy(), x64.cpu().numpy()) <= 1e-8
+    xh, sh = op.solve_reliable_host(b.cpu().numpy(), rtol=1e-10, delta=delta)
+    assert abs(sh["inner_iterations"] - st["inner_iterations"]) <= 2
+    assert rel(xh, x.cpu().numpy()) <= 1e-9
+
+
+def test_reliable_noconv_and_arguments():
+    op, _ = make((4, 4, 4), 2, "diffusion", seed=44)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    x, st = op.solve_reliable(b, rtol=1e-14, maxit=5, raise_on_noconv=False)
+    assert st["status"] == -5 and st["inner_iterations"] >= 5
+    for bad in (0.0, 1.0, -0.5):
+        with pytest.raises(Exception):
+            op.solve_reliable(b, delta=bad)
