@@ -24,6 +24,7 @@
 #include "pa_kernels.cuh"
 #include "pa_tma_f32.cuh"
 #include "pa_df64.cuh"
+#include "geom_df.cuh"
 #include "batch_kernels.cuh"
 #include "mg_kernels.cuh"
 
@@ -104,13 +105,15 @@ struct KernelSet {
   ApplyFn<double> apply;
   ApplyDfFn apply_df;
   int df_smem, df_ne;
+  void (*diag_df)(int, const int*, const float2*, double*);
+  int diag_df_smem, diag_df_ne;
+  void (*rhs_df)(int, int, int, const float2*, const int*, const double*, double, double*);
+  int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
-  void (*rhs)(int, int, const double*, const int*, const double*, const double*, const double*, const double*,
-              double, double*);
   int apply_smem, apply_tpe, apply_ne;
   int d32_stride;
-  int diag_smem, rhs_smem;
+  int diag_smem;
 };
 
 template <int P, int Q, bool DIFF>
@@ -120,6 +123,12 @@ KernelSet make_set() {
   k.apply_df = pa_apply_df<P, Q, DIFF>;
   k.df_smem = DfShape<P, Q, DIFF>::SMEM;
   k.df_ne = DfShape<P, Q, DIFF>::NE;
+  k.diag_df = pa_diag_df<P, Q, DIFF>;
+  k.diag_df_smem = DiagDfShape<P, Q, DIFF>::SMEM;
+  k.diag_df_ne = DiagDfShape<P, Q, DIFF>::NE;
+  k.rhs_df = pa_rhs_df<P, Q>;
+  k.rhs_df_smem = RhsDfShape<P, Q>::SMEM;
+  k.rhs_df_ne = RhsDfShape<P, Q>::NE;
   k.v32[0] = {pa_apply_f32_tma<P, Q, DIFF, true, 1>, TmaShape<P, Q, DIFF, true, 1>::SMEM,
               TmaShape<P, Q, DIFF, true, 1>::NE, TmaShape<P, Q, DIFF, true, 1>::NE, false};
   k.v32[1] = {pa_apply_f32_tma<P, Q, DIFF, false, 1>, TmaShape<P, Q, DIFF, false, 1>::SMEM,
@@ -130,13 +139,11 @@ KernelSet make_set() {
               PipeShape<P, Q, DIFF>::NE, true};
 
   k.diag = pa_diag_f64<P, Q, DIFF>;
-  k.rhs = pa_rhs_f64<P, Q>;
   k.apply_smem = PaShape<double, P, Q, DIFF>::SMEM;
   k.apply_tpe = PaShape<double, P, Q, DIFF>::TPE;
   k.apply_ne = PaShape<double, P, Q, DIFF>::NE;
   k.d32_stride = TmaShape<P, Q, DIFF>::DSTRIDE;
   k.diag_smem = DiagShape<P, Q, DIFF>::SMEM;
-  k.rhs_smem = RhsShape<P, Q>::SMEM;
   return k;
 }
 
@@ -185,6 +192,22 @@ int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vec
   return FEPA_OK;
 }
 
+// Gauss points and weights of q as (hi, lo) float pairs (long double on the host), into
+// the constant-memory slot of q for the double-float geometry
+int upload_gauss_df(int q, const std::vector<long double>& x, const std::vector<long double>& w, cudaStream_t s) {
+  std::vector<float> t(2 * GQ_MAX * 2, 0.f);
+  for (int i = 0; i < q; ++i) {
+    const float xh = (float)x[i], wh = (float)w[i];
+    t[2 * i] = xh;
+    t[2 * i + 1] = (float)(x[i] - (long double)xh);
+    t[2 * (GQ_MAX + i)] = wh;
+    t[2 * (GQ_MAX + i) + 1] = (float)(w[i] - (long double)wh);
+  }
+  CUDA_TRY(cudaMemcpyToSymbolAsync(c_gauss_df, t.data(), t.size() * sizeof(float),
+                                   (size_t)q * 2 * GQ_MAX * 2 * sizeof(float), cudaMemcpyHostToDevice, s));
+  return FEPA_OK;
+}
+
 int allow_smem(const void* fn, int bytes) {
   if (bytes > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   return FEPA_OK;
@@ -217,6 +240,7 @@ struct fepa_op {
   std::vector<double> verts_host;  // host copy of the vertex grid (for derived ops, e.g. multigrid levels)
   // device arrays owned by the op
   double* verts = nullptr;
+  float2* verts_df = nullptr;  // the vertices as (hi, lo) float pairs (double-float geometry)
   int* gmap = nullptr;
   double* qd = nullptr;
   double* B = nullptr;
@@ -276,7 +300,7 @@ void free_op(fepa_op* op) {
   cudaStreamSynchronize(op->stream);
   free_loop(op->cg64);
   free_loop(op->cg32);
-  for (void* p : {(void*)op->verts, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
+  for (void* p : {(void*)op->verts, (void*)op->verts_df, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
                   (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->qddf, (void*)op->err,
                   (void*)op->inv_diag, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->h64,
                   (void*)op->st_ref, (void*)op->partials_ref})
@@ -403,9 +427,19 @@ int ensure_loop(fepa_op* op, CgLoop& L, bool own_x) {
   return ensure_host_state(op);
 }
 
-int compute_diagonal(fepa_op* op, double* out, cudaStream_t s) {
+// diag(A) into out: in double-float when that is the op's FP64 arithmetic (and its D copy
+// is current), else with the FP64 kernel.  prepare: the variant may be chosen (timed)
+// and the D copy built here; the allocation-free solve passes false.
+int compute_diagonal(fepa_op* op, double* out, cudaStream_t s, bool prepare = true) {
+  if (prepare) TRY(prepare_f64(op));
   CUDA_TRY(cudaMemsetAsync(out, 0, op->N * sizeof(double), s));
-  op->ks.diag<<<(int)op->E, op->q * op->q, op->ks.diag_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, out);
+  const KernelSet& k = op->ks;
+  if (op->v64 == 1 && op->qddf_valid) {
+    const int grid = (int)((op->E + k.diag_df_ne - 1) / k.diag_df_ne);
+    k.diag_df<<<grid, dim3(op->q * op->q, k.diag_df_ne), k.diag_df_smem, s>>>((int)op->E, op->gmap, op->qddf, out);
+  } else {
+    k.diag<<<(int)op->E, op->q * op->q, k.diag_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, out);
+  }
   LAUNCH_CHECK();
   return FEPA_OK;
 }
@@ -614,6 +648,49 @@ int ensure_f32(fepa_op* op) {
     op->qd32_valid = true;
   }
   if (op->v32 < 0) TRY(choose_variant32(op));
+  return FEPA_OK;
+}
+
+// D from the vertices (double-float geometry kernel), also refreshing the (hi, lo) and
+// FP32 copies of D when they exist.  Sets op->flag if a det J <= 0.
+template <int Q>
+void launch_geom_q(int nx, int ny, int nz, const float2* vdf, int diffusion, double* qd, float2* qddf, float* qd32,
+                   int d32stride, int* bad, cudaStream_t s) {
+  using G = GeoShape<Q>;
+  const int64_t E = (int64_t)nx * ny * nz;
+  const int grid = (int)((E + G::NE - 1) / G::NE);
+  geom_df<Q><<<grid, dim3(G::TPE, G::NE), 0, s>>>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad);
+}
+
+// the geometry kernel of q (2..10); false if q has none
+bool launch_geom(int q, int nx, int ny, int nz, const float2* vdf, int diffusion, double* qd, float2* qddf,
+                 float* qd32, int d32stride, int* bad, cudaStream_t s) {
+  switch (q) {
+    case 2: launch_geom_q<2>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 3: launch_geom_q<3>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 4: launch_geom_q<4>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 5: launch_geom_q<5>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 6: launch_geom_q<6>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 7: launch_geom_q<7>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 8: launch_geom_q<8>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 9: launch_geom_q<9>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    case 10: launch_geom_q<10>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    default: return false;
+  }
+}
+
+int compute_geometry(fepa_op* op) {
+  cudaStream_t s = op->stream;
+  const int64_t nv3 = 3 * (int64_t)(op->nx + 1) * (op->ny + 1) * (op->nz + 1);
+  if (!op->verts_df) TRY(dalloc(&op->verts_df, nv3));
+  split_pairs<<<grid_for(nv3, 256, 148 * 8), 256, 0, s>>>(nv3, op->verts, op->verts_df);
+  LAUNCH_CHECK();
+  if (!launch_geom(op->q, op->nx, op->ny, op->nz, op->verts_df, op->form == FEPA_DIFFUSION, op->qd, op->qddf,
+                   op->qd32, op->ks.d32_stride, op->flag, s))
+    return fail(FEPA_ERR_UNSUPPORTED, "q1d %d has no geometry kernel", op->q);
+  LAUNCH_CHECK();
+  op->qddf_valid = op->qddf != nullptr;
+  op->qd32_valid = op->qd32 != nullptr;
   return FEPA_OK;
 }
 
@@ -973,8 +1050,9 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   int rc;
   if ((rc = allow_smem((const void*)op->ks.apply, op->ks.apply_smem)) ||
       (rc = allow_smem((const void*)op->ks.apply_df, op->ks.df_smem)) ||
+      (rc = allow_smem((const void*)op->ks.diag_df, op->ks.diag_df_smem)) ||
       (rc = allow_smem((const void*)op->ks.diag, op->ks.diag_smem)) ||
-      (rc = allow_smem((const void*)op->ks.rhs, op->ks.rhs_smem)))
+      (rc = allow_smem((const void*)op->ks.rhs_df, op->ks.rhs_df_smem)))
     return bail(rc);
 
   // host tables
@@ -1013,9 +1091,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   CREATE_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
   build_gmap<<<grid_for(E * n * n * n, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, p, 0, op->gmap);
   g_launches.fetch_add(1);
-  geom_qdata<<<grid_for(E * q3, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, q, op->verts, op->pts, op->wts,
-                                                              form == FEPA_DIFFUSION, op->qd, op->flag);
-  g_launches.fetch_add(1);
+  if ((rc = upload_gauss_df(q, gx, gw, s)) || (rc = compute_geometry(op))) return bail(rc);
   CREATE_TRY(cudaGetLastError());
   CREATE_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CREATE_TRY(cudaStreamSynchronize(s));
@@ -1029,7 +1105,6 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
   if (!op || !vertices) return fail(FEPA_ERR_ARG, "null argument");
   cudaStream_t s = op->stream;
   const int64_t nv = (int64_t)(op->nx + 1) * (op->ny + 1) * (op->nz + 1);
-  const int64_t q3 = (int64_t)op->q * op->q * op->q;
   CUDA_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double),
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   if (on_device) {
@@ -1039,13 +1114,9 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
     op->verts_host.assign(vertices, vertices + 3 * nv);
   }
   CUDA_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
-  geom_qdata<<<grid_for(op->E * q3, 256, 148 * 32), 256, 0, s>>>(op->nx, op->ny, op->nz, op->q, op->verts, op->pts,
-                                                                  op->wts, op->form == FEPA_DIFFUSION, op->qd, op->flag);
-  LAUNCH_CHECK();
+  TRY(compute_geometry(op));  // refreshes D and its existing copies
   op->inv_diag_valid = false;
   op->inv32_valid = false;
-  op->qd32_valid = false;
-  op->qddf_valid = false;
   CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
@@ -1199,11 +1270,15 @@ int fepa_op_diagonal(fepa_op* op, double* diag) {
   return compute_diagonal(op, diag, op->stream);
 }
 
+// load vector in double-float (FP64-accurate; the FP64 pipe would spend ~90 % of the time
+// on the three FP64 sines per point)
 static int rhs_common(fepa_op* op, const double* f_qp, double scale, double* b) {
   cudaStream_t s = op->stream;
   CUDA_TRY(cudaMemsetAsync(b, 0, op->N * sizeof(double), s));
-  op->ks.rhs<<<(int)op->E, op->q * op->q, op->ks.rhs_smem, s>>>(op->nx, op->ny, op->verts, op->gmap, op->pts, op->wts,
-                                                                 op->B, f_qp, scale, b);
+  const KernelSet& k = op->ks;
+  const int grid = (int)((op->E + k.rhs_df_ne - 1) / k.rhs_df_ne);
+  k.rhs_df<<<grid, dim3(op->q * op->q, k.rhs_df_ne), k.rhs_df_smem, s>>>(op->nx, op->ny, op->nz, op->verts_df,
+                                                                         op->gmap, f_qp, scale, b);
   LAUNCH_CHECK();
   return FEPA_OK;
 }
@@ -1333,7 +1408,7 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
   // the array holds whatever the previous call left: reset the scalars and ticket
   CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(CgState), s));
   if (precond) {
-    TRY(compute_diagonal(op, invd, s));  // zeroes invd, then sums the element diagonals
+    TRY(compute_diagonal(op, invd, s, false));  // zeroes invd, then sums the element diagonals
     reciprocal<<<grid_for(N, 256, 148 * 16), 256, 0, s>>>(N, invd, invd);
     LAUNCH_CHECK();
   }

@@ -53,10 +53,43 @@ __device__ __forceinline__ void df_fma(dfl& acc, dfl t, dfl x) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
 }
 
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// a * b (Dekker's product with the exact FMA split of the high words; cross terms by FMA)
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float s = __fadd_rn(p, e);
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+// a + b (TwoSum of the high words, low words added, renormalised: Dekker's addition;
+// absolute error ~2^-48 (|a| + |b|))
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bv = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
+  const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float r = __fadd_rn(s, t);
+  return {r, __fsub_rn(t, __fsub_rn(r, s))};
+}
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
 // renormalise so that |lo| <= ulp(hi)/2 (Fast2Sum; valid as |lo| is far below |hi|)
 __device__ __forceinline__ dfl df_norm(dfl a) {
   const float s = __fadd_rn(a.h, a.l);
   return {s, __fsub_rn(a.l, __fsub_rn(s, a.h))};
+}
+
+// 1 / b: the correctly rounded float reciprocal of the high word refined by one Newton
+// step carried in double-float (r = r0 + r0 (1 - b r0)); relative error ~2^-46
+__device__ __forceinline__ dfl df_recip(dfl b) {
+  const float r0 = __frcp_rn(b.h);
+  dfl e = {1.f, 0.f};
+  df_fma(e, df_neg(b), dfl{r0, 0.f});  // 1 - b r0, accurately
+  return df_norm(dfl{r0, __fmul_rn(r0, df_norm(e).h)});
 }
 
 // tables of every compiled (P, Q) as (hi, lo) pairs: slot as in c_tab32
@@ -321,6 +354,105 @@ __global__ void split_to_df(int64_t count, const double* __restrict__ qd, float2
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
     const dfl v = df_from(qd[t]);
     out[t] = make_float2(v.h, v.l);
+  }
+}
+
+}  // namespace fepa
+
+namespace fepa {
+
+// ---------------------------------------------------------------------------
+// diag(A) in double-float (the matrix-free diagonal of Sec. 2.1 by sum factorisation):
+// diag(a,b,c) = sum_m wt_m sum_{i,j,k} X_m[i][a] Y_m[j][b] Z_m[k][c] D_m(i,j,k), the
+// 1D tables being products B B, B G or G G per direction and component (mass: B B in
+// every direction).  Same stages as the FP64 kernel (z in registers, then y and x
+// through shared memory), several elements per block, D read as (hi, lo) pairs.
+// ---------------------------------------------------------------------------
+template <int P, int Q, bool DIFF>
+struct DiagDfShape {
+  static constexpr int N = P + 1, NC = DIFF ? 6 : 1, TPE = Q * Q;
+  static constexpr int PER = NC * N * Q * Q + NC * N * N * Q;  // T1 + T2 values per element
+  static constexpr int NE0 = (256 / TPE) > 0 ? (256 / TPE) : 1;
+  static constexpr int NE = (NE0 * PER * 8 > 160 * 1024) ? ((160 * 1024) / (PER * 8) > 0 ? (160 * 1024) / (PER * 8) : 1)
+                                                          : NE0;
+  static constexpr int SMEM = (3 * Q * N + NE * PER) * 8;
+};
+
+template <int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(DiagDfShape<P, Q, DIFF>::TPE * DiagDfShape<P, Q, DIFF>::NE)
+pa_diag_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, double* __restrict__ diag) {
+  using S = DiagDfShape<P, Q, DIFF>;
+  using T = TabDf<P, Q>;
+  constexpr int n = S::N, NC = S::NC, TPE = S::TPE, NE = S::NE, Q3 = Q * Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_dg[];
+  dfl* tab = reinterpret_cast<dfl*>(smem_dg);  // [3][Q][n]: B B, B G, G G
+  const int tid = threadIdx.x, el = threadIdx.y, flat = el * TPE + tid;
+  for (int l = flat; l < Q * n; l += TPE * NE) {
+    const int i = l / n, a = l - i * n;
+    const dfl b = T::B(i, a), g = T::G(i, a);
+    tab[l] = df_mul(b, b);
+    tab[Q * n + l] = df_mul(b, g);
+    tab[2 * Q * n + l] = df_mul(g, g);
+  }
+  dfl* T1 = tab + 3 * Q * n + el * S::PER;  // [m][c][j][i]
+  dfl* T2 = T1 + NC * n * TPE;              // [m][c][b][i]
+  const int64_t e = (int64_t)blockIdx.x * NE + el;
+  const bool live = e < E;
+  __syncthreads();
+  // table per direction and component (xx, xy, xz, yy, yz, zz): 0 BB, 1 BG, 2 GG
+  constexpr int selx[6] = {2, 1, 1, 0, 0, 0}, sely[6] = {0, 1, 0, 2, 1, 0}, selz[6] = {0, 0, 1, 0, 1, 2};
+  if (live) {  // z
+    const float2* de = qd + e * NC * Q3 + tid;
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const dfl* Z = tab + (DIFF ? selz[m] : 0) * Q * n;
+      dfl acc[n];
+#pragma unroll
+      for (int c = 0; c < n; ++c) acc[c] = df_zero();
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const dfl dv = df_ld(de + m * Q3 + k * TPE);
+#pragma unroll
+        for (int c = 0; c < n; ++c) df_fma(acc[c], dv, Z[k * n + c]);
+      }
+#pragma unroll
+      for (int c = 0; c < n; ++c) T1[(m * n + c) * TPE + tid] = df_norm(acc[c]);
+    }
+  }
+  __syncthreads();
+  if (live)  // y
+    for (int w = tid; w < NC * n * n * Q; w += TPE) {
+      const int i = w % Q, b = (w / Q) % n, mc = w / (n * Q), m = mc / n;
+      const dfl* Y = tab + (DIFF ? sely[m] : 0) * Q * n;
+      const dfl* src = T1 + mc * TPE + i;
+      dfl s = df_zero();
+#pragma unroll
+      for (int j = 0; j < Q; ++j) df_fma(s, src[j * Q], Y[j * n + b]);
+      T2[w] = df_norm(s);
+    }
+  __syncthreads();
+  if (live) {  // x, weights, scatter
+    const int* g = gmap + e * (n * n * n);
+    for (int w = tid; w < n * n * n; w += TPE) {
+      const int a = w % n, cb = w / n;
+      dfl s = df_zero();
+#pragma unroll
+      for (int m = 0; m < NC; ++m) {
+        const dfl* X = tab + (DIFF ? selx[m] : 0) * Q * n;
+        const dfl* src = T2 + (m * n * n + cb) * Q;
+        dfl sm = df_zero();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) df_fma(sm, src[i], X[i * n + a]);
+        sm = df_norm(sm);
+        if (DIFF && (m == 1 || m == 2 || m == 4)) sm = dfl{2.f * sm.h, 2.f * sm.l};  // off-diagonal components
+        s = df_add(s, sm);
+      }
+      const int gi = g[w];
+      if (gi >= 0)
+        atomicAdd(diag + gi, df_to(s));
+      else if (!((~gi) & ESS_SKIP))
+        atomicAdd(diag + (~gi), 1.0);
+    }
   }
 }
 

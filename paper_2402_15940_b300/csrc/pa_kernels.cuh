@@ -1,10 +1,9 @@
 // Partial-assembly kernels, FP64 (arXiv 2402.15940, Fig. fig_feod and Sec. 2.1-2.2).
 //
-//   geom_qdata       D at every quadrature point from the trilinear map (setup, once)
 //   pa_apply         y += G^T B^T D B G x, fused in one kernel per element group
 //   pa_diag          diag(A) by sum factorisation (the matrix-free diagonal of Sec. 2.1)
-//   pa_rhs           b += G^T B^T (w det J f)
 //   qp_coords        physical quadrature points
+// (geometry D and the load vector are computed in double-float: geom_df.cuh)
 //
 // Element -> DOF map ("gmap", the G operator) entries:
 //   g >= 0                      ordinary DOF g
@@ -26,8 +25,9 @@ struct CgState;  // cg_kernels.cuh
 __device__ __forceinline__ int gmap_dof(int g) { return g >= 0 ? g : ((~g) & ESS_MASK); }
 
 // ---------------------------------------------------------------------------
-// geometry: D = w det J (mass) or w adj(J) adj(J)^T / det J (diffusion, 6 comps)
-// qdata layout [e][comp][q^3], point i + q*(j + q*k)
+// D = w det J (mass) or w adj(J) adj(J)^T / det J (diffusion, 6 comps), stored
+// [e][comp][q^3], point i + q*(j + q*k) (computed by geom_df.cuh); the corners of an
+// element, for the quadrature-point coordinates
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void element_corners(const double* __restrict__ verts, int nx, int ny, int64_t e,
                                                 double X[8][3]) {
@@ -38,67 +38,6 @@ __device__ __forceinline__ void element_corners(const double* __restrict__ verts
     X[c][0] = verts[3 * v + 0];
     X[c][1] = verts[3 * v + 1];
     X[c][2] = verts[3 * v + 2];
-  }
-}
-
-// J[d][r] = d x_d / d xi_r of the trilinear map at xi.
-__device__ __forceinline__ void trilinear_jacobian(const double X[8][3], double s, double t, double u, double J[3][3]) {
-#pragma unroll
-  for (int d = 0; d < 3; ++d) J[d][0] = J[d][1] = J[d][2] = 0.0;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const double fs = (c & 1) ? s : 1.0 - s, ft = (c & 2) ? t : 1.0 - t, fu = (c & 4) ? u : 1.0 - u;
-    const double ds = (c & 1) ? 1.0 : -1.0, dt = (c & 2) ? 1.0 : -1.0, du = (c & 4) ? 1.0 : -1.0;
-    const double g0 = ds * ft * fu, g1 = fs * dt * fu, g2 = fs * ft * du;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      J[d][0] += X[c][d] * g0;
-      J[d][1] += X[c][d] * g1;
-      J[d][2] += X[c][d] * g2;
-    }
-  }
-}
-
-__global__ void geom_qdata(int nx, int ny, int nz, int q, const double* __restrict__ verts,
-                           const double* __restrict__ pts, const double* __restrict__ wts, int diffusion,
-                           double* __restrict__ qd, int* __restrict__ bad) {
-  const int64_t q3 = (int64_t)q * q * q;
-  const int64_t total = (int64_t)nx * ny * nz * q3;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = t / q3;
-    const int qp = (int)(t - e * q3);
-    const int i = qp % q, j = (qp / q) % q, k = qp / (q * q);
-    double X[8][3];
-    element_corners(verts, nx, ny, e, X);
-    double J[3][3];
-    trilinear_jacobian(X, pts[i], pts[j], pts[k], J);
-    // adjugate: adj(J) = det(J) J^{-1}
-    double A[3][3];
-    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
-    if (!(det > 0.0)) atomicOr(bad, 1);
-    const double w = wts[i] * wts[j] * wts[k];
-    if (!diffusion) {
-      qd[e * q3 + qp] = w * det;
-    } else {
-      // (J^{-1} J^{-T}) det = adj adj^T / det
-      const double f = w / det;
-      double* o = qd + e * 6 * q3 + qp;
-      o[0 * q3] = f * (A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2]);
-      o[1 * q3] = f * (A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2]);
-      o[2 * q3] = f * (A[0][0] * A[2][0] + A[0][1] * A[2][1] + A[0][2] * A[2][2]);
-      o[3 * q3] = f * (A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2]);
-      o[4 * q3] = f * (A[1][0] * A[2][0] + A[1][1] * A[2][1] + A[1][2] * A[2][2]);
-      o[5 * q3] = f * (A[2][0] * A[2][0] + A[2][1] * A[2][1] + A[2][2] * A[2][2]);
-    }
   }
 }
 
@@ -446,84 +385,6 @@ pa_diag_f64(int E, const int* __restrict__ gmap, const double* __restrict__ qd, 
       atomicAdd(diag + gi, s);
     else if (!((~gi) & ESS_SKIP))
       atomicAdd(diag + (~gi), 1.0);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// load vector: b[g] += sum over points of w det J f phi_g, by the transposed stages
-// f given per point (f_qp) or as scale * sin(pi x) sin(pi y) sin(pi z) (f_qp == nullptr)
-// ---------------------------------------------------------------------------
-template <int P, int Q>
-struct RhsShape {
-  static constexpr int N = P + 1;
-  static constexpr int SMEM = (2 * Q * N + N * Q * Q + N * N * Q) * 8;
-};
-
-template <int P, int Q>
-__global__ void __launch_bounds__(Q * Q)
-pa_rhs_f64(int nx, int ny, const double* __restrict__ verts, const int* __restrict__ gmap,
-           const double* __restrict__ pts, const double* __restrict__ wts, const double* __restrict__ Btab,
-           const double* __restrict__ f_qp, double scale, double* __restrict__ b) {
-  constexpr int n = P + 1, T = Q * Q;
-  extern __shared__ double smem[];
-  double* sB = smem;
-  double* sP = sB + Q * n;  // points and weights
-  double* sW = sP + Q;
-  double* S2 = sW + Q;      // [c][j][i]
-  double* S1 = S2 + n * T;  // [c][b][i]
-  const int tid = threadIdx.x;
-  const int64_t e = blockIdx.x;
-  for (int i = tid; i < Q * n; i += T) sB[i] = Btab[i];
-  for (int i = tid; i < Q; i += T) { sP[i] = pts[i]; sW[i] = wts[i]; }
-  __syncthreads();
-  double X[8][3];
-  element_corners(verts, nx, ny, e, X);
-  {
-    const int i = tid % Q, j = tid / Q;
-    double acc[n];
-#pragma unroll
-    for (int c = 0; c < n; ++c) acc[c] = 0.0;
-    for (int k = 0; k < Q; ++k) {
-      double J[3][3];
-      trilinear_jacobian(X, sP[i], sP[j], sP[k], J);
-      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-      double f;
-      if (f_qp) {
-        f = f_qp[e * (Q * Q * Q) + tid + k * T];
-      } else {
-        double xp[3] = {0.0, 0.0, 0.0};
-        for (int c = 0; c < 8; ++c) {
-          const double N = ((c & 1) ? sP[i] : 1.0 - sP[i]) * ((c & 2) ? sP[j] : 1.0 - sP[j]) *
-                           ((c & 4) ? sP[k] : 1.0 - sP[k]);
-          xp[0] += N * X[c][0];
-          xp[1] += N * X[c][1];
-          xp[2] += N * X[c][2];
-        }
-        f = scale * sinpi(xp[0]) * sinpi(xp[1]) * sinpi(xp[2]);
-      }
-      const double v = sW[i] * sW[j] * sW[k] * det * f;
-#pragma unroll
-      for (int c = 0; c < n; ++c) acc[c] += sB[k * n + c] * v;
-    }
-#pragma unroll
-    for (int c = 0; c < n; ++c) S2[c * T + tid] = acc[c];
-  }
-  __syncthreads();
-  for (int w = tid; w < n * n * Q; w += T) {
-    const int i = w % Q, bb = (w / Q) % n, c = w / (n * Q);
-    double s = 0.0;
-    for (int j = 0; j < Q; ++j) s += sB[j * n + bb] * S2[c * T + j * Q + i];
-    S1[w] = s;
-  }
-  __syncthreads();
-  const int* g = gmap + e * (n * n * n);
-  for (int w = tid; w < n * n * n; w += T) {
-    const int a = w % n, cb = w / n;
-    double s = 0.0;
-    for (int i = 0; i < Q; ++i) s += sB[i * n + a] * S1[cb * Q + i];
-    atomicAdd(b + gmap_dof(g[w]), s);
   }
 }
 

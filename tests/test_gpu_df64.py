@@ -175,3 +175,66 @@ def test_df_full_size_bp3_p4_sampled():
                            [0, op.N - 1, op.N // 2]])
     ref = O.action_rows(mesh, p, p + 2, O.DIFFUSION, x, rows, ess=ess.astype(np.int64))
     assert np.max(np.abs(y[rows] - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
+def test_diagonal_both_kernels_match_oracle(p, form, variant):
+    """diag(A) by the FP64 kernel (variant 0) and by the double-float kernel (variant 1)."""
+    op, mesh = make(SHAPES[p], p, form, seed=13, variant=variant)
+    d = host(op.diagonal())
+    ref = O.diagonal_elementwise(mesh, p, p + 2, form)
+    assert rel(d, ref) <= TOL and np.max(np.abs(d - ref)) <= 10 * TOL * np.max(np.abs(ref))
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    d = host(op.diagonal())
+    assert rel(d, O.diagonal_elementwise(mesh, p, p + 2, form, ess=ess.astype(np.int64))) <= TOL
+    assert np.all(d[ess] == 1.0)
+
+
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p,q", [(1, 2), (2, 3), (3, 5), (4, 6), (6, 7), (8, 10)])
+def test_geometry_matches_oracle_every_q(p, q, form):
+    """D from the double-float geometry kernel for every compiled quadrature size."""
+    shape = SHAPES[p]
+    verts = FI.perturbed_cube_vertices(*shape, seed=p + q)
+    op = F().Operator(*shape, verts, p, form=form, q=q)
+    mesh = O.HexGridMesh(*shape, verts)
+    qd = host(op.qdata())
+    Fq = O.qp_factors(mesh.element_corners(), O.rule(p, q), form)
+    if form == "mass":
+        assert rel(qd[:, 0, :], Fq) <= TOL
+    else:
+        comps = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+        assert rel(qd, np.stack([Fq[:, :, r, s] for r, s in comps], axis=1)) <= TOL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
+def test_load_vector_matches_oracle(p):
+    """b = G^T B^T (w det J f), double-float kernel: f given per point, and the sine
+    manufactured source (the sine evaluated in double-float: reduction to |r| <= 1/4,
+    Taylor series of sin and cos)."""
+    shape = SHAPES[p]
+    op, mesh = make(shape, p, "diffusion", seed=17)
+    f = FI.uniform_vector(op.E * op.q ** 3, seed=18)
+    ref = O.rhs_from_qp(mesh, p, p + 2, f.reshape(op.E, -1))
+    assert rel(host(op.rhs(dev(f))), ref) <= TOL
+    prob = O.Problem(mesh, p, None, O.DIFFUSION, assemble=False)
+    op.set_essential(op.boundary_dofs())
+    for scale in (3 * math.pi ** 2, -0.5):
+        got = host(op.rhs_sine(scale))
+        ref = prob.sine_rhs() * scale / (3 * math.pi ** 2)
+        assert rel(got, ref) <= TOL
+        assert np.max(np.abs(got - ref)) <= 10 * TOL * np.max(np.abs(ref))
+
+
+def test_load_vector_on_a_shifted_mesh():
+    """Coordinates outside [0, 1] (several periods of the sine, negative values): the
+    reduction x = k/2 + r covers every quadrant."""
+    shape, p = (3, 3, 2), 3
+    verts = FI.perturbed_cube_vertices(*shape, seed=4) * 3.0 - 1.3
+    op = F().Operator(*shape, verts, p, form="mass")
+    mesh = O.HexGridMesh(*shape, verts)
+    prob = O.Problem(mesh, p, None, O.MASS, assemble=False)
+    assert rel(host(op.rhs_sine(1.0)), prob.sine_rhs()) <= TOL   # mass: f = u, scale 1
