@@ -210,6 +210,10 @@ def run_ours(args, rank, world, dist):
     q, N, E = op.q, op.N, op.E
     op.set_essential(op.boundary_dofs())
     op.set_cg_mode(args.cg_mode)
+    if args.f32_variant >= 0:   # pin the kernels (e.g. under a profiler, whose timing misleads the autotuner)
+        op.set_f32_variant(args.f32_variant)
+    if args.f64_variant >= 0:
+        op.set_f64_variant(args.f64_variant)
     verts = torch.from_numpy(verts_np).cuda()
     b = torch.empty(N, dtype=torch.float64, device="cuda")
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -348,7 +352,7 @@ def run_ours(args, rank, world, dist):
                                  "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s (2 DFMA/clk/SM x 148 SMs)"}
             op.set_f64_variant(0)           # the DFMA kernel on the same input, for comparison
             t_dfma = kernel_time(prec)
-            op.set_f64_variant(-1)          # back to the measured choice
+            op.set_f64_variant(args.f64_variant)   # back to the measured (or pinned) choice
             r["dfma_kernel"] = {"kernel": f"pa_apply<double,{p},{q},diffusion>", "apply_ms": 1e3 * t_dfma,
                                 "achieved": fl / t_dfma / 1e9, "unit": "GFLOP/s",
                                 "frac_of_fp64_pipe": fl / t_dfma / 1e9 / FP64_PEAK_GFLOPS}
@@ -554,6 +558,8 @@ def main():
                     help="graph: CG loop in one CUDA graph (default); stream: plain launches (for profiling)")
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--delta", type=float, default=0.03, help="reliable-update replacement factor")
+    ap.add_argument("--f32-variant", type=int, default=-1, help="pin the FP32 action's launch shape (-1: autotune)")
+    ap.add_argument("--f64-variant", type=int, default=-1, help="pin the FP64 action (0 DFMA, 1 double-float)")
     ap.add_argument("--no-reliable", dest="reliable", action="store_false",
                     help="skip the reliable-update mixed solve")
     ap.add_argument("--no-multigrid", dest="multigrid", action="store_false",

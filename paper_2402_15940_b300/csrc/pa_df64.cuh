@@ -160,11 +160,24 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   dfl* S1 = sWall + el * L::WORK;
   dfl* S2 = S1 + L::NC1 * L::S1C;
   const int* g = gmap + (e0 + el) * (n * n * n);
-  if (live)
-    for (int l = tid; l < n * n * n; l += TPE) {
-      const int gi = g[l];
-      sX[(l / n) * L::XL + l % n] = gi >= 0 ? df_from(x[gi]) : df_zero();
+  if (live) {
+    // gather: all map loads first, then all x loads, so the dependent pairs overlap
+    constexpr int GR = (n * n * n + TPE - 1) / TPE;
+    int gi[GR];
+    double xv[GR];
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      gi[r] = l < n * n * n ? __ldg(g + l) : -1;
     }
+#pragma unroll
+    for (int r = 0; r < GR; ++r) xv[r] = gi[r] >= 0 ? __ldg(x + gi[r]) : 0.0;
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      if (l < n * n * n) sX[(l / n) * L::XL + l % n] = df_from(xv[r]);
+    }
+  }
   __syncthreads();
 
   // stage 1 (x): line (b,c) -> S1[m][c][b][i]
@@ -232,9 +245,13 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
       if (DIFF) a1[c] = a2[c] = df_zero();
     }
     const float2* dE = qd + (e0 + el) * (L::NC * L::Q3) + tid;
+    // (loading D one point ahead was measured 1-8 % slower here: this kernel is bound by
+    // arithmetic and the registers are better spent on it)
 #pragma unroll KU
     for (int k = 0; k < Q; ++k) {
-      const float2* dk = dE + k * Q * Q;
+      float2 dc[L::NC];
+#pragma unroll
+      for (int m = 0; m < L::NC; ++m) dc[m] = __ldg(dE + k * Q * Q + m * L::Q3);
       if (DIFF) {
         dfl u0 = df_zero(), u1 = df_zero(), u2 = df_zero();
 #pragma unroll
@@ -246,8 +263,9 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
         u0 = df_norm(u0);
         u1 = df_norm(u1);
         u2 = df_norm(u2);
-        const dfl d00 = df_ld(dk), d01 = df_ld(dk + L::Q3), d02 = df_ld(dk + 2 * L::Q3), d11 = df_ld(dk + 3 * L::Q3),
-                  d12 = df_ld(dk + 4 * L::Q3), d22 = df_ld(dk + 5 * L::Q3);
+        const int i1 = 1 % L::NC, i2 = 2 % L::NC, i3 = 3 % L::NC, i4 = 4 % L::NC, i5 = 5 % L::NC;
+        const dfl d00 = {dc[0].x, dc[0].y}, d01 = {dc[i1].x, dc[i1].y}, d02 = {dc[i2].x, dc[i2].y},
+                  d11 = {dc[i3].x, dc[i3].y}, d12 = {dc[i4].x, dc[i4].y}, d22 = {dc[i5].x, dc[i5].y};
         dfl v0 = df_zero(), v1 = df_zero(), v2 = df_zero();
         df_fma(v0, d00, u0);
         df_fma(v0, d01, u1);
@@ -273,7 +291,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
         for (int c = 0; c < n; ++c) df_fma(u, T::B(k, c), c0[c]);
         u = df_norm(u);
         dfl v = df_zero();
-        df_fma(v, df_ld(dk), u);
+        df_fma(v, dfl{dc[0].x, dc[0].y}, u);
         v = df_norm(v);
 #pragma unroll
         for (int c = 0; c < n; ++c) df_fma(a0[c], T::B(k, c), v);

@@ -250,8 +250,20 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
     a0[c] = 0.f;
     if (DIFF) a1[c] = a2[c] = 0.f;
   }
+  // D of point k+1 is loaded while point k is computed (one step of software pipelining)
+  constexpr int NCD = DIFF ? 6 : 1;
+  float dn[NCD];
+#pragma unroll
+  for (int m = 0; m < NCD; ++m) dn[m] = dE[m * L::DSTRIDE];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
+    float dc[NCD];
+#pragma unroll
+    for (int m = 0; m < NCD; ++m) dc[m] = dn[m];
+    if (k + 1 < Q) {
+#pragma unroll
+      for (int m = 0; m < NCD; ++m) dn[m] = dE[(k + 1) * Q * Q + m * L::DSTRIDE];
+    }
     if (DIFF) {
       float u0 = 0.f, u1 = 0.f, u2 = 0.f;
 #pragma unroll
@@ -260,9 +272,8 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
         u1 = fmaf(T::B(k, c), c1[c], u1);
         u2 = fmaf(T::G(k, c), c2[c], u2);
       }
-      const float* dk = dE + k * Q * Q;
-      const float d00 = dk[0], d01 = dk[L::DSTRIDE], d02 = dk[2 * L::DSTRIDE], d11 = dk[3 * L::DSTRIDE],
-                  d12 = dk[4 * L::DSTRIDE], d22 = dk[5 * L::DSTRIDE];
+      const float d00 = dc[0], d01 = dc[1 % NCD], d02 = dc[2 % NCD], d11 = dc[3 % NCD], d12 = dc[4 % NCD],
+                  d22 = dc[5 % NCD];
       const float v0 = fmaf(d00, u0, fmaf(d01, u1, d02 * u2));
       const float v1 = fmaf(d01, u0, fmaf(d11, u1, d12 * u2));
       const float v2 = fmaf(d02, u0, fmaf(d12, u1, d22 * u2));
@@ -276,7 +287,7 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
       float u = 0.f;
 #pragma unroll
       for (int c = 0; c < n; ++c) u = fmaf(T::B(k, c), c0[c], u);
-      const float v = dE[k * Q * Q] * u;
+      const float v = dc[0] * u;
 #pragma unroll
       for (int c = 0; c < n; ++c) a0[c] = fmaf(T::B(k, c), v, a0[c]);
     }
@@ -392,11 +403,24 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   float* S1 = sWall + el * S::WORK;
   float* S2 = S1 + S::NC1 * S::S1C;
   const int* g = gmap + (e0 + el) * (n * n * n);
-  if (live)
-    for (int l = tid; l < n * n * n; l += TPE) {
-      const int gi = g[l];
-      sX[(l / n) * S::XL + l % n] = gi >= 0 ? x[gi] : 0.f;
+  if (live) {
+    // gather: all map loads first, then all x loads, so the dependent pairs overlap
+    constexpr int GR = (n * n * n + TPE - 1) / TPE;
+    int gi[GR];
+    float xv[GR];
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      gi[r] = l < n * n * n ? __ldg(g + l) : -1;
     }
+#pragma unroll
+    for (int r = 0; r < GR; ++r) xv[r] = gi[r] >= 0 ? __ldg(x + gi[r]) : 0.f;
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      if (l < n * n * n) sX[(l / n) * S::XL + l % n] = xv[r];
+    }
+  }
   __syncthreads();
   {
     int e, ln;
