@@ -138,6 +138,11 @@ def reduce_max_sum(t, work, dist=None, device="cpu"):
 
 # nominal FP64 rate of the B300 (no FP64 tensor-core path); the FP64 pipe bounds this kernel
 FP64_PEAK_GFLOPS = 1250.0
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of the
+# current apply kernels on the default workload: captured at 40^3 elements (413.4 MB FP32 variant
+# 2, 794.9 MB double-float: the algorithmic bytes, y read once for the atomics) and scaled to
+# 64^3 by elements (D, map) and DOFs (x, y).  Only reported when that kernel is the one timed.
+NCU_TRAFFIC_P4_N64 = {"f32_v2": 1.6937e9, "df": 3.2564e9}
 # ceiling of the double-float FP64 action: 12 FP32-pipe instructions per FP64-accurate
 # multiply-add (exact product by FMA, TwoSum accumulation) on 128 FP32 lanes/SM x 148 SMs
 # at 2.032 GHz, 2 flops per multiply-add
@@ -337,8 +342,11 @@ def run_ours(args, rank, world, dist):
             ach = fl / t_apply / 1e9
             v64, vname = op.f64_variant()
             if v64 == 1:
+                traffic = args.traffic_fp64
+                if traffic is None and (p, n) == (4, 64):
+                    traffic = NCU_TRAFFIC_P4_N64["df"]
                 r["roofline"] = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_GFLOPS, "unit": "GFLOP/s",
-                                 "frac": ach / DF_PEAK_GFLOPS, "traffic": args.traffic_fp64,
+                                 "frac": ach / DF_PEAK_GFLOPS, "traffic": traffic,
                                  "kernel": f"pa_apply_df<{p},{q},diffusion> ({vname}, autotuned)",
                                  "apply_ms": 1e3 * t_apply,
                                  "peak_note": "FP64-accurate flops at the FP32 pipe's rate / 12 instructions per "
@@ -360,8 +368,11 @@ def run_ours(args, rank, world, dist):
             by = bytes_per_elem(p + 1, q, "diffusion", p, n, word=4) * E
             ach = by / t_apply / 1e9
             fl = flops_per_elem(p + 1, q, "diffusion") * E
+            traffic = args.traffic_fp32
+            if traffic is None and (p, n) == (4, 64) and op.f32_variant()[0] == 2:
+                traffic = NCU_TRAFFIC_P4_N64["f32_v2"]
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach / hbm_peak, "traffic": args.traffic_fp32,
+                             "frac": ach / hbm_peak, "traffic": traffic,
                              "kernel": f"pa_apply_f32_tma<{p},{q},diffusion> variant {op.f32_variant()[0]} "
                                        f"({op.f32_variant()[1]}, autotuned)", "apply_ms": 1e3 * t_apply,
                              "peak_note": f"HBM copy bandwidth ({hbm_src})",
