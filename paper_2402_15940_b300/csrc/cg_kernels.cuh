@@ -277,8 +277,16 @@ __global__ void __launch_bounds__(RED_THREADS)
 cg32_dot_dh(int64_t N, const float* __restrict__ d, const float* __restrict__ h, CgState* st, double* partials) {
   if (st->done) return;
   float s_h = 0.f, s_l = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    f2_add_prod(s_h, s_l, d[i], h[i]);
+  // 16-byte vector loads over the bulk (the loop's vectors are 256-byte aligned), scalar tail
+  const int64_t N4 = N >> 2, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < N4; i += ts) {
+    const float4 dv = reinterpret_cast<const float4*>(d)[i], hv = reinterpret_cast<const float4*>(h)[i];
+    f2_add_prod(s_h, s_l, dv.x, hv.x);
+    f2_add_prod(s_h, s_l, dv.y, hv.y);
+    f2_add_prod(s_h, s_l, dv.z, hv.z);
+    f2_add_prod(s_h, s_l, dv.w, hv.w);
+  }
+  for (int64_t i = 4 * N4 + t0; i < N; i += ts) f2_add_prod(s_h, s_l, d[i], h[i]);
   double v[1] = {f2_value(s_h, s_l)};
   double blk[1];
   block_sum<1>(v, blk);
@@ -298,14 +306,25 @@ cg32_update(int64_t N, float* __restrict__ x, float* __restrict__ r, const float
   if (st->done) return;
   const float alpha = (float)st->alpha;
   float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fmaf(alpha, d[i], x[i]);
-    const float ri = fmaf(-alpha, h[i], r[i]);
-    r[i] = ri;
-    const float zi = inv_diag ? ri * inv_diag[i] : ri;
-    f2_add_prod(zr_h, zr_l, zi, ri);
+  auto one = [&](float& xi, float& ri, float di, float hi, float wi) {
+    xi = fmaf(alpha, di, xi);
+    ri = fmaf(-alpha, hi, ri);
+    f2_add_prod(zr_h, zr_l, ri * wi, ri);
     f2_add_prod(rr_h, rr_l, ri, ri);
+  };
+  const int64_t N4 = N >> 2, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < N4; i += ts) {  // 16-byte vector accesses over the bulk
+    float4 xv = reinterpret_cast<float4*>(x)[i], rv = reinterpret_cast<float4*>(r)[i];
+    const float4 dv = reinterpret_cast<const float4*>(d)[i], hv = reinterpret_cast<const float4*>(h)[i];
+    const float4 wv = inv_diag ? reinterpret_cast<const float4*>(inv_diag)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+    one(xv.x, rv.x, dv.x, hv.x, wv.x);
+    one(xv.y, rv.y, dv.y, hv.y, wv.y);
+    one(xv.z, rv.z, dv.z, hv.z, wv.z);
+    one(xv.w, rv.w, dv.w, hv.w, wv.w);
+    reinterpret_cast<float4*>(x)[i] = xv;
+    reinterpret_cast<float4*>(r)[i] = rv;
   }
+  for (int64_t i = 4 * N4 + t0; i < N; i += ts) one(x[i], r[i], d[i], h[i], inv_diag ? inv_diag[i] : 1.f);
   double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
   double blk[2];
   block_sum<2>(v, blk);
@@ -336,7 +355,19 @@ cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, fl
     cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
   if (done) return;
   const float beta = (float)st->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t N4 = N >> 2, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < N4; i += ts) {  // 16-byte vector accesses over the bulk
+    const float4 rv = reinterpret_cast<const float4*>(r)[i];
+    const float4 wv = inv_diag ? reinterpret_cast<const float4*>(inv_diag)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
+    float4 dv = reinterpret_cast<float4*>(d)[i];
+    dv.x = fmaf(beta, dv.x, rv.x * wv.x);
+    dv.y = fmaf(beta, dv.y, rv.y * wv.y);
+    dv.z = fmaf(beta, dv.z, rv.z * wv.z);
+    dv.w = fmaf(beta, dv.w, rv.w * wv.w);
+    reinterpret_cast<float4*>(d)[i] = dv;
+    reinterpret_cast<float4*>(h)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int64_t i = 4 * N4 + t0; i < N; i += ts) {
     const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
     d[i] = fmaf(beta, d[i], zi);
     h[i] = 0.f;
