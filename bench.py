@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -70,7 +71,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # samples go to BENCH_CLOCK_DIR if set (to keep them), else to the temporary directory
+        out = os.environ.get("BENCH_CLOCK_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -511,6 +514,85 @@ def run_batch(args, rank, world, dist):
     return 0
 
 
+def run_sweep(args, rank, world, dist):
+    """Operator-action sweep (BP1 mass and BP3 diffusion, p = 1..8, q = p+2, seeded perturbed
+    cubes, x ~ U[-1, 1]) at about 1e5, 1e6 and 3e7 DOFs: single-application GDOF/s of the
+    FP64-accurate action (autotuned kernel) and of the FP32 action, and GDOF/s per Jacobi-PCG
+    iteration (FP64, all boundary DOFs essential for diffusion), each against its roofline."""
+    import torch
+
+    import paper_2402_15940_b300 as F
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    hbm_peak, hbm_src = peaks()
+
+    def ev_time(fn, reps):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    rows = []
+    t_start = time.perf_counter()
+    for p in range(1, 9):
+        for form in ("mass", "diffusion"):
+            for target in (1e5, 1e6, 3e7):
+                n = max(1, int(round((target ** (1.0 / 3.0) - 1) / p)))
+                op = F.Operator(n, n, n, FI.perturbed_cube_vertices(n, n, n, seed=rank), p, form=form)
+                q, N, E = op.q, op.N, op.E
+                x = torch.from_numpy(FI.uniform_vector(N, seed=1)).cuda()
+                y = torch.empty_like(x)
+                t64 = ev_time(lambda: op.apply(x, out=y), 20)
+                x32, y32 = x.float(), torch.empty(N, dtype=torch.float32, device="cuda")
+                t32 = ev_time(lambda: op.apply_f32(x32, out=y32), 20)
+                v64 = op.f64_variant()[0]
+                fl = flops_per_elem(p + 1, q, form) * E
+                by64 = bytes_per_elem(p + 1, q, form, p, n, word=8) * E
+                by32 = bytes_per_elem(p + 1, q, form, p, n, word=4) * E
+                alu_peak = DF_PEAK_GFLOPS if v64 == 1 else FP64_PEAK_GFLOPS
+                # roofline of the FP64-accurate action: the slower of its ALU ceiling and HBM
+                roof64 = min(alu_peak * 1e9 / (fl / E), hbm_peak * 1e9 / (by64 / E)) * E / N
+                if form == "diffusion":
+                    op.set_essential(op.boundary_dofs())
+                b = op.rhs_sine(1.0)
+                xs = torch.zeros(N, dtype=torch.float64, device="cuda")
+                it_lo, it_hi = 10, 60
+                t_lo = ev_time(lambda: op.iterations(b, xs.zero_(), it_lo), 1)
+                t_hi = ev_time(lambda: op.iterations(b, xs.zero_(), it_hi), 1)
+                t_it = max(t_hi - t_lo, 1e-9) / (it_hi - it_lo)
+                rows.append({
+                    "p": p, "form": form, "n": n, "ndofs": N,
+                    "fp64_action": {"kernel": op.f64_variant()[1], "ms": 1e3 * t64, "gdofs": N / t64 / 1e9,
+                                    "gflops": fl / t64 / 1e9, "frac_alu": fl / t64 / 1e9 / alu_peak,
+                                    "gbs": by64 / t64 / 1e9, "frac_hbm": by64 / t64 / 1e9 / hbm_peak,
+                                    "frac_roofline": (N / t64) / roof64},
+                    "fp32_action": {"variant": op.f32_variant()[0], "ms": 1e3 * t32, "gdofs": N / t32 / 1e9,
+                                    "gbs": by32 / t32 / 1e9, "frac_hbm": by32 / t32 / 1e9 / hbm_peak},
+                    "fp64_cg_iteration": {"ms": 1e3 * t_it, "gdofs": N / t_it / 1e9}})
+                del op, x, y, x32, y32, b, xs
+                torch.cuda.empty_cache()
+    if rank == 0:
+        big = [r for r in rows if r["p"] == 4 and r["form"] == "diffusion"][-1]
+        line = {"metric": "BP1/BP3 operator sweep: GDOF/s per FP64-accurate application", "value":
+                big["fp64_action"]["gdofs"], "unit": UNIT, "n_gpus": world, "steps": 20, "warmup": 3,
+                "ms_per_step": big["fp64_action"]["ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 (double-float or DFMA, autotuned) | f32", "data": "synthetic",
+                "config": {"workload": "p = 1..8, mass and diffusion, q = p+2, perturbed cubes at ~1e5, 1e6 and "
+                                       "3e7 DOFs, x ~ U[-1,1]; value = diffusion p=4 at the largest size",
+                           "peaks": {"hbm_gbs": hbm_peak, "hbm_source": hbm_src, "df_gflops": DF_PEAK_GFLOPS,
+                                     "fp64_gflops": FP64_PEAK_GFLOPS}},
+                "sweep": rows, "wall_s": time.perf_counter() - t_start}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args, rank, world, dist):
     """Served solve stream: for each arrival rate, `--requests` requests (mass or
     diffusion, p uniform in 1..8, DOFs log-uniform in 1e3..5e6, FP64 or mixed with
@@ -578,7 +660,7 @@ def main():
     ap.add_argument("--traffic-fp64", type=float, default=None, help="DRAM bytes per FP64 apply launch (ncu)")
     ap.add_argument("--traffic-fp32", type=float, default=None, help="DRAM bytes per FP32 apply launch (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bp3", "batch", "serve"], default="bp3")
+    ap.add_argument("--workload", choices=["bp3", "batch", "serve", "sweep"], default="bp3")
     ap.add_argument("--rates", default="10,100,1000,5000")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--hbm-budget", type=float, default=150e9)
@@ -603,6 +685,8 @@ def main():
             return run_batch(args, rank, world, dist)
         if args.workload == "serve":
             return run_serve(args, rank, world, dist)
+        if args.workload == "sweep":
+            return run_sweep(args, rank, world, dist)
         return run_ours(args, rank, world, dist)
     finally:
         if dist is not None:

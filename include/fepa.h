@@ -189,7 +189,8 @@ int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
  * groups (TMA copy of the next group's D and cp.async gather of its x overlap the
  * current group's arithmetic).  By default (variant -1) the first FP32 use
  * times every variant on this op's mesh and keeps the fastest; the choice is cached per
- * device and (p, q, form) for the process.  All variants compute the same result.
+ * device, (p, q, form) and mesh size class (E < 1e3, 1e4, 1e5, larger) for the process.
+ * All variants compute the same result.
  */
 int fepa_op_set_f32_variant(fepa_op* op, int32_t variant);
 int32_t fepa_op_f32_variant(const fepa_op* op);          /* -1 until chosen */
@@ -197,15 +198,18 @@ const char* fepa_f32_variant_name(int32_t variant);
 
 /*
  * Arithmetic of the FP64 action (fepa_op_apply and every FP64 solve on this op).
- * Variants: 0 = native FP64 (DFMA), 1 = double-float: each value is split into two
- * floats (hi + lo) as it is read, every contraction step is an accurate dot-product
- * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative
- * error), and the element result is recombined in FP64 -- same inputs, outputs and
- * memory traffic, error far inside the FP64 action's tolerance.  This library's own
+ * Variants: 0 = native FP64 (DFMA), 1 = double-float: x is split into two floats
+ * (hi + lo) as it is gathered and D is read as (hi, lo) pairs (a copy of D kept beside
+ * the FP64 one, 8 bytes per value), every contraction step is an accurate dot-product
+ * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative error),
+ * and the element result is recombined in FP64 -- error far inside the FP64 action's
+ * tolerance; valid while values stay within the float exponent range less the low
+ * word's 24 bits (about 1e-30 .. 3e38), outside it force variant 0.  This library's own
  * design for a GPU whose FP64 rate is a small fraction of its FP32 rate; the paper's
  * FP64 kernels have no counterpart.  By default (-1) the first FP64 use times both on
- * this op's mesh and keeps the faster; cached per device and (p, q, form).  The
- * allocation-free solve never times: it uses the chosen or forced variant, else 0.
+ * this op's mesh and keeps the faster; cached per device, (p, q, form) and mesh size
+ * class.  The allocation-free solve never times: it uses the chosen or forced variant
+ * (the double-float one only if its copy of D is current), else 0.
  */
 int fepa_op_set_f64_variant(fepa_op* op, int32_t variant);
 int32_t fepa_op_f64_variant(const fepa_op* op);          /* -1 until chosen */
@@ -375,8 +379,8 @@ int32_t fepa_batch_groups(const fepa_batch* batch);                  /* distinct
 int fepa_batch_set_stream(fepa_batch* batch, void* stream);
 
 /* FP64 action variant of every group (as fepa_op_set_f64_variant: 0 DFMA, 1 double-float,
- * -1 = the process-wide choice for the group's (p, q, form) if one was measured, else
- * the faster of the two timed on the group at the next apply or solve). */
+ * -1 = the process-wide choice for the group's (p, q, form, size class) if one was
+ * measured, else the faster of the two timed on the group at the next apply or solve). */
 int fepa_batch_set_f64_variant(fepa_batch* batch, int32_t variant);
 
 /* y = A x for every problem at once (x, y: device, total DOFs). */

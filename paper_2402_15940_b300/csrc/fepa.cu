@@ -457,14 +457,18 @@ int ensure_inv_diag(fepa_op* op) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the FP32 kernel's launch shape: the compiled variants (TMA-staged or
-// direct D, elements per block) are timed on the op's own mesh the first time a
-// (device, p, q, form) is used in this process; the fastest is cached and reused.
+// Autotuner of the FP32 kernel's launch shape and of the FP64 arithmetic: the compiled
+// variants are timed on the op's own mesh the first time a (device, p, q, form, size
+// class) is used in this process; the fastest is cached and reused.  Size classes of E:
+// < 1e3, < 1e4, < 1e5, >= 1e5 elements (small meshes are launch-bound, large ones not).
 // ---------------------------------------------------------------------------
+constexpr int N_SIZE_CLASSES = 4;
 std::mutex g_tune_mutex;
-int g_tuned[64][FEPA_MAX_ORDER + 1][2][2];
-int g_tuned64[64][FEPA_MAX_ORDER + 1][2][2];
+int g_tuned[64][FEPA_MAX_ORDER + 1][2][2][N_SIZE_CLASSES];
+int g_tuned64[64][FEPA_MAX_ORDER + 1][2][2][N_SIZE_CLASSES];
 bool g_tuned_init = false;
+
+int size_class(int64_t E) { return E < 1000 ? 0 : E < 10000 ? 1 : E < 100000 ? 2 : 3; }
 
 void init_tuned() {
   if (g_tuned_init) return;
@@ -472,7 +476,8 @@ void init_tuned() {
     for (auto& a : *t)
       for (auto& b : a)
         for (auto& c : b)
-          for (int& d : c) d = -1;
+          for (auto& d : c)
+            for (int& v : d) v = -1;
   g_tuned_init = true;
 }
 
@@ -523,7 +528,7 @@ int choose_variant32(fepa_op* op) {
   const int dev = op->device < 64 ? op->device : 63;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   init_tuned();
-  int& slot = g_tuned[dev][op->p][op->q - op->p - 1][op->form];
+  int& slot = g_tuned[dev][op->p][op->q - op->p - 1][op->form][size_class(op->E)];
   if (slot < 0) {
     int best = 0;
     TRY(time_variants32(op, &best));
@@ -585,10 +590,10 @@ int time_variants64(fepa_op* op, int* best) {
 }
 
 // Cached FP64 variant choice for (device, p, q, form), -1 if none yet (caller holds no lock)
-int tuned64_lookup(int device, int p, int q, int form) {
+int tuned64_lookup(int device, int p, int q, int form, int64_t E) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   init_tuned();
-  return g_tuned64[device < 64 ? device : 63][p][q - p - 1][form];
+  return g_tuned64[device < 64 ? device : 63][p][q - p - 1][form][size_class(E)];
 }
 
 // FP64 action variant: the caller's, else the fastest one measured for this device, p, q
@@ -602,7 +607,7 @@ int ensure_v64(fepa_op* op) {
   const int dev = op->device < 64 ? op->device : 63;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   init_tuned();
-  int& slot = g_tuned64[dev][op->p][op->q - op->p - 1][op->form];
+  int& slot = g_tuned64[dev][op->p][op->q - op->p - 1][op->form][size_class(op->E)];
   if (slot < 0) {
     int best = 0;
     TRY(time_variants64(op, &best));

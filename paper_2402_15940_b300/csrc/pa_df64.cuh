@@ -141,6 +141,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   using L = typename S::L;
   using T = TabDf<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
+  constexpr int DQ1 = Q | 1;  // S1 line stride (odd), within the FP32 layout's S1 component size
+  static_assert(DQ1 * n * n <= L::S1C, "S1 component size");
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_df[];
   dfl* sXall = reinterpret_cast<dfl*>(smem_df);
@@ -193,8 +195,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
         df_fma(sb, T::B(i, a), xv[a]);
         if (DIFF) df_fma(sg, T::G(i, a), xv[a]);
       }
-      S1[tid * L::Q1 + i] = df_norm(sb);
-      if (DIFF) S1[L::S1C + tid * L::Q1 + i] = df_norm(sg);
+      S1[tid * DQ1 + i] = df_norm(sb);
+      if (DIFF) S1[L::S1C + tid * DQ1 + i] = df_norm(sg);
     }
   }
   __syncthreads();
@@ -205,8 +207,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     dfl vb[n], vg[n];
 #pragma unroll
     for (int b = 0; b < n; ++b) {
-      vb[b] = S1[(b + n * c) * L::Q1 + i];
-      if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * L::Q1 + i];
+      vb[b] = S1[(b + n * c) * DQ1 + i];
+      if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * DQ1 + i];
     }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -331,8 +333,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
           df_fma(t1, T::B(j, b), v2[j]);
         }
       }
-      S1[(b + n * c) * L::Q1 + i] = df_norm(t0);
-      if (DIFF) S1[L::S1C + (b + n * c) * L::Q1 + i] = df_norm(t1);
+      S1[(b + n * c) * DQ1 + i] = df_norm(t0);
+      if (DIFF) S1[L::S1C + (b + n * c) * DQ1 + i] = df_norm(t1);
     }
   }
   __syncthreads();
@@ -342,8 +344,8 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     dfl t0[Q], t1[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      t0[i] = S1[tid * L::Q1 + i];
-      if (DIFF) t1[i] = S1[L::S1C + tid * L::Q1 + i];
+      t0[i] = S1[tid * DQ1 + i];
+      if (DIFF) t1[i] = S1[L::S1C + tid * DQ1 + i];
     }
 #pragma unroll
     for (int a = 0; a < n; ++a) {
