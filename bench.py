@@ -558,7 +558,7 @@ def run_sweep(args, rank, world, dist):
                 by32 = bytes_per_elem(p + 1, q, form, p, n, word=4) * E
                 alu_peak = DF_PEAK_GFLOPS if v64 == 1 else FP64_PEAK_GFLOPS
                 # roofline of the FP64-accurate action: the slower of its ALU ceiling and HBM
-                roof64 = min(alu_peak * 1e9 / (fl / E), hbm_peak * 1e9 / (by64 / E)) * E / N
+                roof64 = min(alu_peak * 1e9 / (fl / E), hbm_peak * 1e9 / (by64 / E)) * N / E
                 if form == "diffusion":
                     op.set_essential(op.boundary_dofs())
                 b = op.rhs_sine(1.0)
