@@ -203,7 +203,7 @@ __device__ __forceinline__ void f32_stage1(int tid, bool live, const float* sX, 
   float xv[n];
 #pragma unroll
   for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
-  float* o = S1 + (tid % n) * L::Q1 + (tid / n) * L::CS;
+  float* o = S1 + (L::CS == n * L::Q1 ? tid * L::Q1 : (tid % n) * L::Q1 + (tid / n) * L::CS);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     float sb = 0.f, sg = 0.f;
@@ -256,8 +256,9 @@ __device__ __forceinline__ void f32_stage2(int tid, bool live, const float* S1, 
 
 // stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers; D at dE
 // (shared or global), component stride DSTRIDE, point k at dE[k*Q*Q]
-template <int P, int Q, bool DIFF>
-__device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE) {
+// PRE: the column's D was loaded into dpre[k * NCD + m] before the preceding barrier
+template <int P, int Q, bool DIFF, bool PRE = false>
+__device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE, const float* dpre = nullptr) {
   using L = F32Layout<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
@@ -276,16 +277,23 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
   // D of point k+1 is loaded while point k is computed (one step of software pipelining)
   constexpr int NCD = DIFF ? 6 : 1;
   float dn[NCD];
+  if (!PRE) {
 #pragma unroll
-  for (int m = 0; m < NCD; ++m) dn[m] = dE[m * L::DSTRIDE];
+    for (int m = 0; m < NCD; ++m) dn[m] = dE[m * L::DSTRIDE];
+  }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     float dc[NCD];
+    if (PRE) {
 #pragma unroll
-    for (int m = 0; m < NCD; ++m) dc[m] = dn[m];
-    if (k + 1 < Q) {
+      for (int m = 0; m < NCD; ++m) dc[m] = dpre[k * NCD + m];
+    } else {
 #pragma unroll
-      for (int m = 0; m < NCD; ++m) dn[m] = dE[(k + 1) * Q * Q + m * L::DSTRIDE];
+      for (int m = 0; m < NCD; ++m) dc[m] = dn[m];
+      if (k + 1 < Q) {
+#pragma unroll
+        for (int m = 0; m < NCD; ++m) dn[m] = dE[(k + 1) * Q * Q + m * L::DSTRIDE];
+      }
     }
     if (DIFF) {
       float u0 = 0.f, u1 = 0.f, u2 = 0.f;
@@ -367,7 +375,7 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
   constexpr int n = L::N;
   if (!(live && tid < n * n)) return;
   float t0[Q], t1[Q];
-  const float* in = S1 + (tid % n) * L::Q1 + (tid / n) * L::CS;
+  const float* in = S1 + (L::CS == n * L::Q1 ? tid * L::Q1 : (tid % n) * L::Q1 + (tid / n) * L::CS);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     t0[i] = in[i];
@@ -397,7 +405,9 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 // ---------------------------------------------------------------------------
 // PF: L2 prefetch at block start (TMA engine, one thread): 1 = the group's D (unless staged),
 // 2 = also its map entries.  Measured on B300: 4-11 % faster for p = 2..8 (PF 2 best).
-template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4)>
+// DEARLY (measured): loading the stage-3 D column before the barrier is 3-6 % faster for
+// p <= 3 and 3-17 % slower from p = 4 (the 6 q registers it holds cost occupancy there).
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3)>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
@@ -458,6 +468,17 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     float* S1e = sWall + e * S::WORK;
     f32_stage2<P, Q, DIFF>(ln, e < ne, S1e, S1e + S::NC1 * S::S1C);
   }
+  // DEARLY: the stage-3 thread loads its whole D column before the barrier, so the loads
+  // overlap the wait for the other threads' stage 2
+  constexpr int NCD = DIFF ? 6 : 1;
+  float dpre[(DEARLY && !STAGE_D) ? NCD * Q : 1];
+  if (DEARLY && !STAGE_D && live) {
+    const float* dg = qd32 + (e0 + el) * S::DELEM + tid;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+      for (int m = 0; m < NCD; ++m) dpre[k * NCD + m] = __ldg(dg + k * Q * Q + m * S::DSTRIDE);
+  }
   if (STAGE_D) {
     // D must have landed before stage 3; every thread observes the barrier (bounded)
     const bool ok = mbar_wait_bounded(mbar);
@@ -472,7 +493,7 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     __syncthreads();
   }
   const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
-  f32_stage3<P, Q, DIFF>(tid, live, S2, dE);
+  f32_stage3<P, Q, DIFF, DEARLY && !STAGE_D>(tid, live, S2, dE, dpre);
   __syncthreads();
   {
     int e, ln;
