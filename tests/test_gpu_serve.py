@@ -49,7 +49,9 @@ def test_resumable_solve_equals_one_shot(kind, step):
             break
     assert st["done"] and st["status"] == 0 and st["rel_residual"] <= 1e-10
     key = "iterations" if kind == "cg" else "inner_iterations"
-    assert abs(st["iterations"] - s1[key]) <= 1
+    # FP64 CG is reproducible to one iteration; the FP32 inner counts may move by a few
+    # (the FP32 scatter's atomic summation order varies from run to run)
+    assert abs(st["iterations"] - s1[key]) <= (1 if kind == "cg" else max(4, 0.1 * s1[key]))
     assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
 
 
@@ -89,7 +91,9 @@ def test_server_results_same_alone_and_in_the_mix():
             assert abs(sa["iterations"] - o.iterations) <= 1
         else:
             xa, sa = op.solve_refined(b, rtol=1e-10)
-            assert abs(sa["inner_iterations"] - o.iterations) <= 2
+            # the FP32 scatter's atomic summation order varies from run to run, so the inner
+            # FP32 iteration counts may move by a few; the solutions are compared below
+            assert abs(sa["inner_iterations"] - o.iterations) <= max(4, 0.1 * sa["inner_iterations"])
         assert rel(o.result, xa.cpu().numpy()) <= 1e-9, r
         # and the oracle's tight solution of the same problem
         mesh = O.HexGridMesh(*r.n, FI.perturbed_cube_vertices(*r.n, seed=r.mesh_seed))
