@@ -401,8 +401,8 @@ int fepa_batch_solve(fepa_batch* batch, const double* b, double* x, double rtol,
  * acceleration).  Levels p, max(1, p/2), ..., 1 built from the fine op's mesh and form;
  * essential DOFs must be none or exactly the boundary (each level then fixes its own
  * boundary).  Smoother: `smooth_degree` Chebyshev-Jacobi steps on
- * [0.25, 1.1] * lambda_max(D^{-1}A) (power iteration at set-up); coarsest level:
- * `coarse_degree` steps on [0.003, 1.2] * lambda_max.  The V-cycle is symmetric and
+ * [0.245, 1.08] * lambda_max(D^{-1}A) (10 Lanczos steps at set-up); coarsest level:
+ * `coarse_degree` steps on [0.003, 1.18] * lambda_max.  The V-cycle is symmetric and
  * linear, so it preconditions plain CG.  precision: FEPA_MG_FP64, or FEPA_MG_FP32 for an
  * FP32 V-cycle (FP32 operators, smoothers and transfers on every level) inside the FP64
  * CG (whose operator action, dot products and scalars stay FP64).  The fine op must

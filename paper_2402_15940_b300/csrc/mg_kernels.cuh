@@ -270,7 +270,7 @@ __global__ void convert(int64_t N, const A* __restrict__ in, B* __restrict__ out
     out[i] = (B)in[i];
 }
 
-// deterministic pseudo-random start vector for the power iteration (splitmix64 of the index)
+// deterministic pseudo-random start vector for the eigenvalue estimate (splitmix64 of the index)
 template <typename T>
 __global__ void hash_fill(int64_t N, T* __restrict__ v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -282,44 +282,102 @@ __global__ void hash_fill(int64_t N, T* __restrict__ v) {
   }
 }
 
-// out[0] += (a, b), out[1] += (a, D a) with D = 1/w (w may be null: (a, a)): power iteration
+// ---------------------------------------------------------------------------
+// lambda_max(D^{-1} A) by the Lanczos process on S = D^{-1/2} A D^{-1/2} (symmetric,
+// same spectrum): u_{j+1} beta_{j+1} = S u_j - alpha_j u_j - beta_j u_{j-1}.  The
+// coefficients stay on the device (fixed-order block reductions, the last block writes
+// them), the host takes the largest eigenvalue of the small tridiagonal matrix at the end.
+// ---------------------------------------------------------------------------
+constexpr int MG_LANCZOS = 10;
+
+struct LanczosState {
+  double alpha[MG_LANCZOS];
+  double beta[MG_LANCZOS + 1];  // beta[0] = norm of the start vector, beta[j+1] = ||w_j||
+  unsigned int ticket;
+};
+
+// beta[0] = ||v||
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
-dot2(int64_t N, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ w, double* __restrict__ out) {
-  // per-thread partial sums in T (FP32 for an FP32 V-cycle: the eigenvalue estimate needs
-  // a few digits, and FP64 products would run on the slow FP64 pipe), block sums in FP64
-  T p0 = T(0), p1 = T(0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const T ai = a[i];
-    p0 += ai * b[i];
-    p1 += w ? ai * ai / w[i] : ai * ai;   // w = 1/diag: (a, D a)
-  }
-  double v[2] = {(double)p0, (double)p1};
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (threadIdx.x == 0) {
-    atomicAdd(out, blk[0]);
-    atomicAdd(out + 1, blk[1]);
-  }
-}
-
-// v = s * D^{-1} h
-template <typename T>
-__global__ void scaled_jacobi(int64_t N, T s, const T* __restrict__ invd, const T* __restrict__ h, T* __restrict__ v) {
+lz_norm(int64_t N, const T* __restrict__ v, LanczosState* st, double* partials) {
+  // per-thread sums in T (an FP32 V-cycle's estimate needs a few digits, and FP64 products
+  // would run on the slow FP64 pipe), block and grid sums in FP64
+  T a0 = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = s * invd[i] * h[i];
+    a0 += v[i] * v[i];
+  double acc[1] = {(double)a0};
+  double blk[1];
+  block_sum<1>(acc, blk);
+  if (publish_partials<1>(blk, partials, &st->ticket)) {
+    double tot[1];
+    final_sums<1>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->beta[0] = sqrt(tot[0]);
+      st->ticket = 0;
+    }
+  }
 }
 
-// Power-iteration step without a host round trip: lambda = dots[0] / dots[1] (the
-// Rayleigh quotient just reduced), v = D^{-1} h / lambda, h = 0 for the next product,
-// and the other dot pair cleared for the next reduction.
+// u = v / beta[0]; t = D^{-1/2} u; h = 0
 template <typename T>
-__global__ void power_step(int64_t N, const double* __restrict__ dots, double* __restrict__ next,
-                           const T* __restrict__ invd, T* __restrict__ h, T* __restrict__ v) {
-  const T s = (T)(dots[1] / dots[0]);
-  if (blockIdx.x == 0 && threadIdx.x < 2) next[threadIdx.x] = 0.0;
+__global__ void lz_start(int64_t N, const T* __restrict__ v, const T* __restrict__ invd, const LanczosState* st,
+                         T* __restrict__ u, T* __restrict__ t, T* __restrict__ h) {
+  const T sc = (T)(1.0 / st->beta[0]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    v[i] = s * invd[i] * h[i];
+    const T ui = sc * v[i];
+    u[i] = ui;
+    t[i] = sqrt(invd[i]) * ui;
+    h[i] = T(0);
+  }
+}
+
+// w = D^{-1/2} h - beta_j u_prev (into u_prev); alpha_j = (w, u) / (u, u);
+// beta_{j+1} = ||w - alpha_j u|| = sqrt((w, w) - alpha_j (w, u)).  The measured (u, u) keeps
+// rounding in u's norm from compounding (with (u, u) taken as 1 an FP32 run drifts by a
+// factor ~(alpha/beta)^2 per step); a beta within rounding of zero (an invariant subspace,
+// e.g. a level with a handful of free DOFs) is returned as exactly zero.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+lz_reduce(int64_t N, int j, const T* __restrict__ h, const T* __restrict__ invd, const T* __restrict__ u,
+          T* __restrict__ uprev, LanczosState* st, double* partials) {
+  const T bj = j > 0 ? (T)st->beta[j] : T(0);
+  T a0 = T(0), a1 = T(0), a2 = T(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const T w = sqrt(invd[i]) * h[i] - bj * uprev[i];
+    const T ui = u[i];
+    uprev[i] = w;
+    a0 += w * ui;
+    a1 += w * w;
+    a2 += ui * ui;
+  }
+  double acc[3] = {(double)a0, (double)a1, (double)a2};
+  double blk[3];
+  block_sum<3>(acc, blk);
+  if (publish_partials<3>(blk, partials, &st->ticket)) {
+    double tot[3];
+    final_sums<3>(partials, tot);
+    if (threadIdx.x == 0) {
+      const double a = tot[2] > 0.0 ? tot[0] / tot[2] : 0.0;
+      const double b2 = tot[1] - a * tot[0];
+      const double floor2 = (sizeof(T) == 4 ? 1e-5 : 1e-13) * tot[1];  // ~100x the rounding of (w, w)
+      st->alpha[j] = a;
+      st->beta[j + 1] = b2 > floor2 ? sqrt(b2) : 0.0;
+      st->ticket = 0;
+    }
+  }
+}
+
+// u_next = (w - alpha_j u) / beta_{j+1} (in place of w); t = D^{-1/2} u_next; h = 0
+template <typename T>
+__global__ void lz_next(int64_t N, int j, const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ invd,
+                        const LanczosState* st, T* __restrict__ t, T* __restrict__ h) {
+  const T a = (T)st->alpha[j];
+  const double b = st->beta[j + 1];
+  const T ib = b > 0.0 ? (T)(1.0 / b) : T(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const T un = (w[i] - a * u[i]) * ib;
+    w[i] = un;
+    t[i] = sqrt(invd[i]) * un;
     h[i] = T(0);
   }
 }

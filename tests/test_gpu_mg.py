@@ -13,7 +13,7 @@ import oracle as O
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SMOOTH_LO, SMOOTH_HI, COARSE_LO, COARSE_HI = 0.25, 1.1, 0.003, 1.2
+SMOOTH_LO, SMOOTH_HI, COARSE_LO, COARSE_HI = 0.245, 1.08, 0.003, 1.18
 
 
 def F():
@@ -90,7 +90,7 @@ def test_lambda_max_estimate():
         prob = O.Problem(mesh, lv["order"], None, O.DIFFUSION)
         A = prob.Ac.toarray()
         lam = np.linalg.eigvals(A / np.diag(A)[:, None]).real.max()
-        assert 0.9 * lam <= lv["lambda_max"] <= lam * (1 + 1e-9)
+        assert 0.95 * lam <= lv["lambda_max"] <= lam * (1 + 1e-9)   # largest Ritz value: from below
 
 
 @pytest.mark.parametrize("form", ["diffusion", "mass"])
@@ -162,7 +162,7 @@ def test_update_follows_moved_mesh(precision):
     x2, s2 = mg2.solve(op2.rhs_sine(1.0), rtol=1e-10)
     assert abs(s1["iterations"] - s2["iterations"]) <= 1   # atomic summation order may move the stop
     assert rel(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-9
-    tol = 1e-9 if precision == "fp64" else 1e-5   # FP32 atomics reorder the power iteration's sums
+    tol = 1e-9 if precision == "fp64" else 1e-5   # FP32 atomics reorder the Lanczos process's sums
     for a, c in zip(mg.levels, mg2.levels):
         assert abs(a["lambda_max"] / c["lambda_max"] - 1) < tol
 
@@ -181,7 +181,8 @@ def test_vcycle_matches_oracle_and_is_deterministic(form, p, shape):
     b = FI.uniform_vector(op.N, seed=9)
     if form == "diffusion":
         b[probs[0].ess] = 0.0
-    ref = O.pmg_vcycle(As, [A.diagonal() for A in As], Ps, [lv["lambda_max"] for lv in mg.levels], 2, 24, b, ess=ess)
+    ref = O.pmg_vcycle(As, [A.diagonal() for A in As], Ps, [lv["lambda_max"] for lv in mg.levels], 2, 24, b,
+                        smooth=(SMOOTH_LO, SMOOTH_HI), coarse=(COARSE_LO, COARSE_HI), ess=ess)
     z1 = mg.vcycle(dev(b)).cpu().numpy()
     z2 = mg.vcycle(dev(b)).cpu().numpy()
     assert rel(z1, ref) <= 1e-11
