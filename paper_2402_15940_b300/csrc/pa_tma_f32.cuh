@@ -39,9 +39,10 @@ struct Tab32 {
   static __device__ __forceinline__ float G(int i, int a) { return c_tab32[OFF + 100 + i * (P + 1) + a]; }
 };
 
-// S1 strides and element padding per (P, Q), from an exhaustive search of a model of the
-// warp access patterns (stage 1 writing and stage 1^T reading line (b,c); stage 2 reading
-// and stage 2^T writing along b for thread (i,c); elements dealt over the block): the
+// S1 strides and element padding per (P, Q) of the double-float kernel's layout (the FP32
+// kernels use F32Smem below), from an exhaustive search of a model of the warp access
+// patterns (stage 1 writing and stage 1^T reading line (b,c); stage 2 reading and stage
+// 2^T writing along b for thread (i,c); elements dealt over the block): the
 // fewest shared-memory wavefronts, 27-50 % fewer than the plain odd strides.  Measured on
 // B300: 7-11 % faster for p = 2, 3, neutral at p = 4, 4-13 % slower from p = 5 (where the
 // model's pick changes more than the conflicts), so used up to p = 4.
@@ -58,12 +59,13 @@ constexpr S1Pick s1_pick(int P, int Q) {
                               : S1Pick{Q | 1, (P + 1) * (Q | 1), 0};
 }
 
-// Shared-memory layout of one element's stage buffers (floats), padded:
+// Shared-memory layout of one element's stage buffers of the double-float kernel (in
+// elements of its word type), padded:
 //   X  [c][b][a]     line (b,c) of length n at stride XL (odd)
 //   S1 [m][c][b][i]  entry (b,c,i) at b*Q1 + c*CS + i (strides from s1_pick)
 //   S2 [m][c][j][i]  plane c of Q*Q at stride P2 (P2 = Q mod 32: consecutive planes
 //                    start Q banks apart)
-// (the double-float kernel uses the same sizes with its own line stride Q1 in S1)
+// (the double-float kernel takes these sizes with its own line stride Q1 in S1)
 template <int P, int Q, bool DIFF>
 struct F32Layout {
   static constexpr int N = P + 1;
@@ -86,23 +88,82 @@ struct F32Layout {
   static constexpr int NE0 = (256 / TPE) > 0 ? (256 / TPE) : 1;
 };
 
+// Shared-memory layout of the FP32 kernels: X, S1 and S2 in three regions, each with its
+// own per-element stride, so that the stride of each region can place the elements that
+// share a warp on different banks without constraining the other two.  Line and plane
+// strides and the pads come from an exhaustive search of a model of every warp access of
+// variants 1 and 2 (gather store; stages 1, 2, 3, 2^T, 1^T; elements dealt over the
+// block) at NE0 and NE0 / 2 elements per block, the shared memory per element held at or
+// below the plain layout's (more costs variant 3 a block per SM at p = 4).  The model
+// reproduces the shared-memory wavefront count that ncu reports for p = 4 (189 per
+// element before, 168 after); measured on B300 the action gets 2-6 % faster for p <= 4.
+struct SmemPick {
+  int xl, xpad, q1, cs, s1pad, p2, s2pad;
+};
+constexpr SmemPick smem_pick(int P, int Q, bool DIFF) {
+  return (P == 1 && Q == 2 && DIFF) ? SmemPick{2, 4, 3, 6, 4, 6, 0}
+         : (P == 1 && Q == 2 && !DIFF) ? SmemPick{2, 4, 3, 6, 0, 6, 0}
+         : (P == 1 && Q == 3 && DIFF) ? SmemPick{5, 0, 3, 14, 4, 29, 27}
+         : (P == 1 && Q == 3 && !DIFF) ? SmemPick{2, 0, 3, 14, 0, 29, 15}
+         : (P == 2 && Q == 3 && DIFF) ? SmemPick{3, 0, 5, 35, 0, 35, 0}
+         : (P == 2 && Q == 3 && !DIFF) ? SmemPick{3, 0, 5, 35, 0, 35, 0}
+         : (P == 2 && Q == 4 && DIFF) ? SmemPick{3, 0, 5, 20, 4, 20, 8}
+         : (P == 2 && Q == 4 && !DIFF) ? SmemPick{3, 0, 5, 20, 0, 20, 0}
+         : (P == 3 && Q == 4 && DIFF) ? SmemPick{5, 0, 5, 20, 16, 20, 0}
+         : (P == 3 && Q == 4 && !DIFF) ? SmemPick{5, 0, 5, 20, 0, 20, 0}
+         : (P == 3 && Q == 5 && DIFF) ? SmemPick{5, 0, 8, 37, 12, 26, 1}
+         : (P == 3 && Q == 5 && !DIFF) ? SmemPick{5, 0, 8, 37, 0, 26, 17}
+         : (P == 4 && Q == 5 && DIFF) ? SmemPick{5, 0, 7, 37, 7, 37, 14}
+         : (P == 4 && Q == 5 && !DIFF) ? SmemPick{5, 0, 7, 37, 0, 37, 0}
+         : (P == 4 && Q == 6 && DIFF) ? SmemPick{5, 0, 7, 38, 2, 38, 4}
+         : (P == 4 && Q == 6 && !DIFF) ? SmemPick{5, 0, 9, 45, 0, 38, 0}
+         // p >= 5: the plain odd strides (the search's picks measured no faster there,
+         // p = 8 diffusion 2-4 % slower)
+         : SmemPick{(P + 1) | 1, 0, Q | 1, (P + 1) * (Q | 1), 0,
+                    Q * Q + (((Q - (Q * Q) % 32) % 32) + 32) % 32, 0};
+}
+
+template <int P, int Q, bool DIFF>
+struct F32Smem {
+  static constexpr SmemPick K = smem_pick(P, Q, DIFF);
+  static constexpr int N = P + 1;
+  static constexpr int NC = DIFF ? 6 : 1;
+  static constexpr int Q3 = Q * Q * Q;
+  static constexpr int DSTRIDE = (Q3 + 3) & ~3;  // floats per stored D component (16-byte multiple)
+  static constexpr int DELEM = NC * DSTRIDE;     // floats of D per element
+  static constexpr int NC1 = DIFF ? 2 : 1;
+  static constexpr int NC2 = DIFF ? 3 : 1;
+  static constexpr int XL = K.xl;               // X [c][b][a]: line (b,c) at stride XL
+  static constexpr int XE = XL * N * N + K.xpad;  // X region per element
+  static constexpr int Q1 = K.q1;               // S1 [m][c][b][i]: entry (b,c,i) at b*Q1 + c*CS + i
+  static constexpr int CS = K.cs;
+  static constexpr int S1C = CS * N;            // one S1 component
+  static constexpr int W1 = NC1 * S1C + K.s1pad;  // S1 region per element
+  static constexpr int P2 = K.p2;               // S2 [m][c][j][i]: plane c at stride P2
+  static constexpr int S2C = P2 * N;            // one S2 component
+  static constexpr int W2 = NC2 * S2C + K.s2pad;  // S2 region per element
+  static_assert(XL >= N && Q1 >= Q && CS >= N * Q1 && P2 >= Q * Q, "layout strides");
+  static constexpr int TPE = Q * Q;
+  static constexpr int NE0 = (256 / TPE) > 0 ? (256 / TPE) : 1;
+};
+
 // Launch shape of variants 0-2.
 template <int P, int Q, bool DIFF, bool STAGE_D = true, int NE_DIV = 1>
-struct TmaShape : F32Layout<P, Q, DIFF> {
-  using L = F32Layout<P, Q, DIFF>;
+struct TmaShape : F32Smem<P, Q, DIFF> {
+  using L = F32Smem<P, Q, DIFF>;
   static constexpr int NE = (L::NE0 / NE_DIV) > 0 ? (L::NE0 / NE_DIV) : 1;
-  static constexpr int SMEM = 16 + NE * ((STAGE_D ? L::DELEM : 0) + L::XSZ + L::WORK) * 4;
+  static constexpr int SMEM = 16 + NE * ((STAGE_D ? L::DELEM : 0) + L::XE + L::W1 + L::W2) * 4;
 };
 
 // Launch shape of variant 3 (double-buffered D, x and map per block).
 template <int P, int Q, bool DIFF>
-struct PipeShape : F32Layout<P, Q, DIFF> {
-  using L = F32Layout<P, Q, DIFF>;
+struct PipeShape : F32Smem<P, Q, DIFF> {
+  using L = F32Smem<P, Q, DIFF>;
   static constexpr int NE = L::NE0;
   static constexpr int T = L::TPE * NE;
   static constexpr int IDX = NE * L::N * L::N * L::N;  // map entries per group
   static constexpr int IDXR = (IDX + T - 1) / T;       // per thread
-  static constexpr int SMEM = 16 + 2 * NE * L::DELEM * 4 + 2 * NE * L::XSZ * 4 + 2 * IDX * 4 + NE * L::WORK * 4;
+  static constexpr int SMEM = 16 + 2 * NE * L::DELEM * 4 + 2 * NE * L::XE * 4 + 2 * IDX * 4 + NE * (L::W1 + L::W2) * 4;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -196,7 +257,7 @@ __device__ __forceinline__ void stage_item(int tid, int el, int& e, int& line) {
 // stage 1 (x): line (b,c) -> S1[m][c][b][i] for all i
 template <int P, int Q, bool DIFF>
 __device__ __forceinline__ void f32_stage1(int tid, bool live, const float* sX, float* S1) {
-  using L = F32Layout<P, Q, DIFF>;
+  using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
   if (!(live && tid < n * n)) return;
@@ -221,7 +282,7 @@ __device__ __forceinline__ void f32_stage1(int tid, bool live, const float* sX, 
 //   DIFF: m=0 (x:G,y:B), m=1 (x:B,y:G), m=2 (x:B,y:B); mass: m=0 (B,B)
 template <int P, int Q, bool DIFF>
 __device__ __forceinline__ void f32_stage2(int tid, bool live, const float* S1, float* S2) {
-  using L = F32Layout<P, Q, DIFF>;
+  using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
   if (!(live && tid < Q * n)) return;
@@ -259,7 +320,7 @@ __device__ __forceinline__ void f32_stage2(int tid, bool live, const float* S1, 
 // PRE: the column's D was loaded into dpre[k * NCD + m] before the preceding barrier
 template <int P, int Q, bool DIFF, bool PRE = false>
 __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE, const float* dpre = nullptr) {
-  using L = F32Layout<P, Q, DIFF>;
+  using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
   if (!live) return;
@@ -338,7 +399,7 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
 //                             S1[1][c][b][i] = sum_j G[j][b] A1 + B[j][b] A2
 template <int P, int Q, bool DIFF>
 __device__ __forceinline__ void f32_stage2t(int tid, bool live, const float* S2, float* S1) {
-  using L = F32Layout<P, Q, DIFF>;
+  using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
   if (!(live && tid < Q * n)) return;
@@ -370,7 +431,7 @@ __device__ __forceinline__ void f32_stage2t(int tid, bool live, const float* S2,
 template <int P, int Q, bool DIFF>
 __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1, const int* gl,
                                             const float* __restrict__ x, float* __restrict__ y) {
-  using L = F32Layout<P, Q, DIFF>;
+  using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
   if (!(live && tid < n * n)) return;
@@ -417,8 +478,9 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_tma[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma);
   float* sD = reinterpret_cast<float*>(smem_tma + 16);
-  float* sXall = sD + (STAGE_D ? NE * S::DELEM : 0);
-  float* sWall = sXall + NE * S::XSZ;
+  float* sXall = sD + (STAGE_D ? NE * S::DELEM : 0);  // [NE][XE]
+  float* sS1 = sXall + NE * S::XE;                     // [NE][W1]
+  float* sS2 = sS1 + NE * S::W1;                       // [NE][W2]
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
@@ -433,9 +495,8 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     bulk_copy_g2s(sD, qd32 + e0 * S::DELEM, bytes, mbar);
   }
   const bool live = el < ne;
-  float* sX = sXall + el * S::XSZ;
-  float* S1 = sWall + el * S::WORK;
-  float* S2 = S1 + S::NC1 * S::S1C;
+  float* sX = sXall + el * S::XE;
+  float* S2 = sS2 + el * S::W2;
   const int* g = gmap + (e0 + el) * (n * n * n);
   if (live) {
     // gather: all map loads first, then all x loads, so the dependent pairs overlap
@@ -459,14 +520,13 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-    f32_stage1<P, Q, DIFF>(ln, e < ne, sXall + e * S::XSZ, sWall + e * S::WORK);
+    f32_stage1<P, Q, DIFF>(ln, e < ne, sXall + e * S::XE, sS1 + e * S::W1);
   }
   __syncthreads();
   {
     int e, ln;
     stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-    float* S1e = sWall + e * S::WORK;
-    f32_stage2<P, Q, DIFF>(ln, e < ne, S1e, S1e + S::NC1 * S::S1C);
+    f32_stage2<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, sS2 + e * S::W2);
   }
   // DEARLY: the stage-3 thread loads its whole D column before the barrier, so the loads
   // overlap the wait for the other threads' stage 2
@@ -498,14 +558,13 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   {
     int e, ln;
     stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-    float* S1e = sWall + e * S::WORK;
-    f32_stage2t<P, Q, DIFF>(ln, e < ne, S1e + S::NC1 * S::S1C, S1e);
+    f32_stage2t<P, Q, DIFF>(ln, e < ne, sS2 + e * S::W2, sS1 + e * S::W1);
   }
   __syncthreads();
   {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-    f32_stage1t<P, Q, DIFF>(ln, e < ne, sWall + e * S::WORK, gmap + (e0 + e) * (n * n * n), x, y);
+    f32_stage1t<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, gmap + (e0 + e) * (n * n * n), x, y);
   }
 }
 
@@ -525,12 +584,12 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
   extern __shared__ __align__(16) unsigned char smem_pipe[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_pipe);  // [2]
   float* sD = reinterpret_cast<float*>(smem_pipe + 16);     // [2][NE*DELEM]
-  float* sX = sD + 2 * NE * S::DELEM;                       // [2][NE*XSZ]
-  int* sI = reinterpret_cast<int*>(sX + 2 * NE * S::XSZ);   // [2][IDX]
-  float* sW = reinterpret_cast<float*>(sI + 2 * S::IDX);    // [NE][WORK]
+  float* sX = sD + 2 * NE * S::DELEM;                       // [2][NE][XE]
+  int* sI = reinterpret_cast<int*>(sX + 2 * NE * S::XE);    // [2][IDX]
+  float* sS1 = reinterpret_cast<float*>(sI + 2 * S::IDX);   // [NE][W1]
+  float* sS2 = sS1 + NE * S::W1;                            // [NE][W2]
   const int tid = threadIdx.x, el = threadIdx.y, flat = el * TPE + tid;
-  float* S1 = sW + el * S::WORK;
-  float* S2 = S1 + S::NC1 * S::S1C;
+  float* S2 = sS2 + el * S::W2;
 
   // D of group gg into buffer b (one thread)
   auto issue_d = [&](int gg, int b) {
@@ -561,7 +620,7 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
         const int gi = r[k];
         sI[b * S::IDX + f] = gi;
         const int e = f / n3, l = f - e * n3;
-        float* dst = sX + b * NE * S::XSZ + e * S::XSZ + (l / n) * S::XL + (l % n);
+        float* dst = sX + b * NE * S::XE + e * S::XE + (l / n) * S::XL + (l % n);
         if (gi >= 0)
           cp_async4(dst, x + gi);
         else
@@ -599,14 +658,13 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
     {
       int e, ln;
       stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-      f32_stage1<P, Q, DIFF>(ln, e < ne, sX + cur * NE * S::XSZ + e * S::XSZ, sW + e * S::WORK);
+      f32_stage1<P, Q, DIFF>(ln, e < ne, sX + cur * NE * S::XE + e * S::XE, sS1 + e * S::W1);
     }
     __syncthreads();
     {
       int e, ln;
       stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-      float* S1e = sW + e * S::WORK;
-      f32_stage2<P, Q, DIFF>(ln, e < ne, S1e, S1e + S::NC1 * S::S1C);
+      f32_stage2<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, sS2 + e * S::W2);
     }
     if (has_next) gather(gn, nxt, r);
     const uint32_t pc = cur ? ph1 : ph0, pn = cur ? ph0 : ph1;
@@ -626,14 +684,13 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
     {
       int e, ln;
       stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-      float* S1e = sW + e * S::WORK;
-      f32_stage2t<P, Q, DIFF>(ln, e < ne, S1e + S::NC1 * S::S1C, S1e);
+      f32_stage2t<P, Q, DIFF>(ln, e < ne, sS2 + e * S::W2, sS1 + e * S::W1);
     }
     __syncthreads();
     {
       int e, ln;
       stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-      f32_stage1t<P, Q, DIFF>(ln, e < ne, sW + e * S::WORK, sI + cur * S::IDX + e * n3, x, y);
+      f32_stage1t<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, sI + cur * S::IDX + e * n3, x, y);
     }
     __syncthreads();
     cur = nxt;

@@ -44,13 +44,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def oracle_action(mesh, p, form, x, ess=None):
+def oracle_action(mesh, p, form, x, ess=None, q=None):
+    q = p + 2 if q is None else q
     if p <= 5:
-        A = O.assemble_csr(mesh, p, p + 2, form)
+        A = O.assemble_csr(mesh, p, q, form)
         if ess is not None:
             A = O.constrain(A, ess)
         return A @ x
-    return O.action_elementwise(mesh, p, p + 2, form, x, ess=ess)
+    return O.action_elementwise(mesh, p, q, form, x, ess=ess)
 
 
 @pytest.mark.parametrize("form", ["mass", "diffusion"])
@@ -76,6 +77,28 @@ def test_every_f32_variant_matches_oracle(form, p, variant):
     y = op.apply_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
     assert op.f32_variant()[0] == variant
     assert rel(y, oracle_action(mesh, p, form, x32.astype(np.float64), ess=ess.astype(np.int64))) <= TOL32
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("form", ["mass", "diffusion"])
+@pytest.mark.parametrize("p", list(range(1, 9)))
+def test_f32_variants_with_q_p_plus_1(p, form, variant):
+    """Every variant at q = p + 1 (each (p, q, form) has its own shared-memory layout) on a
+    mesh of several blocks of elements with a ragged last block."""
+    shape = (5, 3, 2) if p <= 4 else (3, 2, 2)
+    op, mesh = make_q(shape, p, form, p + 1, seed=40 + p)
+    op.set_f32_variant(variant)
+    ess = op.boundary_dofs()
+    op.set_essential(ess)
+    x32 = FI.uniform_vector(op.N, seed=41 + p).astype(np.float32)
+    y = op.apply_f32(torch.from_numpy(x32).cuda()).cpu().numpy()
+    ref = oracle_action(mesh, p, form, x32.astype(np.float64), ess=ess.astype(np.int64), q=p + 1)
+    assert rel(y, ref) <= TOL32
+
+
+def make_q(shape, p, form, q, seed=0):
+    verts = FI.perturbed_cube_vertices(*shape, seed=seed)
+    return F().Operator(*shape, verts, p, form=form, q=q), O.HexGridMesh(*shape, verts)
 
 
 def test_autotuned_variant_is_recorded():
