@@ -498,6 +498,37 @@ def run_batch(args, rank, world, dist):
         ev1.record()
         torch.cuda.synchronize()
     t, work = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, dofit, dist, device="cuda")
+    launches64 = F.launch_count() - l0
+
+    # the same batch by batched mixed-precision refinement (FP32 corrections, FP64 residuals)
+    def step_refined():
+        x.zero_()
+        _, st = bt.solve_refined(b, x, rtol=args.rtol, inner_rtol=args.inner_rtol)
+        return st
+
+    for _ in range(args.warmup):
+        step_refined()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    l1 = F.launch_count()
+    dofit32, maxin, outer = 0.0, [], []
+    with ClockSampler(local) as clk32:
+        ev0.record()
+        for _ in range(args.steps):
+            st = step_refined()
+            dofit32 += st["dof_iterations"]
+            maxin.append(int(st["max_inner_iterations"]))
+            outer.append(int(st["outer_iterations"]))
+        ev1.record()
+        torch.cuda.synchronize()
+    t32, work32 = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, dofit32, dist, device="cuda")
+    refined = {"solver": "FP64 iterative refinement (per-problem FP64 residual and stop) around batched FP32 "
+                         f"Jacobi-PCG corrections (inner rtol {args.inner_rtol}), one CUDA-graph loop per step",
+               "ms_per_step": 1e3 * t32 / args.steps, "solves_per_s": args.batch_count * world * args.steps / t32,
+               "gdofs_per_fp32_iter": work32 / t32 / 1e9, "max_inner_iterations_per_step": maxin,
+               "outer_iterations_per_step": outer, "time_to_solution_speedup_vs_fp64": t / t32,
+               "gpu_launches": F.launch_count() - l1, "clocks": clk32.summary()}
     if rank == 0:
         line = {"metric": "batched BP1/BP3 solves: GDOF/s per CG iter", "value": work / t / 1e9, "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -509,7 +540,7 @@ def run_batch(args, rank, world, dist):
                            "total_dofs": bt.N, "groups": bt.groups},
                 "solves_per_s": args.batch_count * world * args.steps / t,
                 "max_iterations_per_step": maxits, "setup_s": setup_s,
-                "gpu_launches": F.launch_count() - l0, "clocks": clk.summary()}
+                "gpu_launches": launches64, "clocks": clk.summary(), "mixed_refined": refined}
         print(json.dumps(line), flush=True)
     return 0
 

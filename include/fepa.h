@@ -395,6 +395,35 @@ int fepa_batch_apply(fepa_batch* batch, const double* x, double* y);
 int fepa_batch_solve(fepa_batch* batch, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
                      fepa_batch_stats* stats, int32_t* iterations);
 
+typedef struct fepa_batch_refine_stats {
+  int32_t max_inner_iterations;  /* FP32 iterations of the problem that needed the most (all steps) */
+  int32_t converged;             /* problems whose FP64 residual reached rtol */
+  int32_t status;                /* FEPA_OK when all did, else FEPA_ERR_NOCONV */
+  int32_t outer_iterations;      /* refinement steps taken (FP32 correction solves) */
+  double dof_iterations;         /* sum over problems of N_i * FP32 iterations_i */
+  double max_rel_residual;       /* largest FP64 ||b_i - A x_i|| / ||b_i|| at exit */
+} fepa_batch_refine_stats;
+
+/*
+ * Mixed-precision solve of every problem, all at once: FP64 iterative refinement around
+ * FP32 Jacobi-PCG corrections, as fepa_solve_refined does for one operator, over the
+ * batch of fepa_batch_solve (the operator and solver of Fig. fig_feod, Sec. 2.1, 2.3;
+ * the mixed precision is this library's addition).
+ * Each step computes every problem's FP64 residual b_i - A x_i with the FP64 action;
+ * problems at ||r_i|| <= rtol ||b_i|| are finished and do no further work (their elements
+ * are skipped by the FP32 action); the others solve A e_i = r_i in FP32 to relative
+ * tolerance inner_rtol (relaxed on a problem's last step to what reaching rtol needs) or
+ * inner_maxit iterations, in one CUDA-graph loop over the batch, and x_i += e_i.
+ *   b, x        device, total DOFs (x: initial guesses in, solutions out, updated in place)
+ *   iterations  host int32 [count]: FP32 iterations of each problem over all steps (may be null)
+ * The first call builds an FP32 copy of every group's D (half the FP64 D's size).
+ * FEPA_ERR_NOCONV if a problem has not reached rtol after max_outer steps;
+ * FEPA_ERR_TIMEOUT if an FP32 action kernel gave up its bounded wait.
+ */
+int fepa_batch_solve_refined(fepa_batch* batch, const double* b, double* x, double rtol, int32_t max_outer,
+                             double inner_rtol, int32_t inner_maxit, int32_t precond,
+                             fepa_batch_refine_stats* stats, int32_t* iterations);
+
 /* ---------------------------------------------------------------------------
  * p-multigrid preconditioner (Sec. 2.1: a hierarchy of orders on one mesh, transfers
  * between them by sum factorisation, diagonal-based smoothers with Chebyshev

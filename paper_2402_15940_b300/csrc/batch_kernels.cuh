@@ -185,6 +185,184 @@ bcg_direction(ChunkTable t, const double* __restrict__ r, double* __restrict__ d
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched mixed-precision refinement: per problem, FP64 residual -> FP32 Jacobi-PCG
+// correction (per-problem stop) -> FP64 update, as the single-problem refinement.  The
+// FP32 kernels mirror the FP64 ones above with FP32 vectors and two-float dot products.
+// ---------------------------------------------------------------------------
+
+// r32 = b - h rounded to FP32 (h = A x from the FP64 action); per problem rr = ||r||^2,
+// bb = ||b||^2 into pr; a problem whose rr <= rtol2 bb is finished (pdone = 1).
+__global__ void __launch_bounds__(RED_THREADS)
+bref_residual(ChunkTable t, const double* __restrict__ b, const double* __restrict__ h, float* __restrict__ r32,
+              BState* pr, int* pdone, BGlobal* gs, double rtol2, double* partials) {
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double bi = b[i];
+    const double ri = bi - h[i];
+    r32[i] = (float)ri;
+    v[0] += ri * ri;
+    v[1] += bi * bi;
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
+      BState& q = pr[j];
+      q.rr = s[0];
+      q.bb = s[1];
+      q.converged = s[0] <= rtol2 * s[1] ? 1 : 0;
+      pdone[j] = q.converged;
+      return !q.converged;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+// Start of the FP32 correction solves A e = r: e = 0, d = z, h = 0 everywhere; for every
+// problem not finished, rho = (z, r), rr = (r, r) and the stop at rr <= tol^2 ||r||^2 with
+// tol = inner_tol(inner_rtol, rtol, its outer residual).
+__global__ void __launch_bounds__(RED_THREADS)
+bcg32_init(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, float* __restrict__ d,
+           float* __restrict__ h, const float* __restrict__ inv_diag, BState* ps, const BState* __restrict__ pr,
+           int* pdone, BGlobal* gs, double inner_rtol, double rtol, int maxit, double* partials) {
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float ri = r[i];
+    const float zi = inv_diag ? ri * inv_diag[i] : ri;
+    e[i] = 0.f;
+    d[i] = zi;
+    h[i] = 0.f;
+    f2_add_prod(zr_h, zr_l, zi, ri);
+    f2_add_prod(rr_h, rr_l, ri, ri);
+  }
+  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
+      BState& q = ps[j];
+      q.iter = 0;
+      q.maxit = maxit;
+      q.alpha = q.beta = 0.0;
+      q.rho = s[0];
+      q.rr = s[1];
+      q.bb = s[1];
+      if (pdone[j]) {  // finished by the outer test: no correction
+        q.converged = 1;
+        q.tol2 = 0.0;
+        return false;
+      }
+      const double rel = pr[j].bb > 0.0 ? sqrt(pr[j].rr / pr[j].bb) : 0.0;
+      const double tol = inner_tol(inner_rtol, rtol, rel);
+      q.tol2 = tol * tol * s[1];
+      q.converged = s[1] <= q.tol2 ? 1 : 0;
+      pdone[j] = q.converged;
+      return !q.converged;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+bcg32_dot_dh(ChunkTable t, const float* __restrict__ d, const float* __restrict__ h, BState* ps,
+             const int* __restrict__ pdone, BGlobal* gs, double* partials) {
+  if (gs->done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  float s_h = 0.f, s_l = 0.f;
+  if (!pdone[prob]) {
+    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) f2_add_prod(s_h, s_l, d[i], h[i]);
+  }
+  double v[1] = {f2_value(s_h, s_l)};
+  double blk[1];
+  block_sum<1>(v, blk);
+  if (publish_partials<1>(blk, partials, &gs->ticket)) {
+    per_problem<1>(t, partials, [&](int j, const double* s) {
+      if (!pdone[j]) ps[j].alpha = ps[j].rho / s[0];
+      return false;
+    });
+    if (threadIdx.x == 0) gs->ticket = 0;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const float* __restrict__ d,
+             const float* __restrict__ h, const float* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
+             double* partials) {
+  if (gs->done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+  if (!pdone[prob]) {
+    const float alpha = (float)ps[prob].alpha;
+    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      e[i] = fmaf(alpha, d[i], e[i]);
+      const float ri = fmaf(-alpha, h[i], r[i]);
+      r[i] = ri;
+      const float zi = inv_diag ? ri * inv_diag[i] : ri;
+      f2_add_prod(zr_h, zr_l, zi, ri);
+      f2_add_prod(rr_h, rr_l, ri, ri);
+    }
+  }
+  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
+      if (pdone[j]) return false;
+      BState& q = ps[j];
+      q.iter += 1;
+      q.rr = s[1];
+      int stop = 0;
+      if (s[1] <= q.tol2) {
+        q.converged = 1;
+        stop = 1;
+      } else if (q.iter >= q.maxit) {
+        stop = 1;
+      }
+      q.beta = s[0] / q.rho;
+      q.rho = s[0];
+      pdone[j] = stop;
+      return !stop;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+// d = z + beta d, h = 0 for problems still iterating; block 0 sets the while-condition
+__global__ void __launch_bounds__(RED_THREADS)
+bcg32_direction(ChunkTable t, const float* __restrict__ r, float* __restrict__ d, float* __restrict__ h,
+                const float* __restrict__ inv_diag, const BState* ps, const int* __restrict__ pdone,
+                const BGlobal* gs, cudaGraphConditionalHandle cond, int use_cond) {
+  const int done = gs->done;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (done) return;
+  const int prob = t.blk_prob[blockIdx.x];
+  if (pdone[prob]) return;
+  const float beta = (float)ps[prob].beta;
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+    d[i] = fmaf(beta, d[i], zi);
+    h[i] = 0.f;
+  }
+}
+
 // 1 on the boundary DOFs of one problem's node grid (concatenated numbering)
 __global__ void mark_boundary(int64_t Nx, int64_t Ny, int64_t Nz, int64_t dof_off, unsigned char* __restrict__ mask) {
   const int64_t total = Nx * Ny * Nz;

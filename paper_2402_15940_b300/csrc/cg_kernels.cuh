@@ -222,6 +222,13 @@ namespace fepa {
 // exact sums by TwoSum), i.e. to about 48 significant bits on the FP32 pipe, then
 // combined across threads and blocks in FP64.  Scalars (alpha, beta, rho) stay FP64.
 // ---------------------------------------------------------------------------
+// Inner tolerance of a refinement step at outer residual rel: inner_rtol, relaxed when
+// less is enough to reach rtol (the last correction: 0.25 rtol / rel, at most 0.5)
+__host__ __device__ inline double inner_tol(double inner_rtol, double rtol, double rel) {
+  const double need = rel > 0.0 ? 0.25 * rtol / rel : inner_rtol;
+  return need > inner_rtol ? (need < 0.5 ? need : 0.5) : inner_rtol;
+}
+
 __device__ __forceinline__ void f2_add_prod(float& hi, float& lo, float a, float b) {
   const float p = __fmul_rn(a, b);
   const float pe = __fmaf_rn(a, b, -p);   // a*b - p exactly

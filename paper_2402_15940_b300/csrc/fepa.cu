@@ -88,7 +88,8 @@ inline int grid_for(int64_t work, int threads, int cap) {
 template <typename R>
 using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*, const int*,
                          const int*);
-using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, int*);
+using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, const int*, const int*,
+                           int*);
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
 constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
@@ -365,7 +366,7 @@ int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const i
   const int grid = op->v32_grid[v];
   if (grid <= 0) return fail(FEPA_ERR_UNSUPPORTED, "FP32 variant %d cannot run with this shape", v);
   k.fn<<<grid, dim3(op->ks.apply_tpe, k.threads_y), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip,
-                                                                  op->err);
+                                                                  nullptr, nullptr, op->err);
   BODY_CHECK();
   return FEPA_OK;
 }
@@ -836,13 +837,8 @@ int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int 
   return FEPA_OK;
 }
 
-// Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG.
-// Inner tolerance of a refinement step at outer residual rel: inner_rtol, relaxed when
-// less is enough to reach rtol (the last correction: 0.25 rtol / rel, at most 0.5)
-double inner_tol(double inner_rtol, double rtol, double rel) {
-  const double need = rel > 0.0 ? 0.25 * rtol / rel : inner_rtol;
-  return need > inner_rtol ? (need < 0.5 ? need : 0.5) : inner_rtol;
-}
+// Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG (the inner
+// tolerance of each step: inner_tol in cg_kernels.cuh).
 
 int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_outer, double inner_rtol,
                 int inner_maxit, int precond, fepa_refine_stats* stats) {

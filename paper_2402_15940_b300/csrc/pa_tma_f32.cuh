@@ -471,7 +471,8 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3)>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
-                 float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
+                 float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
+                 const int* __restrict__ prob_done, int* __restrict__ err) {
   using S = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
   if (skip && *skip) return;
@@ -484,6 +485,10 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+  // batched problems (elem_prob, prob_done): the elements of a converged problem do no
+  // work, and a block whose elements all belong to converged problems leaves at once
+  auto alive = [&](int e) { return e < ne && !(elem_prob && prob_done[elem_prob[e0 + e]]); };
+  if (elem_prob && !__syncthreads_or(alive(el))) return;
   if (PF > 0 && tid == 0 && el == 0) {
     if (!STAGE_D) prefetch_range(qd32 + e0 * S::DELEM, (size_t)ne * S::DELEM * 4u);
     if (PF >= 2) prefetch_range(gmap + e0 * (n * n * n), 4u * (size_t)ne * n * n * n);
@@ -494,7 +499,7 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     mbar_expect_tx(mbar, bytes);
     bulk_copy_g2s(sD, qd32 + e0 * S::DELEM, bytes, mbar);
   }
-  const bool live = el < ne;
+  const bool live = alive(el);
   float* sX = sXall + el * S::XE;
   float* S2 = sS2 + el * S::W2;
   const int* g = gmap + (e0 + el) * (n * n * n);
@@ -520,13 +525,13 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-    f32_stage1<P, Q, DIFF>(ln, e < ne, sXall + e * S::XE, sS1 + e * S::W1);
+    f32_stage1<P, Q, DIFF>(ln, alive(e), sXall + e * S::XE, sS1 + e * S::W1);
   }
   __syncthreads();
   {
     int e, ln;
     stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-    f32_stage2<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, sS2 + e * S::W2);
+    f32_stage2<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, sS2 + e * S::W2);
   }
   // DEARLY: the stage-3 thread loads its whole D column before the barrier, so the loads
   // overlap the wait for the other threads' stage 2
@@ -558,23 +563,25 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   {
     int e, ln;
     stage_item<FLAT, Q * n, TPE>(tid, el, e, ln);
-    f32_stage2t<P, Q, DIFF>(ln, e < ne, sS2 + e * S::W2, sS1 + e * S::W1);
+    f32_stage2t<P, Q, DIFF>(ln, alive(e), sS2 + e * S::W2, sS1 + e * S::W1);
   }
   __syncthreads();
   {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-    f32_stage1t<P, Q, DIFF>(ln, e < ne, sS1 + e * S::W1, gmap + (e0 + e) * (n * n * n), x, y);
+    f32_stage1t<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, gmap + (e0 + e) * (n * n * n), x, y);
   }
 }
 
 // ---------------------------------------------------------------------------
-// variant 3: persistent, software-pipelined over element groups
+// variant 3: persistent, software-pipelined over element groups (elem_prob and
+// prob_done are not read: the batched solve does not select this variant)
 // ---------------------------------------------------------------------------
 template <int P, int Q, bool DIFF, bool FLAT = (P <= 4)>
 __global__ void __launch_bounds__(PipeShape<P, Q, DIFF>::T)
 pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
-                  float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
+                  float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
+                  const int* __restrict__ prob_done, int* __restrict__ err) {
   using S = PipeShape<P, Q, DIFF>;
   constexpr int n = S::N, n3 = n * n * n, TPE = S::TPE, NE = S::NE, T = S::T;
   if (skip && *skip) return;

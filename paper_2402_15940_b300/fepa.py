@@ -53,6 +53,15 @@ class BatchStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class BatchRefineStats(ctypes.Structure):
+    _fields_ = [("max_inner_iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("dof_iterations", ctypes.c_double), ("max_rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SolverState(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("outer_iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
@@ -114,6 +123,8 @@ SIGNATURES = [
     ("fepa_batch_set_f64_variant", ctypes.c_int, [_P, _I32]),
     ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
     ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
+    ("fepa_batch_solve_refined", ctypes.c_int,
+     [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(BatchRefineStats), _P]),
     ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     ("fepa_mg_update", ctypes.c_int, [_P]),
     ("fepa_mg_destroy", None, [_P]),
@@ -516,6 +527,26 @@ class Batch:
         rc = self._lib.fepa_batch_solve(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
                                         _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(maxit),
                                         _PRECONDS[precond], ctypes.byref(st), its.ctypes.data_as(ctypes.c_void_p))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        d = st.as_dict()
+        d["iterations"] = its
+        return x, d
+
+    def solve_refined(self, b, x=None, rtol=1e-10, max_outer=50, inner_rtol=1e-4, inner_maxit=20000,
+                      precond="jacobi", raise_on_noconv=True):
+        """FP64 iterative refinement around batched FP32 Jacobi-PCG corrections (every problem
+        to rtol on its FP64 residual); stats["iterations"]: FP32 iterations per problem."""
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = BatchRefineStats()
+        its = np.zeros(self.count, dtype=np.int32)
+        self._sync_stream()
+        rc = self._lib.fepa_batch_solve_refined(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                                _dev_ptr(x, torch.float64, self.N, "x"), float(rtol),
+                                                int(max_outer), float(inner_rtol), int(inner_maxit),
+                                                _PRECONDS[precond], ctypes.byref(st),
+                                                its.ctypes.data_as(ctypes.c_void_p))
         if rc != ERR_NOCONV or raise_on_noconv:
             _check(rc)
         d = st.as_dict()

@@ -148,3 +148,101 @@ def test_batch_512_problem_mix_sampled():
         Ax = O.action_rows(mesh, pr["p"], pr["p"] + 2, pr["form"], x[sl], rows,
                            ess=None if ess is None else ess.astype(np.int64))
         assert np.max(np.abs(b[sl][rows] - Ax)) <= 1e-10 * np.linalg.norm(b[sl])
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision batched solve: FP64 refinement around batched FP32 Jacobi-PCG.
+# The FP64 residual decides each problem's stop, so every solution is checked to the
+# same 1e-10 residual and 1e-9 solution tolerance as the FP64 batch; FP32 iteration
+# counts depend on the atomic summation order of the FP32 action and are compared
+# loosely (within 10 % or 4 of the problem solved alone).
+# ---------------------------------------------------------------------------
+def test_batch_refined_matches_oracle_and_alone():
+    probs = small_mix(seed=2, count=12)
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets)
+    x, st = bt.solve_refined(torch.from_numpy(b).cuda(), rtol=1e-10)
+    x = x.cpu().numpy()
+    assert st["converged"] == len(probs) and st["status"] == 0
+    assert st["max_rel_residual"] <= 1e-10 and st["outer_iterations"] >= 1
+    its = st["iterations"]
+    assert st["max_inner_iterations"] == its.max()
+    sizes = np.diff(bt.offsets)
+    assert st["dof_iterations"] == pytest.approx(float(np.dot(sizes, its)))
+    for i, pr in enumerate(probs):
+        sl = slice(bt.offsets[i], bt.offsets[i + 1])
+        xo, _, _ = oracle_problem(pr).solve(b[sl], rtol=1e-12)
+        assert rel(x[sl], xo) <= 1e-9, i
+        op = F().Operator(*pr["n"], pr["vertices"], pr["p"], form=pr["form"])
+        if pr["form"] == "diffusion":
+            op.set_essential(op.boundary_dofs())
+        xa, sa = op.solve_refined(torch.from_numpy(np.ascontiguousarray(b[sl])).cuda(), rtol=1e-10)
+        assert abs(sa["inner_iterations"] - int(its[i])) <= max(4, 0.1 * sa["inner_iterations"]), i
+        assert rel(x[sl], xa.cpu().numpy()) <= 1e-9, i
+
+
+def test_batch_refined_skips_finished_problems():
+    """A zero right-hand side and an exact initial guess finish before any FP32 step (no
+    iterations); the others still converge, and repeated solves reuse the FP32 data."""
+    probs = small_mix(seed=3, count=6)
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets, seed=9)
+    b[bt.offsets[1]:bt.offsets[2]] = 0.0
+    x_ref, _ = bt.solve(torch.from_numpy(b).cuda(), rtol=1e-12)
+    x0 = torch.zeros(bt.N, dtype=torch.float64, device="cuda")
+    sl4 = slice(int(bt.offsets[4]), int(bt.offsets[5]))
+    x0[sl4] = x_ref[sl4]
+    x, st = bt.solve_refined(torch.from_numpy(b).cuda(), x=x0, rtol=1e-10)
+    its = st["iterations"]
+    assert its[1] == 0 and its[4] == 0
+    # the others iterate unless all their DOFs are on the boundary (b_i = 0 there too)
+    live = [i for i in (0, 2, 3, 5) if np.any(b[bt.offsets[i]:bt.offsets[i + 1]] != 0.0)]
+    assert len(live) >= 3 and all(its[i] > 0 for i in live)
+    assert all(its[i] == 0 for i in (0, 2, 3, 5) if i not in live)
+    assert st["converged"] == len(probs) and st["max_rel_residual"] <= 1e-10
+    assert float(torch.abs(x[bt.offsets[1]:bt.offsets[2]]).max()) == 0.0
+    x2, st2 = bt.solve_refined(torch.from_numpy(b).cuda(), rtol=1e-10)
+    assert st2["converged"] == len(probs)
+    assert rel(x2.cpu().numpy(), x_ref.cpu().numpy()) <= 1e-9
+
+
+def test_batch_refined_noconv_and_arguments():
+    probs = small_mix(seed=5, count=4)
+    bt = F().Batch(probs)
+    b = torch.from_numpy(rhs_for(probs, bt.offsets)).cuda()
+    from paper_2402_15940_b300.fepa import ERR_NOCONV
+    x, st = bt.solve_refined(b, rtol=1e-14, max_outer=1, inner_maxit=3, raise_on_noconv=False)
+    assert st["status"] == ERR_NOCONV and st["converged"] < len(probs)
+    assert st["outer_iterations"] == 1 and st["max_inner_iterations"] <= 3
+    with pytest.raises(F().FepaError):
+        bt.solve_refined(b, max_outer=1, inner_maxit=3, rtol=1e-14)
+    for kw in ({"inner_rtol": 0.0}, {"inner_rtol": 1.0}, {"max_outer": 0}, {"inner_maxit": 0}, {"rtol": -1.0}):
+        with pytest.raises(F().FepaError):
+            bt.solve_refined(b, **kw)
+
+
+def test_batch_refined_512_problem_mix_sampled():
+    """The 512-problem mix of the FP64 batch test solved by batched mixed-precision
+    refinement: every problem reaches 1e-10 on its FP64 residual; sampled problems match
+    the FP64 batch solution and, on sampled rows, the oracle's residual."""
+    mix = FI.problem_mix(512, seed=0)
+    probs = [{"n": m["n"], "p": m["p"], "form": m["form"],
+              "vertices": FI.perturbed_cube_vertices(*m["n"], seed=m["mesh_seed"])} for m in mix]
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets, seed=11)
+    bd = torch.from_numpy(b).cuda()
+    x, st = bt.solve_refined(bd, rtol=1e-10)
+    assert st["converged"] == 512 and st["max_rel_residual"] <= 1e-10
+    x64, _ = bt.solve(bd, rtol=1e-10, maxit=20000)
+    x, x64 = x.cpu().numpy(), x64.cpu().numpy()
+    rng = np.random.default_rng(6)
+    for i in rng.choice(512, 6, replace=False):
+        pr = probs[i]
+        sl = slice(bt.offsets[i], bt.offsets[i + 1])
+        assert rel(x[sl], x64[sl]) <= 1e-8, i
+        mesh = O.HexGridMesh(*pr["n"], pr["vertices"])
+        n_i = int(bt.offsets[i + 1] - bt.offsets[i])
+        rows = rng.choice(n_i, min(n_i, 20), replace=False)
+        ess = O.boundary_dofs(mesh, pr["p"]).astype(np.int64) if pr["form"] == "diffusion" else None
+        Ax = O.action_rows(mesh, pr["p"], pr["p"] + 2, pr["form"], x[sl], rows, ess=ess)
+        assert np.max(np.abs(b[sl][rows] - Ax)) <= 1e-10 * np.linalg.norm(b[sl])
