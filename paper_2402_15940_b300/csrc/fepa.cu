@@ -111,6 +111,7 @@ struct KernelSet {
   void (*rhs_df)(int, int, int, const float2*, const int*, const double*, double, double*);
   int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
+  Apply32Variant v32_batch;  // variant 2 built to skip the elements of converged batch problems
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   int apply_smem, apply_tpe, apply_ne;
   int d32_stride;
@@ -136,6 +137,9 @@ KernelSet make_set() {
               TmaShape<P, Q, DIFF, false, 1>::NE, TmaShape<P, Q, DIFF, false, 1>::NE, false};
   k.v32[2] = {pa_apply_f32_tma<P, Q, DIFF, false, 2>, TmaShape<P, Q, DIFF, false, 2>::SMEM,
               TmaShape<P, Q, DIFF, false, 2>::NE, TmaShape<P, Q, DIFF, false, 2>::NE, false};
+  k.v32_batch = {pa_apply_f32_tma<P, Q, DIFF, false, 2, 2, (P <= 4), (P <= 3), true>,
+                 TmaShape<P, Q, DIFF, false, 2>::SMEM, TmaShape<P, Q, DIFF, false, 2>::NE,
+                 TmaShape<P, Q, DIFF, false, 2>::NE, false};
   k.v32[3] = {pa_apply_f32_pipe<P, Q, DIFF>, PipeShape<P, Q, DIFF>::SMEM, PipeShape<P, Q, DIFF>::NE,
               PipeShape<P, Q, DIFF>::NE, true};
 

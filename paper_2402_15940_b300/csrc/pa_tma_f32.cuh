@@ -468,7 +468,10 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 // 2 = also its map entries.  Measured on B300: 4-11 % faster for p = 2..8 (PF 2 best).
 // DEARLY (measured): loading the stage-3 D column before the barrier is 3-6 % faster for
 // p <= 3 and 3-17 % slower from p = 4 (the 6 q registers it holds cost occupancy there).
-template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3)>
+// BSKIP: the batched build, which reads elem_prob / prob_done (a separate instantiation, so
+// the single-operator kernels carry none of its checks: they cost those 5 % when tested).
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3),
+          bool BSKIP = false>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
@@ -485,10 +488,10 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   const int tid = threadIdx.x, el = threadIdx.y;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
-  // batched problems (elem_prob, prob_done): the elements of a converged problem do no
-  // work, and a block whose elements all belong to converged problems leaves at once
-  auto alive = [&](int e) { return e < ne && !(elem_prob && prob_done[elem_prob[e0 + e]]); };
-  if (elem_prob && !__syncthreads_or(alive(el))) return;
+  // batched problems (BSKIP): the elements of a converged problem do no work, and a block
+  // whose elements all belong to converged problems leaves at once
+  auto alive = [&](int e) { return e < ne && !(BSKIP && prob_done[elem_prob[e0 + e]]); };
+  if (BSKIP && !__syncthreads_or(alive(el))) return;
   if (PF > 0 && tid == 0 && el == 0) {
     if (!STAGE_D) prefetch_range(qd32 + e0 * S::DELEM, (size_t)ne * S::DELEM * 4u);
     if (PF >= 2) prefetch_range(gmap + e0 * (n * n * n), 4u * (size_t)ne * n * n * n);
