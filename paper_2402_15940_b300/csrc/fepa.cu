@@ -194,6 +194,38 @@ int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vec
   const size_t slot = (size_t)((p - 1) * 2 + (q - p - 1)) * TAB_SLOT * 2;
   CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float), slot * sizeof(float),
                                    cudaMemcpyHostToDevice, s));
+  if (q != p + 2) return FEPA_OK;
+  // even/odd tables of B, G (q x n) and B^T, G^T (n x q) for the double-float action
+  std::vector<float> teo(4 * EO_MAT * 2, 0.f);
+  auto put = [&](int mat, int k, double v) {
+    const float h = (float)v;
+    teo[2 * (mat * EO_MAT + k)] = h;
+    teo[2 * (mat * EO_MAT + k) + 1] = (float)(v - (double)h);
+  };
+  for (int mat = 0; mat < 4; ++mat) {
+    const std::vector<double>& M = (mat % 2 == 0) ? Bh : Gh;
+    const int NO = mat < 2 ? q : n, NI = mat < 2 ? n : q, HO = NO / 2, HI = NI / 2;
+    const double S = (mat % 2 == 0) ? 1.0 : -1.0;
+    auto m = [&](int o, int i) { return mat < 2 ? M[o * n + i] : M[i * n + o]; };  // B(q, a) at q*n + a
+    double scale = 0.0;
+    for (int o = 0; o < NO; ++o)
+      for (int i = 0; i < NI; ++i) scale = std::max(scale, fabs(m(o, i)));
+    for (int o = 0; o < NO; ++o)
+      for (int i = 0; i < NI; ++i)
+        if (fabs(m(NO - 1 - o, NI - 1 - i) - S * m(o, i)) > 1e-13 * scale)
+          return fail(FEPA_ERR_CUDA, "1D tables of p=%d q=%d are not symmetric", p, q);
+    for (int o = 0; o < HO; ++o)
+      for (int i = 0; i < HI; ++i) {
+        put(mat, o * HI + i, 0.5 * (m(o, i) + m(o, NI - 1 - i)));
+        put(mat, HO * HI + o * HI + i, 0.5 * (m(o, i) - m(o, NI - 1 - i)));
+      }
+    if (NI % 2)
+      for (int o = 0; o < HO; ++o) put(mat, 2 * HO * HI + o, m(o, HI));
+    if (NO % 2)
+      for (int i = 0; i <= HI && i < NI; ++i) put(mat, 2 * HO * HI + HO + i, m(HO, i));
+  }
+  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabeo, teo.data(), teo.size() * sizeof(float),
+                                   (size_t)(p - 1) * 4 * EO_MAT * 2 * sizeof(float), cudaMemcpyHostToDevice, s));
   return FEPA_OK;
 }
 

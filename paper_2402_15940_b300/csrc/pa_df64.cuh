@@ -95,6 +95,70 @@ __device__ __forceinline__ dfl df_recip(dfl b) {
 // tables of every compiled (P, Q) as (hi, lo) pairs: slot as in c_tab32
 __constant__ float c_tabdf[TAB_SLOT * TAB_SLOTS * 2];
 
+// Even/odd form of the 1D contractions (q = p + 2).  The GLL nodes and the Gauss points are
+// symmetric about 1/2, so B(Q-1-q, n-1-a) = B(q, a) and G(Q-1-q, n-1-a) = -G(q, a).  For a
+// matrix M with M(NO-1-o, NI-1-i) = S M(o, i) (S = +1 for B and B^T, -1 for G and G^T):
+// with x+_i = x_i + x_{NI-1-i}, x-_i = x_i - x_{NI-1-i} (i < NI/2) and x_mid the middle
+// input when NI is odd,
+//   E_o = sum_i e(o,i) x+_i + M(o, mid) x_mid,  e(o,i) = (M(o,i) + M(o,NI-1-i)) / 2
+//   O_o = sum_i d(o,i) x-_i,                      d(o,i) = (M(o,i) - M(o,NI-1-i)) / 2
+//   y_o = E_o + O_o,  y_{NO-1-o} = S (E_o - O_o)   (o < NO/2),
+// and for odd NO the middle output is sum_i M(mid, i) x(+ or -)_i (+ M(mid, mid) x_mid
+// when S = +1): half the multiply-adds of the direct form for n + Q extra additions.
+// Tables per q = p + 2 slot (p - 1): matrices 0 B, 1 G (Q x n), 2 B^T, 3 G^T (n x Q), each
+// EO_MAT (hi, lo) pairs: e (NO/2 x NI/2), d, M(o, mid) (o < NO/2), M(mid, i) (i <= NI/2).
+constexpr int EO_MAT = 52;
+__constant__ float c_tabeo[FEPA_MAX_ORDER * 4 * EO_MAT * 2];
+
+template <int P, int MAT>
+struct TabEo {
+  static constexpr int NO = MAT < 2 ? P + 2 : P + 1, NI = MAT < 2 ? P + 1 : P + 2;
+  static constexpr int HO = NO / 2, HI = NI / 2;
+  static_assert(2 * HO * HI + HO + HI + 1 <= EO_MAT, "even/odd table size");
+  static constexpr int OFF = ((P - 1) * 4 + MAT) * EO_MAT * 2;
+  static __device__ __forceinline__ dfl at(int k) { return {c_tabeo[OFF + 2 * k], c_tabeo[OFF + 2 * k + 1]}; }
+  static __device__ __forceinline__ dfl E(int o, int i) { return at(o * HI + i); }
+  static __device__ __forceinline__ dfl D(int o, int i) { return at(HO * HI + o * HI + i); }
+  static __device__ __forceinline__ dfl MC(int o) { return at(2 * HO * HI + o); }
+  static __device__ __forceinline__ dfl MR(int i) { return at(2 * HO * HI + HO + i); }
+};
+
+// x+ and x- of the mirrored input pairs
+template <int NI>
+__device__ __forceinline__ void eo_split(const dfl (&x)[NI], dfl (&xp)[NI / 2], dfl (&xm)[NI / 2]) {
+#pragma unroll
+  for (int i = 0; i < NI / 2; ++i) {
+    xp[i] = df_add(x[i], x[NI - 1 - i]);
+    xm[i] = df_sub(x[i], x[NI - 1 - i]);
+  }
+}
+
+// y = M x from the split input (outputs normalised)
+template <class TE, int S>
+__device__ __forceinline__ void eo_apply(const dfl (&xp)[TE::HI], const dfl (&xm)[TE::HI], dfl xmid,
+                                         dfl (&y)[TE::NO]) {
+  constexpr int HO = TE::HO, HI = TE::HI, NO = TE::NO, NI = TE::NI;
+#pragma unroll
+  for (int o = 0; o < HO; ++o) {
+    dfl e = df_zero(), d = df_zero();
+#pragma unroll
+    for (int i = 0; i < HI; ++i) {
+      df_fma(e, TE::E(o, i), xp[i]);
+      df_fma(d, TE::D(o, i), xm[i]);
+    }
+    if (NI % 2) df_fma(e, TE::MC(o), xmid);
+    y[o] = df_add(e, d);
+    y[NO - 1 - o] = S > 0 ? df_sub(e, d) : df_sub(d, e);
+  }
+  if (NO % 2) {
+    dfl m = df_zero();
+#pragma unroll
+    for (int i = 0; i < HI; ++i) df_fma(m, TE::MR(i), S > 0 ? xp[i] : xm[i]);
+    if (S > 0 && NI % 2) df_fma(m, TE::MR(HI), xmid);
+    y[HO] = df_norm(m);
+  }
+}
+
 template <int P, int Q>
 struct TabDf {
   static constexpr int OFF = ((P - 1) * 2 + (Q - P - 1)) * TAB_SLOT * 2;
@@ -142,6 +206,13 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   using T = TabDf<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
   constexpr int DQ1 = Q | 1;  // S1 line stride (odd), within the FP32 layout's S1 component size
+  // even/odd line contractions (tables for q = p + 2; at p = 1 the extra additions cost more
+  // than the halved multiply-adds save: measured 2 % slower there, 2-35 % faster from p = 2)
+  constexpr bool EO = (Q == P + 2) && P >= 2;
+  using EB = TabEo<P, 0>;
+  using EG = TabEo<P, 1>;
+  using EBT = TabEo<P, 2>;
+  using EGT = TabEo<P, 3>;
   static_assert(DQ1 * n * n <= L::S1C, "S1 component size");
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_df[];
@@ -187,16 +258,28 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     dfl xv[n];
 #pragma unroll
     for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
+    if constexpr (EO) {
+      dfl xp[n / 2], xm[n / 2], yb[Q], yg[Q];
+      eo_split<n>(xv, xp, xm);
+      eo_apply<EB, 1>(xp, xm, xv[n / 2], yb);
+      if (DIFF) eo_apply<EG, -1>(xp, xm, xv[n / 2], yg);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      dfl sb = df_zero(), sg = df_zero();
-#pragma unroll
-      for (int a = 0; a < n; ++a) {
-        df_fma(sb, T::B(i, a), xv[a]);
-        if (DIFF) df_fma(sg, T::G(i, a), xv[a]);
+      for (int i = 0; i < Q; ++i) {
+        S1[tid * DQ1 + i] = yb[i];
+        if (DIFF) S1[L::S1C + tid * DQ1 + i] = yg[i];
       }
-      S1[tid * DQ1 + i] = df_norm(sb);
-      if (DIFF) S1[L::S1C + tid * DQ1 + i] = df_norm(sg);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        dfl sb = df_zero(), sg = df_zero();
+#pragma unroll
+        for (int a = 0; a < n; ++a) {
+          df_fma(sb, T::B(i, a), xv[a]);
+          if (DIFF) df_fma(sg, T::G(i, a), xv[a]);
+        }
+        S1[tid * DQ1 + i] = df_norm(sb);
+        if (DIFF) S1[L::S1C + tid * DQ1 + i] = df_norm(sg);
+      }
     }
   }
   __syncthreads();
@@ -210,24 +293,43 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
       vb[b] = S1[(b + n * c) * DQ1 + i];
       if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * DQ1 + i];
     }
+    if constexpr (EO) {
+      dfl bp[n / 2], bm[n / 2], yb[Q];
+      eo_split<n>(vb, bp, bm);
+      eo_apply<EB, 1>(bp, bm, vb[n / 2], yb);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      dfl bb = df_zero(), bg = df_zero(), gb = df_zero();
-#pragma unroll
-      for (int b = 0; b < n; ++b) {
-        df_fma(bb, T::B(j, b), vb[b]);
-        if (DIFF) {
-          df_fma(bg, T::G(j, b), vb[b]);
-          df_fma(gb, T::B(j, b), vg[b]);
-        }
-      }
-      const int o = c * L::P2 + j * Q + i;
+      for (int j = 0; j < Q; ++j) S2[(DIFF ? 2 * L::S2C : 0) + c * L::P2 + j * Q + i] = yb[j];
       if (DIFF) {
-        S2[o] = df_norm(gb);
-        S2[L::S2C + o] = df_norm(bg);
-        S2[2 * L::S2C + o] = df_norm(bb);
-      } else {
-        S2[o] = df_norm(bb);
+        dfl yg[Q];
+        eo_apply<EG, -1>(bp, bm, vb[n / 2], yg);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) S2[L::S2C + c * L::P2 + j * Q + i] = yg[j];
+        dfl gp[n / 2], gm[n / 2];
+        eo_split<n>(vg, gp, gm);
+        eo_apply<EB, 1>(gp, gm, vg[n / 2], yg);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) S2[c * L::P2 + j * Q + i] = yg[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        dfl bb = df_zero(), bg = df_zero(), gb = df_zero();
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          df_fma(bb, T::B(j, b), vb[b]);
+          if (DIFF) {
+            df_fma(bg, T::G(j, b), vb[b]);
+            df_fma(gb, T::B(j, b), vg[b]);
+          }
+        }
+        const int o = c * L::P2 + j * Q + i;
+        if (DIFF) {
+          S2[o] = df_norm(gb);
+          S2[L::S2C + o] = df_norm(bg);
+          S2[2 * L::S2C + o] = df_norm(bb);
+        } else {
+          S2[o] = df_norm(bb);
+        }
       }
     }
   }
@@ -322,19 +424,36 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
         v2[j] = S2[2 * L::S2C + c * L::P2 + j * Q + i];
       }
     }
+    if constexpr (EO) {
+      dfl p0[Q / 2], m0[Q / 2], y0[n];
+      eo_split<Q>(v0, p0, m0);
+      eo_apply<EBT, 1>(p0, m0, v0[Q / 2], y0);
 #pragma unroll
-    for (int b = 0; b < n; ++b) {
-      dfl t0 = df_zero(), t1 = df_zero();
+      for (int b = 0; b < n; ++b) S1[(b + n * c) * DQ1 + i] = y0[b];
+      if (DIFF) {
+        dfl p1[Q / 2], m1[Q / 2], y1[n];
+        eo_split<Q>(v1, p1, m1);
+        eo_apply<EGT, -1>(p1, m1, v1[Q / 2], y1);
+        eo_split<Q>(v2, p0, m0);
+        eo_apply<EBT, 1>(p0, m0, v2[Q / 2], y0);
 #pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        df_fma(t0, T::B(j, b), v0[j]);
-        if (DIFF) {
-          df_fma(t1, T::G(j, b), v1[j]);
-          df_fma(t1, T::B(j, b), v2[j]);
-        }
+        for (int b = 0; b < n; ++b) S1[L::S1C + (b + n * c) * DQ1 + i] = df_add(y1[b], y0[b]);
       }
-      S1[(b + n * c) * DQ1 + i] = df_norm(t0);
-      if (DIFF) S1[L::S1C + (b + n * c) * DQ1 + i] = df_norm(t1);
+    } else {
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        dfl t0 = df_zero(), t1 = df_zero();
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          df_fma(t0, T::B(j, b), v0[j]);
+          if (DIFF) {
+            df_fma(t1, T::G(j, b), v1[j]);
+            df_fma(t1, T::B(j, b), v2[j]);
+          }
+        }
+        S1[(b + n * c) * DQ1 + i] = df_norm(t0);
+        if (DIFF) S1[L::S1C + (b + n * c) * DQ1 + i] = df_norm(t1);
+      }
     }
   }
   __syncthreads();
@@ -347,18 +466,39 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
       t0[i] = S1[tid * DQ1 + i];
       if (DIFF) t1[i] = S1[L::S1C + tid * DQ1 + i];
     }
+    dfl ys[n];
+    if constexpr (EO) {
+      dfl pp[Q / 2], mm[Q / 2], yb[n];
+      if (DIFF) {
+        eo_split<Q>(t0, pp, mm);
+        eo_apply<EGT, -1>(pp, mm, t0[Q / 2], ys);
+        eo_split<Q>(t1, pp, mm);
+        eo_apply<EBT, 1>(pp, mm, t1[Q / 2], yb);
+#pragma unroll
+        for (int a = 0; a < n; ++a) ys[a] = df_add(ys[a], yb[a]);
+      } else {
+        eo_split<Q>(t0, pp, mm);
+        eo_apply<EBT, 1>(pp, mm, t0[Q / 2], ys);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        dfl s = df_zero();
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (DIFF) {
+            df_fma(s, T::G(i, a), t0[i]);
+            df_fma(s, T::B(i, a), t1[i]);
+          } else {
+            df_fma(s, T::B(i, a), t0[i]);
+          }
+        }
+        ys[a] = s;
+      }
+    }
 #pragma unroll
     for (int a = 0; a < n; ++a) {
-      dfl s = df_zero();
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (DIFF) {
-          df_fma(s, T::G(i, a), t0[i]);
-          df_fma(s, T::B(i, a), t1[i]);
-        } else {
-          df_fma(s, T::B(i, a), t0[i]);
-        }
-      }
+      const dfl s = ys[a];
       const int gi = g[a + n * tid];
       if (gi >= 0) {
         atomicAdd(y + gi, df_to(s));
