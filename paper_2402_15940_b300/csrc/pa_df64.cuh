@@ -190,10 +190,14 @@ struct DfShape {
 // Lower orders and the mass form are fastest with no constraint (an explicit minimum
 // of 1 lets the allocator take up to 255 registers: 1.1-2x slower); the mass form rolls
 // its (short) stage-3 loop from p = 6 on.
+// EO3: stage 3 (z, D, z^T) also in even/odd form over mirrored point pairs (q = p + 2).
+// Measured against the even/odd line stages alone: mass 1-7 % faster; diffusion p = 3, 4, 8
+// 4-8 % faster, p = 2, 5, 6, 7 2-18 % slower (more live values: spills at p = 6, 7).
 template <int P, int Q, bool DIFF>
 struct DfTune {
   static constexpr int MINB = (DIFF && P >= 4) ? 2 : 0;
   static constexpr int KU = (P >= (DIFF ? 4 : 6)) ? 1 : Q;
+  static constexpr bool EO3 = DIFF ? (P == 3 || P == 4 || P == 8) : (P >= 2);
 };
 
 template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
@@ -351,6 +355,158 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     const float2* dE = qd + (e0 + el) * (L::NC * L::Q3) + tid;
     // (loading D one point ahead was measured 1-8 % slower here: this kernel is bound by
     // arithmetic and the registers are better spent on it)
+    if constexpr (EO && DfTune<P, Q, DIFF>::EO3) {
+      // z contraction, D and z^T in even/odd form over the mirrored point pairs (k, Q-1-k):
+      // u at both points from the split column, then the pair's sums and differences of v
+      // accumulate into the even (E) and odd (O) halves of a (mirrored outputs recombined
+      // at the end)
+      constexpr int HN = n / 2, HQ = Q / 2;
+      dfl c0p[HN], c0m[HN], c1p[HN], c1m[HN], c2p[HN], c2m[HN];
+      dfl ae0[HN], ao0[HN], ae1[HN], ao1[HN], ae2[HN], ao2[HN];
+      dfl am0 = df_zero(), am1 = df_zero(), am2 = df_zero();
+      eo_split<n>(c0, c0p, c0m);
+      if (DIFF) {
+        eo_split<n>(c1, c1p, c1m);
+        eo_split<n>(c2, c2p, c2m);
+      }
+#pragma unroll
+      for (int c = 0; c < HN; ++c) {
+        ae0[c] = ao0[c] = df_zero();
+        if (DIFF) ae1[c] = ao1[c] = ae2[c] = ao2[c] = df_zero();
+      }
+      // v = D u at point k (diffusion: symmetric 3 x 3; mass: scalar)
+      auto dpoint = [&](int k, dfl u0, dfl u1, dfl u2, dfl& v0, dfl& v1, dfl& v2) {
+        float2 dc[L::NC];
+#pragma unroll
+        for (int m = 0; m < L::NC; ++m) dc[m] = __ldg(dE + k * Q * Q + m * L::Q3);
+        if (DIFF) {
+          const int i1 = 1 % L::NC, i2 = 2 % L::NC, i3 = 3 % L::NC, i4 = 4 % L::NC, i5 = 5 % L::NC;
+          const dfl d00 = {dc[0].x, dc[0].y}, d01 = {dc[i1].x, dc[i1].y}, d02 = {dc[i2].x, dc[i2].y},
+                    d11 = {dc[i3].x, dc[i3].y}, d12 = {dc[i4].x, dc[i4].y}, d22 = {dc[i5].x, dc[i5].y};
+          v0 = df_zero(); v1 = df_zero(); v2 = df_zero();
+          df_fma(v0, d00, u0);
+          df_fma(v0, d01, u1);
+          df_fma(v0, d02, u2);
+          df_fma(v1, d01, u0);
+          df_fma(v1, d11, u1);
+          df_fma(v1, d12, u2);
+          df_fma(v2, d02, u0);
+          df_fma(v2, d12, u1);
+          df_fma(v2, d22, u2);
+          v0 = df_norm(v0);
+          v1 = df_norm(v1);
+          v2 = df_norm(v2);
+        } else {
+          v0 = df_zero();
+          df_fma(v0, dfl{dc[0].x, dc[0].y}, u0);
+          v0 = df_norm(v0);
+        }
+      };
+#pragma unroll KU
+      for (int kk = 0; kk < HQ; ++kk) {
+        const int k2 = Q - 1 - kk;
+        dfl e0 = df_zero(), o0 = df_zero(), e1 = df_zero(), o1 = df_zero(), e2 = df_zero(), o2 = df_zero();
+#pragma unroll
+        for (int i = 0; i < HN; ++i) {
+          df_fma(e0, EB::E(kk, i), c0p[i]);
+          df_fma(o0, EB::D(kk, i), c0m[i]);
+          if (DIFF) {
+            df_fma(e1, EB::E(kk, i), c1p[i]);
+            df_fma(o1, EB::D(kk, i), c1m[i]);
+            df_fma(e2, EG::E(kk, i), c2p[i]);
+            df_fma(o2, EG::D(kk, i), c2m[i]);
+          }
+        }
+        if (n % 2) {
+          df_fma(e0, EB::MC(kk), c0[HN]);
+          if (DIFF) {
+            df_fma(e1, EB::MC(kk), c1[HN]);
+            df_fma(e2, EG::MC(kk), c2[HN]);
+          }
+        }
+        dfl va0, va1, va2, vb0, vb1, vb2;  // v at kk and at k2
+        if (DIFF) {
+          dpoint(kk, df_add(e0, o0), df_add(e1, o1), df_add(e2, o2), va0, va1, va2);
+          dpoint(k2, df_sub(e0, o0), df_sub(e1, o1), df_sub(o2, e2), vb0, vb1, vb2);
+        } else {
+          dpoint(kk, df_add(e0, o0), e1, e2, va0, va1, va2);
+          dpoint(k2, df_sub(e0, o0), e1, e2, vb0, vb1, vb2);
+        }
+        const dfl p0 = df_add(va0, vb0), q0 = df_sub(va0, vb0);
+        dfl p1, q1, p2, q2;
+        if (DIFF) {
+          p1 = df_add(va1, vb1);
+          q1 = df_sub(va1, vb1);
+          p2 = df_add(va2, vb2);
+          q2 = df_sub(va2, vb2);
+        }
+#pragma unroll
+        for (int c = 0; c < HN; ++c) {
+          df_fma(ae0[c], EBT::E(c, kk), p0);
+          df_fma(ao0[c], EBT::D(c, kk), q0);
+          if (DIFF) {
+            df_fma(ae1[c], EBT::E(c, kk), p1);
+            df_fma(ao1[c], EBT::D(c, kk), q1);
+            df_fma(ae2[c], EGT::E(c, kk), p2);
+            df_fma(ao2[c], EGT::D(c, kk), q2);
+          }
+        }
+        if (n % 2) {
+          df_fma(am0, EBT::MR(kk), p0);
+          if (DIFF) {
+            df_fma(am1, EBT::MR(kk), p1);
+            df_fma(am2, EGT::MR(kk), q2);
+          }
+        }
+      }
+      if (Q % 2) {  // the middle point
+        dfl u0 = df_zero(), u1 = df_zero(), u2 = df_zero();
+#pragma unroll
+        for (int i = 0; i < HN; ++i) {
+          df_fma(u0, EB::MR(i), c0p[i]);
+          if (DIFF) {
+            df_fma(u1, EB::MR(i), c1p[i]);
+            df_fma(u2, EG::MR(i), c2m[i]);
+          }
+        }
+        if (n % 2) {
+          df_fma(u0, EB::MR(HN), c0[HN]);
+          if (DIFF) df_fma(u1, EB::MR(HN), c1[HN]);
+        }
+        dfl v0, v1, v2;
+        dpoint(HQ, df_norm(u0), df_norm(u1), df_norm(u2), v0, v1, v2);
+#pragma unroll
+        for (int c = 0; c < HN; ++c) {
+          df_fma(ae0[c], EBT::MC(c), v0);
+          if (DIFF) {
+            df_fma(ae1[c], EBT::MC(c), v1);
+            df_fma(ae2[c], EGT::MC(c), v2);
+          }
+        }
+        if (n % 2) {
+          df_fma(am0, EBT::MR(HQ), v0);
+          if (DIFF) df_fma(am1, EBT::MR(HQ), v1);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < HN; ++c) {
+        a0[c] = df_add(ae0[c], ao0[c]);
+        a0[n - 1 - c] = df_sub(ae0[c], ao0[c]);
+        if (DIFF) {
+          a1[c] = df_add(ae1[c], ao1[c]);
+          a1[n - 1 - c] = df_sub(ae1[c], ao1[c]);
+          a2[c] = df_add(ae2[c], ao2[c]);
+          a2[n - 1 - c] = df_sub(ao2[c], ae2[c]);
+        }
+      }
+      if (n % 2) {
+        a0[HN] = am0;
+        if (DIFF) {
+          a1[HN] = am1;
+          a2[HN] = am2;
+        }
+      }
+    } else {
 #pragma unroll KU
     for (int k = 0; k < Q; ++k) {
       float2 dc[L::NC];
@@ -400,6 +556,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
 #pragma unroll
         for (int c = 0; c < n; ++c) df_fma(a0[c], T::B(k, c), v);
       }
+    }
     }
 #pragma unroll
     for (int c = 0; c < n; ++c) {
