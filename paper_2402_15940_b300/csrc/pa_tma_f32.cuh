@@ -461,6 +461,35 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
   }
 }
 
+// stage 1^T (x) and G^T into shared memory: line (b,c) -> Y[c][b][a] (X's layout) for
+// the scatter that follows in element-local DOF order (coalesced map loads and atomics)
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float* S1, float* Y) {
+  using L = F32Smem<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if (!(live && tid < n * n)) return;
+  float t0[Q], t1[Q];
+  const float* in = S1 + (L::CS == n * L::Q1 ? tid * L::Q1 : (tid % n) * L::Q1 + (tid / n) * L::CS);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    t0[i] = in[i];
+    if (DIFF) t1[i] = in[L::S1C + i];
+  }
+#pragma unroll
+  for (int a = 0; a < n; ++a) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (DIFF)
+        s = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], s));
+      else
+        s = fmaf(T::B(i, a), t0[i], s);
+    }
+    Y[tid * L::XL + a] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // variants 0-2: one element group per block
 // ---------------------------------------------------------------------------
@@ -569,10 +598,44 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     f32_stage2t<P, Q, DIFF>(ln, alive(e), sS2 + e * S::W2, sS1 + e * S::W1);
   }
   __syncthreads();
-  {
+  // YSM: stage 1^T writes the element results into the (free) X buffer and the block then
+  // scatters them in element-local DOF order like the gather, so the map loads and the
+  // atomics are coalesced over consecutive DOFs instead of strided by lines.  Measured on
+  // B300: p = 3..8 2-14 % faster (mass p = 8 22 %), p = 1, 2 4-7 % slower.
+  constexpr bool YSM = P >= 3;
+  if (!YSM) {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
     f32_stage1t<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, gmap + (e0 + e) * (n * n * n), x, y);
+    return;
+  }
+  {
+    int e, ln;
+    stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
+    f32_stage1t_smem<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, sXall + e * S::XE);
+  }
+  __syncthreads();
+  // scatter in element-local DOF order, as the gather: map loads first, then the atomics
+  if (live) {
+    constexpr int GR = (n * n * n + TPE - 1) / TPE;
+    int gi[GR];
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      gi[r] = l < n * n * n ? __ldg(g + l) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+      const int l = tid + r * TPE;
+      if (l < n * n * n) {
+        const int gv = gi[r];
+        if (gv >= 0) {
+          atomicAdd(y + gv, sX[(l / n) * S::XL + l % n]);
+        } else if (!((~gv) & ESS_SKIP)) {
+          atomicAdd(y + (~gv), x[~gv]);
+        }
+      }
+    }
   }
 }
 
