@@ -307,31 +307,32 @@ cg32_dot_dh(int64_t N, const float* __restrict__ d, const float* __restrict__ h,
   }
 }
 
+// r -= alpha h; rho_new = (z, r) with z = r * inv_diag; rr = (r, r); stop test.  (x is
+// advanced by the direction kernel, which reads d anyway: one N-vector pass fewer per
+// iteration; the last iteration's x update is applied by cg32_flush.)
 __global__ void __launch_bounds__(RED_THREADS)
-cg32_update(int64_t N, float* __restrict__ x, float* __restrict__ r, const float* __restrict__ d,
-            const float* __restrict__ h, const float* __restrict__ inv_diag, CgState* st, double* partials) {
+cg32_update(int64_t N, float* __restrict__ r, const float* __restrict__ h, const float* __restrict__ inv_diag,
+            CgState* st, double* partials) {
   if (st->done) return;
   const float alpha = (float)st->alpha;
   float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
-  auto one = [&](float& xi, float& ri, float di, float hi, float wi) {
-    xi = fmaf(alpha, di, xi);
+  auto one = [&](float& ri, float hi, float wi) {
     ri = fmaf(-alpha, hi, ri);
     f2_add_prod(zr_h, zr_l, ri * wi, ri);
     f2_add_prod(rr_h, rr_l, ri, ri);
   };
   const int64_t N4 = N >> 2, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = t0; i < N4; i += ts) {  // 16-byte vector accesses over the bulk
-    float4 xv = reinterpret_cast<float4*>(x)[i], rv = reinterpret_cast<float4*>(r)[i];
-    const float4 dv = reinterpret_cast<const float4*>(d)[i], hv = reinterpret_cast<const float4*>(h)[i];
+    float4 rv = reinterpret_cast<float4*>(r)[i];
+    const float4 hv = reinterpret_cast<const float4*>(h)[i];
     const float4 wv = inv_diag ? reinterpret_cast<const float4*>(inv_diag)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
-    one(xv.x, rv.x, dv.x, hv.x, wv.x);
-    one(xv.y, rv.y, dv.y, hv.y, wv.y);
-    one(xv.z, rv.z, dv.z, hv.z, wv.z);
-    one(xv.w, rv.w, dv.w, hv.w, wv.w);
-    reinterpret_cast<float4*>(x)[i] = xv;
+    one(rv.x, hv.x, wv.x);
+    one(rv.y, hv.y, wv.y);
+    one(rv.z, hv.z, wv.z);
+    one(rv.w, hv.w, wv.w);
     reinterpret_cast<float4*>(r)[i] = rv;
   }
-  for (int64_t i = 4 * N4 + t0; i < N; i += ts) one(x[i], r[i], d[i], h[i], inv_diag ? inv_diag[i] : 1.f);
+  for (int64_t i = 4 * N4 + t0; i < N; i += ts) one(r[i], h[i], inv_diag ? inv_diag[i] : 1.f);
   double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
   double blk[2];
   block_sum<2>(v, blk);
@@ -354,19 +355,31 @@ cg32_update(int64_t N, float* __restrict__ x, float* __restrict__ r, const float
   }
 }
 
+// With update_x: x += alpha d (this iteration's step, d still the old direction); then
+// d = z + beta d and h = 0 for the next action.  Block 0 sets the while-condition.  Once
+// the loop is done nothing is written: the final step's x update is cg32_flush's.
 __global__ void __launch_bounds__(RED_THREADS)
 cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, float* __restrict__ h,
-               const float* __restrict__ inv_diag, const CgState* st, cudaGraphConditionalHandle cond, int use_cond) {
+               const float* __restrict__ inv_diag, float* __restrict__ x, int update_x, const CgState* st,
+               cudaGraphConditionalHandle cond, int use_cond) {
   const int done = st->done;
   if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
     cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
   if (done) return;
-  const float beta = (float)st->beta;
+  const float beta = (float)st->beta, alpha = update_x ? (float)st->alpha : 0.f;
   const int64_t N4 = N >> 2, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = t0; i < N4; i += ts) {  // 16-byte vector accesses over the bulk
     const float4 rv = reinterpret_cast<const float4*>(r)[i];
     const float4 wv = inv_diag ? reinterpret_cast<const float4*>(inv_diag)[i] : make_float4(1.f, 1.f, 1.f, 1.f);
     float4 dv = reinterpret_cast<float4*>(d)[i];
+    if (update_x) {
+      float4 xv = reinterpret_cast<float4*>(x)[i];
+      xv.x = fmaf(alpha, dv.x, xv.x);
+      xv.y = fmaf(alpha, dv.y, xv.y);
+      xv.z = fmaf(alpha, dv.z, xv.z);
+      xv.w = fmaf(alpha, dv.w, xv.w);
+      reinterpret_cast<float4*>(x)[i] = xv;
+    }
     dv.x = fmaf(beta, dv.x, rv.x * wv.x);
     dv.y = fmaf(beta, dv.y, rv.y * wv.y);
     dv.z = fmaf(beta, dv.z, rv.z * wv.z);
@@ -375,10 +388,20 @@ cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, fl
     reinterpret_cast<float4*>(h)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   for (int64_t i = 4 * N4 + t0; i < N; i += ts) {
+    if (update_x) x[i] = fmaf(alpha, d[i], x[i]);
     const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
     d[i] = fmaf(beta, d[i], zi);
     h[i] = 0.f;
   }
+}
+
+// x += alpha d for the final step of a finished FP32 loop (done and at least one step):
+// its direction kernel returned before advancing x
+__global__ void cg32_flush(int64_t N, float* __restrict__ x, const float* __restrict__ d, const CgState* st) {
+  if (!(st->done && st->iter > 0)) return;
+  const float alpha = (float)st->alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fmaf(alpha, d[i], x[i]);
 }
 
 // Outer step of the refinement: r = b - h in FP64 (h = A x from the FP64 operator),

@@ -767,9 +767,9 @@ int body32(fepa_op* op, CgLoop& L, const float* invd, cudaStream_t s, cudaGraphC
   TRY(launch_apply32_nocount(op, d, h, &L.st->done, s));
   cg32_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
   BODY_CHECK();
-  cg32_update<<<rb, RED_THREADS, 0, s>>>(op->N, x, r, d, h, invd, L.st, L.partials);
+  cg32_update<<<rb, RED_THREADS, 0, s>>>(op->N, r, h, invd, L.st, L.partials);
   BODY_CHECK();
-  cg32_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, L.st, cond, use_cond);
+  cg32_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, x, 1, L.st, cond, use_cond);
   BODY_CHECK();
   return FEPA_OK;
 }
@@ -927,6 +927,8 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     CgState hin;
     TRY(run_loop(op, L, precond, body, &hin));
     inner_total += hin.iter;
+    cg32_flush<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, (float*)L.x, (const float*)L.d, L.st);
+    LAUNCH_CHECK();
     refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
     LAUNCH_CHECK();
     ++outer;
@@ -1002,6 +1004,8 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
       CgState hin;
       TRY(run_loop(op, L, precond, body, &hin));
       iters = hin.iter;
+      cg32_flush<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, (float*)L.x, (const float*)L.d, L.st);
+      LAUNCH_CHECK();
       refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
       LAUNCH_CHECK();
       TRY(residual(&rel, &bb));
@@ -1010,7 +1014,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
                                                          delta * delta, floor2, L.partials);
       LAUNCH_CHECK();
       cg32_direction<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.d, (float*)L.h, invd,
-                                                          L.st, 0, 0);
+                                                          nullptr, 0, L.st, 0, 0);
       LAUNCH_CHECK();
       ++replacements;
     }
