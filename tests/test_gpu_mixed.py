@@ -173,6 +173,22 @@ def test_refined_noconv():
     assert st["status"] == -5 and st["outer_iterations"] == 1
 
 
+@pytest.mark.parametrize("mode", ["graph", "stream"])
+def test_refined_single_step_corrections(mode):
+    """Inner solves of one FP32 CG step each: every correction is that step's alpha d, which
+    the loop's last (flushed) x update must deliver, so the FP64 refinement still converges,
+    in graph and stream mode alike."""
+    op, mesh = make((3, 3, 3), 2, "mass", seed=46)
+    op.set_cg_mode(mode)
+    b = op.rhs_sine(1.0)
+    x, st = op.solve_refined(b, rtol=1e-8, max_outer=400, inner_maxit=1)
+    op.set_cg_mode("graph")
+    assert st["status"] == 0 and st["rel_residual"] <= 1e-8
+    assert st["outer_iterations"] > 3 and st["inner_iterations"] == st["outer_iterations"]
+    xo, _, _ = O.Problem(mesh, 2, None, "mass").solve(b.cpu().numpy(), rtol=1e-12)
+    assert rel(x.cpu().numpy(), xo) <= 1e-6
+
+
 @pytest.mark.parametrize("solver", ["cg", "refined"])
 def test_stream_mode_equals_graph_mode(solver):
     op, _ = make((5, 4, 4), 3, "diffusion", seed=45)
