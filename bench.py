@@ -379,6 +379,7 @@ def run_ours(args, rank, world, dist):
                              "kernel": f"pa_apply_f32_tma<{p},{q},diffusion> variant {op.f32_variant()[0]} "
                                        f"({op.f32_variant()[1]}, autotuned)", "apply_ms": 1e3 * t_apply,
                              "peak_note": f"HBM copy bandwidth ({hbm_src})",
+                             "frac_of_nominal_8tbs": ach / 8000.0,
                              "fp32_tflops": fl / t_apply / 1e12}
         r["apply_gdofs"] = N / t_apply / 1e9
         r["e2e"] = None if args.no_e2e else e2e(prec)
