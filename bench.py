@@ -524,6 +524,36 @@ def run_batch(args, rank, world, dist):
         ev1.record()
         torch.cuda.synchronize()
     t32, work32 = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, dofit32, dist, device="cuda")
+
+    # and by batched reliable updates (per-problem FP32 recurrences, FP64 residual replacement)
+    def step_reliable():
+        x.zero_()
+        _, st = bt.solve_reliable(b, x, rtol=args.rtol, delta=args.delta)
+        return st
+
+    for _ in range(args.warmup):
+        step_reliable()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    l2 = F.launch_count()
+    dofitr, maxr, repl = 0.0, [], []
+    with ClockSampler(local) as clkr:
+        ev0.record()
+        for _ in range(args.steps):
+            st = step_reliable()
+            dofitr += st["dof_iterations"]
+            maxr.append(int(st["max_inner_iterations"]))
+            repl.append(int(st["outer_iterations"]))
+        ev1.record()
+        torch.cuda.synchronize()
+    tr, workr = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, dofitr, dist, device="cuda")
+    reliable = {"solver": "batched FP32 Jacobi-PCG recurrences with FP64 residual replacement each time they "
+                          f"fall by {args.delta} (reliable updates), one CUDA-graph loop per segment",
+                "ms_per_step": 1e3 * tr / args.steps, "solves_per_s": args.batch_count * world * args.steps / tr,
+                "gdofs_per_fp32_iter": workr / tr / 1e9, "max_inner_iterations_per_step": maxr,
+                "replacements_per_step": repl, "time_to_solution_speedup_vs_fp64": t / tr,
+                "gpu_launches": F.launch_count() - l2, "clocks": clkr.summary()}
     refined = {"solver": "FP64 iterative refinement (per-problem FP64 residual and stop) around batched FP32 "
                          f"Jacobi-PCG corrections (inner rtol {args.inner_rtol}), one CUDA-graph loop per step",
                "ms_per_step": 1e3 * t32 / args.steps, "solves_per_s": args.batch_count * world * args.steps / t32,
@@ -541,7 +571,8 @@ def run_batch(args, rank, world, dist):
                            "total_dofs": bt.N, "groups": bt.groups},
                 "solves_per_s": args.batch_count * world * args.steps / t,
                 "max_iterations_per_step": maxits, "setup_s": setup_s,
-                "gpu_launches": launches64, "clocks": clk.summary(), "mixed_refined": refined}
+                "gpu_launches": launches64, "clocks": clk.summary(), "mixed_refined": refined,
+                "mixed_reliable": reliable}
         print(json.dumps(line), flush=True)
     return 0
 

@@ -424,6 +424,24 @@ int fepa_batch_solve_refined(fepa_batch* batch, const double* b, double* x, doub
                              double inner_rtol, int32_t inner_maxit, int32_t precond,
                              fepa_batch_refine_stats* stats, int32_t* iterations);
 
+/*
+ * Mixed-precision CG with reliable updates for every problem at once, as fepa_solve_reliable
+ * does for one operator: one FP32 Jacobi-PCG recurrence per problem (per-problem scalars and
+ * stops, one CUDA-graph loop over the batch) whose residual is replaced by the FP64 residual
+ * b_i - A x_i each time it has fallen by delta since the last replacement, the FP32 iterate
+ * being added to the FP64 x first; directions and scalars carry over each replacement.  The
+ * batch steps together: a replacement happens when every problem still running has reached
+ * its segment end.  Problems at ||r_i|| <= rtol ||b_i|| drop out (their elements are skipped).
+ *   delta       replacement factor in (0, 1)
+ *   maxit       limit on each problem's FP32 iterations in total
+ *   stats       outer_iterations = replacements, max_inner_iterations = the largest FP32 count
+ *   iterations  host int32 [count]: each problem's FP32 iterations (may be null)
+ * FEPA_ERR_NOCONV if a problem has not reached rtol within maxit FP32 iterations.
+ */
+int fepa_batch_solve_reliable(fepa_batch* batch, const double* b, double* x, double rtol, double delta,
+                              int32_t maxit, int32_t precond, fepa_batch_refine_stats* stats,
+                              int32_t* iterations);
+
 /* ---------------------------------------------------------------------------
  * p-multigrid preconditioner (Sec. 2.1: a hierarchy of orders on one mesh, transfers
  * between them by sum factorisation, diagonal-based smoothers with Chebyshev

@@ -226,11 +226,12 @@ bref_residual(ChunkTable t, const double* __restrict__ b, const double* __restri
 
 // Start of the FP32 correction solves A e = r: e = 0, d = z, h = 0 everywhere; for every
 // problem not finished, rho = (z, r), rr = (r, r) and the stop at rr <= tol^2 ||r||^2 with
-// tol = inner_tol(inner_rtol, rtol, its outer residual).
+// tol = inner_tol(inner_rtol, rtol, its outer residual) -- or, for the reliable-update solve
+// (delta2 > 0), the first segment's stop at rr <= max(delta2 ||r||^2, rtol^2 ||b||^2 / 4).
 __global__ void __launch_bounds__(RED_THREADS)
 bcg32_init(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, float* __restrict__ d,
            float* __restrict__ h, const float* __restrict__ inv_diag, BState* ps, const BState* __restrict__ pr,
-           int* pdone, BGlobal* gs, double inner_rtol, double rtol, int maxit, double* partials) {
+           int* pdone, BGlobal* gs, double inner_rtol, double rtol, int maxit, double delta2, double* partials) {
   const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
   float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -259,9 +260,14 @@ bcg32_init(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, flo
         q.tol2 = 0.0;
         return false;
       }
-      const double rel = pr[j].bb > 0.0 ? sqrt(pr[j].rr / pr[j].bb) : 0.0;
-      const double tol = inner_tol(inner_rtol, rtol, rel);
-      q.tol2 = tol * tol * s[1];
+      if (delta2 > 0.0) {
+        const double floor2 = 0.25 * rtol * rtol * pr[j].bb;
+        q.tol2 = delta2 * s[1] > floor2 ? delta2 * s[1] : floor2;
+      } else {
+        const double rel = pr[j].bb > 0.0 ? sqrt(pr[j].rr / pr[j].bb) : 0.0;
+        const double tol = inner_tol(inner_rtol, rtol, rel);
+        q.tol2 = tol * tol * s[1];
+      }
       q.converged = s[1] <= q.tol2 ? 1 : 0;
       pdone[j] = q.converged;
       return !q.converged;
@@ -335,6 +341,50 @@ bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const f
       q.rho = s[0];
       pdone[j] = stop;
       return !stop;
+    });
+    if (threadIdx.x == 0) {
+      gs->active = active;
+      gs->done = active == 0;
+      gs->ticket = 0;
+    }
+  }
+}
+
+// Residual replacement of the batched reliable-update solve (as cg32_replace, per problem):
+// r holds each problem's FP64 residual b - A x rounded to FP32 and e = 0; every problem not
+// finished by the FP64 test (pdone 0) and below maxit gets rho = (z, r), rr = (r, r), beta
+// rescaled so that the next direction continues its recurrence (d = z + rho / rho_prev d),
+// and its next stop at rr <= max(delta2 rr, rtol^2 ||b||^2 / 4); the others stop.
+__global__ void __launch_bounds__(RED_THREADS)
+bcg32_replace(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, const float* __restrict__ inv_diag,
+              BState* ps, const BState* __restrict__ pr, int* pdone, BGlobal* gs, double delta2, double rtol,
+              double* partials) {
+  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
+  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const float ri = r[i];
+    const float zi = inv_diag ? ri * inv_diag[i] : ri;
+    e[i] = 0.f;
+    f2_add_prod(zr_h, zr_l, zi, ri);
+    f2_add_prod(rr_h, rr_l, ri, ri);
+  }
+  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+    const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
+      BState& q = ps[j];
+      if (pdone[j] || q.iter >= q.maxit) {
+        pdone[j] = 1;
+        return false;
+      }
+      q.beta = q.beta != 0.0 ? s[0] / (q.rho / q.beta) : 0.0;
+      q.rho = s[0];
+      q.rr = s[1];
+      const double floor2 = 0.25 * rtol * rtol * pr[j].bb;
+      q.tol2 = delta2 * s[1] > floor2 ? delta2 * s[1] : floor2;
+      q.converged = 0;
+      return true;
     });
     if (threadIdx.x == 0) {
       gs->active = active;

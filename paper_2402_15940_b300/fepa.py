@@ -125,6 +125,8 @@ SIGNATURES = [
     ("fepa_batch_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(BatchStats), _P]),
     ("fepa_batch_solve_refined", ctypes.c_int,
      [_P, _P, _P, _D, _I32, _D, _I32, _I32, ctypes.POINTER(BatchRefineStats), _P]),
+    ("fepa_batch_solve_reliable", ctypes.c_int,
+     [_P, _P, _P, _D, _D, _I32, _I32, ctypes.POINTER(BatchRefineStats), _P]),
     ("fepa_mg_create", ctypes.c_int, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     ("fepa_mg_update", ctypes.c_int, [_P]),
     ("fepa_mg_destroy", None, [_P]),
@@ -547,6 +549,27 @@ class Batch:
                                                 int(max_outer), float(inner_rtol), int(inner_maxit),
                                                 _PRECONDS[precond], ctypes.byref(st),
                                                 its.ctypes.data_as(ctypes.c_void_p))
+        if rc != ERR_NOCONV or raise_on_noconv:
+            _check(rc)
+        d = st.as_dict()
+        d["iterations"] = its
+        return x, d
+
+
+    def solve_reliable(self, b, x=None, rtol=1e-10, delta=0.03, maxit=20000, precond="jacobi",
+                       raise_on_noconv=True):
+        """Batched mixed-precision CG with reliable updates (per-problem FP32 recurrences whose
+        residuals are replaced by FP64 residuals); stats["iterations"]: FP32 iterations per problem,
+        stats["outer_iterations"]: replacements."""
+        torch = _torch()
+        x = torch.zeros(self.N, dtype=torch.float64, device="cuda") if x is None else x
+        st = BatchRefineStats()
+        its = np.zeros(self.count, dtype=np.int32)
+        self._sync_stream()
+        rc = self._lib.fepa_batch_solve_reliable(self._h, _dev_ptr(b, torch.float64, self.N, "b"),
+                                                 _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), float(delta),
+                                                 int(maxit), _PRECONDS[precond], ctypes.byref(st),
+                                                 its.ctypes.data_as(ctypes.c_void_p))
         if rc != ERR_NOCONV or raise_on_noconv:
             _check(rc)
         d = st.as_dict()

@@ -246,3 +246,64 @@ def test_batch_refined_512_problem_mix_sampled():
         ess = O.boundary_dofs(mesh, pr["p"]).astype(np.int64) if pr["form"] == "diffusion" else None
         Ax = O.action_rows(mesh, pr["p"], pr["p"] + 2, pr["form"], x[sl], rows, ess=ess)
         assert np.max(np.abs(b[sl][rows] - Ax)) <= 1e-10 * np.linalg.norm(b[sl])
+
+
+# ---------------------------------------------------------------------------
+# Batched reliable updates: one FP32 recurrence per problem with FP64 residual replacement.
+# ---------------------------------------------------------------------------
+def test_batch_reliable_matches_oracle_and_alone():
+    probs = small_mix(seed=2, count=12)
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets)
+    x, st = bt.solve_reliable(torch.from_numpy(b).cuda(), rtol=1e-10)
+    x = x.cpu().numpy()
+    assert st["converged"] == len(probs) and st["status"] == 0
+    assert st["max_rel_residual"] <= 1e-10
+    its = st["iterations"]
+    assert st["max_inner_iterations"] == its.max()
+    for i, pr in enumerate(probs):
+        sl = slice(bt.offsets[i], bt.offsets[i + 1])
+        xo, _, _ = oracle_problem(pr).solve(b[sl], rtol=1e-12)
+        assert rel(x[sl], xo) <= 1e-9, i
+        op = F().Operator(*pr["n"], pr["vertices"], pr["p"], form=pr["form"])
+        if pr["form"] == "diffusion":
+            op.set_essential(op.boundary_dofs())
+        xa, sa = op.solve_reliable(torch.from_numpy(np.ascontiguousarray(b[sl])).cuda(), rtol=1e-10)
+        # the batch replaces when every running problem has ended its segment, so a problem's
+        # replacements (and FP32 count) can differ a little from its solve alone
+        assert abs(sa["inner_iterations"] - int(its[i])) <= max(6, 0.15 * sa["inner_iterations"]), i
+        assert rel(x[sl], xa.cpu().numpy()) <= 1e-9, i
+
+
+def test_batch_reliable_finished_problems_and_errors():
+    probs = small_mix(seed=3, count=6)
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets, seed=9)
+    b[bt.offsets[1]:bt.offsets[2]] = 0.0
+    bd = torch.from_numpy(b).cuda()
+    x, st = bt.solve_reliable(bd, rtol=1e-10)
+    assert st["iterations"][1] == 0 and st["converged"] == len(probs)
+    assert float(torch.abs(x[bt.offsets[1]:bt.offsets[2]]).max()) == 0.0
+    from paper_2402_15940_b300.fepa import ERR_NOCONV
+    x, st = bt.solve_reliable(bd, rtol=1e-14, maxit=5, raise_on_noconv=False)
+    assert st["status"] == ERR_NOCONV and st["max_inner_iterations"] <= 5 + 1
+    for kw in ({"delta": 0.0}, {"delta": 1.0}, {"maxit": 0}, {"rtol": -1.0}):
+        with pytest.raises(F().FepaError):
+            bt.solve_reliable(bd, **kw)
+
+
+def test_batch_reliable_512_problem_mix_sampled():
+    mix = FI.problem_mix(512, seed=0)
+    probs = [{"n": m["n"], "p": m["p"], "form": m["form"],
+              "vertices": FI.perturbed_cube_vertices(*m["n"], seed=m["mesh_seed"])} for m in mix]
+    bt = F().Batch(probs)
+    b = rhs_for(probs, bt.offsets, seed=11)
+    bd = torch.from_numpy(b).cuda()
+    x, st = bt.solve_reliable(bd, rtol=1e-10)
+    assert st["converged"] == 512 and st["max_rel_residual"] <= 1e-10
+    x64, _ = bt.solve(bd, rtol=1e-10, maxit=20000)
+    x, x64 = x.cpu().numpy(), x64.cpu().numpy()
+    rng = np.random.default_rng(7)
+    for i in rng.choice(512, 6, replace=False):
+        sl = slice(bt.offsets[i], bt.offsets[i + 1])
+        assert rel(x[sl], x64[sl]) <= 1e-8, i
