@@ -533,7 +533,6 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   }
   const bool live = alive(el);
   float* sX = sXall + el * S::XE;
-  float* S2 = sS2 + el * S::W2;
   const int* g = gmap + (e0 + el) * (n * n * n);
   if (live) {
     // gather: all map loads first, then all x loads, so the dependent pairs overlap
@@ -589,8 +588,27 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   } else {
     __syncthreads();
   }
-  const float* dE = (STAGE_D ? sD + el * S::DELEM : qd32 + (e0 + el) * S::DELEM) + tid;
-  f32_stage3<P, Q, DIFF, DEARLY && !STAGE_D>(tid, live, S2, dE, dpre);
+  // stage-3 columns: when an element's Q^2 columns are not a whole number of warps, the
+  // first NE * 32W threads can take columns 0..32W-1 element by element (whole warps on one
+  // element: contiguous S2 and D) and the rest the tails, so that only one warp spans
+  // elements (modelled: 17 % fewer stage-3 shared wavefronts at p = 4).  Measured on B300:
+  // 2.8 % faster at Q = 6 (BP3 p = 4), 3.3 % at Q = 10, neutral at Q = 7, 3 % slower at
+  // Q = 9 -- used for Q = 6 and 10.
+  int e3 = el, c3 = tid;
+  if constexpr ((Q == 6 || Q == 10) && !DEARLY) {
+    constexpr int W = TPE / 32, TT = TPE - 32 * W;
+    const int flat = el * TPE + tid;
+    if (flat < NE * 32 * W) {
+      e3 = flat / (32 * W);
+      c3 = flat - e3 * (32 * W);
+    } else {
+      const int f = flat - NE * 32 * W;
+      e3 = f / TT;
+      c3 = 32 * W + (f - e3 * TT);
+    }
+  }
+  const float* dE = (STAGE_D ? sD + e3 * S::DELEM : qd32 + (e0 + e3) * S::DELEM) + c3;
+  f32_stage3<P, Q, DIFF, DEARLY && !STAGE_D>(c3, alive(e3), sS2 + e3 * S::W2, dE, dpre);
   __syncthreads();
   {
     int e, ln;
