@@ -145,7 +145,7 @@ FP64_PEAK_GFLOPS = 1250.0
 # current apply kernels on the default workload: captured at 40^3 elements (413.1 MB FP32 variant
 # 2, 794.8 MB double-float: the algorithmic bytes, y read once for the atomics) and scaled to
 # 64^3 by elements (D, map) and DOFs (x, y).  Only reported when that kernel is the one timed.
-NCU_TRAFFIC_P4_N64 = {"f32_v2": 1.6921e9, "df": 3.2555e9}
+NCU_TRAFFIC_P4_N64 = {"f32_v2": 1.6919e9, "df": 3.2555e9}
 # ceiling of the double-float FP64 action: 12 FP32-pipe instructions per FP64-accurate
 # multiply-add (exact product by FMA, TwoSum accumulation) on 128 FP32 lanes/SM x 148 SMs
 # at 2.032 GHz, 2 flops per multiply-add
