@@ -142,10 +142,10 @@ def reduce_max_sum(t, work, dist=None, device="cpu"):
 # nominal FP64 rate of the B300 (no FP64 tensor-core path); the FP64 pipe bounds this kernel
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of the
-# current apply kernels on the default workload: captured at 40^3 elements (413.1 MB FP32 variant
-# 2, 794.8 MB double-float: the algorithmic bytes, y read once for the atomics) and scaled to
-# 64^3 by elements (D, map) and DOFs (x, y).  Only reported when that kernel is the one timed.
-NCU_TRAFFIC_P4_N64 = {"f32_v2": 1.6919e9, "df": 3.2555e9}
+# current apply kernels on the default workload: captured at 40^3 elements (412.9 / 413.0 MB FP32
+# variants 1 / 2, 794.8 MB double-float: the algorithmic bytes, y read once for the atomics) and
+# scaled to 64^3 by elements (D, map) and DOFs (x, y).  Only reported when that kernel is timed.
+NCU_TRAFFIC_P4_N64 = {"f32_v1": 1.6910e9, "f32_v2": 1.6916e9, "df": 3.2555e9}
 # ceiling of the double-float FP64 action: 12 FP32-pipe instructions per FP64-accurate
 # multiply-add (exact product by FMA, TwoSum accumulation) on 128 FP32 lanes/SM x 148 SMs
 # at 2.032 GHz, 2 flops per multiply-add
@@ -372,8 +372,8 @@ def run_ours(args, rank, world, dist):
             ach = by / t_apply / 1e9
             fl = flops_per_elem(p + 1, q, "diffusion") * E
             traffic = args.traffic_fp32
-            if traffic is None and (p, n) == (4, 64) and op.f32_variant()[0] == 2:
-                traffic = NCU_TRAFFIC_P4_N64["f32_v2"]
+            if traffic is None and (p, n) == (4, 64):
+                traffic = NCU_TRAFFIC_P4_N64.get(f"f32_v{op.f32_variant()[0]}")
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak, "traffic": traffic,
                              "kernel": f"pa_apply_f32_tma<{p},{q},diffusion> variant {op.f32_variant()[0]} "
