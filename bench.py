@@ -222,6 +222,7 @@ def run_ours(args, rank, world, dist):
         op.set_f32_variant(args.f32_variant)
     if args.f64_variant >= 0:
         op.set_f64_variant(args.f64_variant)
+    op.set_fused_dot(args.fused_dot)
     verts = torch.from_numpy(verts_np).cuda()
     b = torch.empty(N, dtype=torch.float64, device="cuda")
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -291,7 +292,11 @@ def run_ours(args, rank, world, dist):
             yr = torch.empty_like(xr)
         else:
             xr = torch.from_numpy(FI.uniform_vector(N, seed=1).astype(np.float32)).cuda()
-            fn = lambda out: op.apply_f32(xr, out=out)  # noqa: E731
+            if args.fused_dot:   # the build the CG loop runs: the action with (d, A d) fused
+                xax = torch.empty(1, dtype=torch.float64, device="cuda")
+                fn = lambda out: op.apply_f32_dot(xr, out=out, xax=xax)  # noqa: E731
+            else:
+                fn = lambda out: op.apply_f32(xr, out=out)  # noqa: E731
             yr = torch.empty_like(xr)
         for _ in range(3):
             fn(yr)
@@ -373,11 +378,13 @@ def run_ours(args, rank, world, dist):
             fl = flops_per_elem(p + 1, q, "diffusion") * E
             traffic = args.traffic_fp32
             if traffic is None and (p, n) == (4, 64):
-                traffic = NCU_TRAFFIC_P4_N64.get(f"f32_v{op.f32_variant()[0]}")
+                traffic = NCU_TRAFFIC_P4_N64.get(f"f32{'dot' if args.fused_dot else ''}_v{op.f32_variant()[0]}")
             r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                              "frac": ach / hbm_peak, "traffic": traffic,
                              "kernel": f"pa_apply_f32_tma<{p},{q},diffusion> variant {op.f32_variant()[0]} "
-                                       f"({op.f32_variant()[1]}, autotuned)", "apply_ms": 1e3 * t_apply,
+                                       f"({op.f32_variant()[1]}, autotuned)"
+                                       + (", (d, A d) fused; timed with its slot collection" if args.fused_dot else ""),
+                             "apply_ms": 1e3 * t_apply,
                              "peak_note": f"HBM copy bandwidth ({hbm_src})",
                              "frac_of_nominal_8tbs": ach / 8000.0,
                              "fp32_tflops": fl / t_apply / 1e12}
@@ -723,6 +730,8 @@ def main():
     ap.add_argument("--traffic-fp64", type=float, default=None, help="DRAM bytes per FP64 apply launch (ncu)")
     ap.add_argument("--traffic-fp32", type=float, default=None, help="DRAM bytes per FP32 apply launch (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fused-dot", dest="fused_dot", action="store_false",
+                    help="FP32 CG: (d, A d) by a separate pass instead of from the action kernel")
     ap.add_argument("--workload", choices=["bp3", "batch", "serve", "sweep"], default="bp3")
     ap.add_argument("--rates", default="10,100,1000,5000")
     ap.add_argument("--requests", type=int, default=48)

@@ -145,6 +145,15 @@ int fepa_op_set_stream(fepa_op* op, void* stream);
  * Both run the same kernels and give the same iterates. */
 int fepa_op_set_cg_mode(fepa_op* op, int32_t mode);
 
+/* FP32 inner CG of the mixed solves (fepa_solve_refined, fepa_solve_reliable and the
+ * refined resumable solve): with enable != 0 (the default) the FP32 action kernel also
+ * forms (d, A d) = sum over elements of d_e . (A_e d_e) plus d_g^2 at essential DOFs
+ * (Sec. 2.3: the dot product fused into the operator kernel), summed in FP32 per warp and
+ * added into 256 doubles, and the separate (d, h) pass over two N-vectors is dropped.  Used where the chosen FP32 variant has that build (p >= 3, variants 0-2);
+ * elsewhere, and with enable = 0, (d, h) is a separate reduction.  The two agree to FP32
+ * rounding of the element results, not bitwise.  Returns FEPA_ERR_ARG for a null op. */
+int fepa_op_set_fused_dot(fepa_op* op, int32_t enable);
+
 /* Boundary DOFs of the node grid, ascending, written to dofs (host, capacity
  * entries); *count receives the total (which may exceed capacity: then nothing
  * is written and FEPA_ERR_ARG is returned). dofs may be null to query the count. */
@@ -181,6 +190,16 @@ int fepa_op_apply(fepa_op* op, const double* x, double* y);
  * FEPA_ERR_TIMEOUT.
  */
 int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
+
+/*
+ * y = A x in FP32 as fepa_op_apply_f32, and *xax = (x, A x) (xax: one device double),
+ * the sum over elements of x_e . (A_e x_e) with x_e zero at essential DOFs, plus x_g^2
+ * at each essential DOF: the fused (d, A d) of the FP32 CG (fepa_op_set_fused_dot), the
+ * dot product of Sec. 2.3 formed inside the operator kernel.  Where the op's FP32 variant
+ * has no such build (p < 3, variant 3) the product is a separate pass over x and y.
+ * Enqueued on the op's stream; *xax is valid when that work completes.
+ */
+int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax);
 
 /*
  * Launch shape of the FP32 kernel.  Variants: 0 = D staged into shared memory by a TMA

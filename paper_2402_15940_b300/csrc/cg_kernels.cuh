@@ -309,12 +309,27 @@ cg32_dot_dh(int64_t N, const float* __restrict__ d, const float* __restrict__ h,
 
 // r -= alpha h; rho_new = (z, r) with z = r * inv_diag; rr = (r, r); stop test.  (x is
 // advanced by the direction kernel, which reads d anyway: one N-vector pass fewer per
-// iteration; the last iteration's x update is applied by cg32_flush.)
+// iteration; the last iteration's x update is applied by cg32_flush.)  dh_slots: the
+// action kernel accumulated (d, h) into these RED_THREADS doubles; every block sums them
+// and forms alpha = rho / (d, h) itself (block 0 also stores it); null: alpha is st->alpha.
 __global__ void __launch_bounds__(RED_THREADS)
 cg32_update(int64_t N, float* __restrict__ r, const float* __restrict__ h, const float* __restrict__ inv_diag,
-            CgState* st, double* partials) {
+            CgState* st, double* partials, const double* __restrict__ dh_slots) {
   if (st->done) return;
-  const float alpha = (float)st->alpha;
+  float alpha;
+  if (dh_slots) {
+    __shared__ double s_alpha;
+    double v[1] = {__ldcg(dh_slots + threadIdx.x)}, tot[1];
+    block_sum<1>(v, tot);
+    if (threadIdx.x == 0) {
+      s_alpha = st->rho / tot[0];
+      if (blockIdx.x == 0) st->alpha = s_alpha;
+    }
+    __syncthreads();
+    alpha = (float)s_alpha;
+  } else {
+    alpha = (float)st->alpha;
+  }
   float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
   auto one = [&](float& ri, float hi, float wi) {
     ri = fmaf(-alpha, hi, ri);
@@ -356,12 +371,14 @@ cg32_update(int64_t N, float* __restrict__ r, const float* __restrict__ h, const
 }
 
 // With update_x: x += alpha d (this iteration's step, d still the old direction); then
-// d = z + beta d and h = 0 for the next action.  Block 0 sets the while-condition.  Once
-// the loop is done nothing is written: the final step's x update is cg32_flush's.
+// d = z + beta d and h = 0 for the next action.  Block 0 sets the while-condition and
+// clears dh_slots (if given) for the next action's (d, h).  Once the loop is done nothing
+// else is written: the final step's x update is cg32_flush's.
 __global__ void __launch_bounds__(RED_THREADS)
 cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, float* __restrict__ h,
                const float* __restrict__ inv_diag, float* __restrict__ x, int update_x, const CgState* st,
-               cudaGraphConditionalHandle cond, int use_cond) {
+               cudaGraphConditionalHandle cond, int use_cond, double* __restrict__ dh_slots) {
+  if (dh_slots && blockIdx.x == 0) dh_slots[threadIdx.x] = 0.0;
   const int done = st->done;
   if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
     cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
@@ -393,6 +410,26 @@ cg32_direction(int64_t N, const float* __restrict__ r, float* __restrict__ d, fl
     d[i] = fmaf(beta, d[i], zi);
     h[i] = 0.f;
   }
+}
+
+// (x, y) of two FP32 vectors added into the DOT_SLOTS-style slots (RED_THREADS doubles,
+// slot blockIdx.x mod RED_THREADS): the unfused form of the action kernel's (x, A x)
+__global__ void __launch_bounds__(RED_THREADS)
+dot32_slots(int64_t N, const float* __restrict__ x, const float* __restrict__ y, double* slots) {
+  float s_h = 0.f, s_l = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    f2_add_prod(s_h, s_l, x[i], y[i]);
+  double v[1] = {f2_value(s_h, s_l)}, blk[1];
+  block_sum<1>(v, blk);
+  if (threadIdx.x == 0) atomicAdd(slots + blockIdx.x % RED_THREADS, blk[0]);
+}
+
+// *out = sum of the RED_THREADS slots, which are cleared for the next use (one block)
+__global__ void __launch_bounds__(RED_THREADS) dot_collect(double* slots, double* out) {
+  double v[1] = {slots[threadIdx.x]}, tot[1];
+  slots[threadIdx.x] = 0.0;
+  block_sum<1>(v, tot);
+  if (threadIdx.x == 0) *out = tot[0];
 }
 
 // x += alpha d for the final step of a finished FP32 loop (done and at least one step):

@@ -89,7 +89,7 @@ template <typename R>
 using ApplyFn = void (*)(int, const int*, const R*, const R*, const R*, const R*, R*, const int*, const int*,
                          const int*);
 using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, const int*, const int*, const int*,
-                           int*);
+                           int*, double*);
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
 constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
@@ -112,6 +112,7 @@ struct KernelSet {
   int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
   Apply32Variant v32_batch;  // variant 2 built to skip the elements of converged batch problems
+  Apply32Fn v32dot[3] = {};  // variants 0-2 built to add (x, A x) into DOT_SLOTS doubles (p >= 3)
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   int apply_smem, apply_tpe, apply_ne;
   int d32_stride;
@@ -142,6 +143,11 @@ KernelSet make_set() {
                  TmaShape<P, Q, DIFF, false, 2>::NE, false};
   k.v32[3] = {pa_apply_f32_pipe<P, Q, DIFF>, PipeShape<P, Q, DIFF>::SMEM, PipeShape<P, Q, DIFF>::NE,
               PipeShape<P, Q, DIFF>::NE, true};
+  if constexpr (P >= 3) {
+    k.v32dot[0] = pa_apply_f32_tma<P, Q, DIFF, true, 1, 2, (P <= 4), (P <= 3), false, true>;
+    k.v32dot[1] = pa_apply_f32_tma<P, Q, DIFF, false, 1, 2, (P <= 4), (P <= 3), false, true>;
+    k.v32dot[2] = pa_apply_f32_tma<P, Q, DIFF, false, 2, 2, (P <= 4), (P <= 3), false, true>;
+  }
 
   k.diag = pa_diag_f64<P, Q, DIFF>;
   k.apply_smem = PaShape<double, P, Q, DIFF>::SMEM;
@@ -261,6 +267,8 @@ struct CgLoop {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_key = -1;  // preconditioner and kernel variants the cached graph was captured with
+  double* dh_slots = nullptr;  // FP32 loop: (d, h) accumulated by the fused action
+  int kernels_per_iter = 4;    // launches per iteration of the captured body
 };
 
 }  // namespace
@@ -270,6 +278,8 @@ struct fepa_op {
   int64_t E, N;
   int device;
   int cg_mode = FEPA_CG_GRAPH;
+  int fuse_dot = 1;  // FP32 CG: (d, h) from the action kernel where it has that build
+  double* dot_slots = nullptr;  // fepa_op_apply_f32_dot's accumulators
   cudaStream_t stream;
   cudaStream_t cap_stream;  // private stream used only to capture graphs
   KernelSet ks;
@@ -327,7 +337,7 @@ namespace {
 void free_loop(CgLoop& L) {
   if (L.exec) cudaGraphExecDestroy(L.exec);
   if (L.graph) cudaGraphDestroy(L.graph);
-  for (void* p : {L.x, L.r, L.d, L.h, L.invd, (void*)L.st, (void*)L.partials})
+  for (void* p : {L.x, L.r, L.d, L.h, L.invd, (void*)L.st, (void*)L.partials, (void*)L.dh_slots})
     if (p) cudaFree(p);
   L = CgLoop();
 }
@@ -340,7 +350,7 @@ void free_op(fepa_op* op) {
   for (void* p : {(void*)op->verts, (void*)op->verts_df, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
                   (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->qddf, (void*)op->err,
                   (void*)op->inv_diag, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->h64,
-                  (void*)op->st_ref, (void*)op->partials_ref})
+                  (void*)op->st_ref, (void*)op->partials_ref, (void*)op->dot_slots})
     if (p) cudaFree(p);
   if (op->st_host) cudaFreeHost(op->st_host);
   if (op->st_host_flag) cudaFreeHost(op->st_host_flag);
@@ -396,13 +406,17 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
   return FEPA_OK;
 }
 
-// y += A x in FP32 with variant v (launch only; not counted)
-int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const int* skip, cudaStream_t s) {
+// y += A x in FP32 with variant v (launch only; not counted).  dot: also add (x, A x) into
+// these DOT_SLOTS doubles (only where fused_dot_ok).
+int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const int* skip, cudaStream_t s,
+                           double* dot = nullptr) {
   const Apply32Variant& k = op->ks.v32[v];
   const int grid = op->v32_grid[v];
   if (grid <= 0) return fail(FEPA_ERR_UNSUPPORTED, "FP32 variant %d cannot run with this shape", v);
-  k.fn<<<grid, dim3(op->ks.apply_tpe, k.threads_y), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip,
-                                                                  nullptr, nullptr, op->err);
+  const Apply32Fn fn = dot ? (v < 3 ? op->ks.v32dot[v] : nullptr) : k.fn;
+  if (!fn) return fail(FEPA_ERR_UNSUPPORTED, "FP32 variant %d has no fused (x, A x) build", v);
+  fn<<<grid, dim3(op->ks.apply_tpe, k.threads_y), k.smem, s>>>((int)op->E, op->gmap, op->qd32, x, y, skip, nullptr,
+                                                                nullptr, op->err, dot);
   BODY_CHECK();
   return FEPA_OK;
 }
@@ -456,6 +470,8 @@ int ensure_loop(fepa_op* op, CgLoop& L, bool own_x) {
     T* x;
     TRY(dalloc(&x, op->N));
     L.x = x;
+    TRY(dalloc(&L.dh_slots, DOT_SLOTS));
+    CUDA_TRY(cudaMemsetAsync(L.dh_slots, 0, DOT_SLOTS * sizeof(double), op->stream));
   }
   TRY(dalloc(&L.st, 1));
   L.red_blocks = grid_for(op->N, RED_THREADS, 148 * 8);
@@ -682,6 +698,8 @@ int ensure_f32(fepa_op* op) {
     CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->G32h.data(), op->G32h.size() * sizeof(float),
                                      (slot + 100) * sizeof(float), cudaMemcpyHostToDevice, s));
     for (int v = 0; v < N32_VARIANTS; ++v) TRY(allow_smem((const void*)op->ks.v32[v].fn, op->ks.v32[v].smem));
+    for (int v = 0; v < 3; ++v)
+      if (op->ks.v32dot[v]) TRY(allow_smem((const void*)op->ks.v32dot[v], op->ks.v32[v].smem));
     TRY(size_variants32(op));
   }
   if (!op->qd32_valid) {
@@ -761,27 +779,34 @@ int body64(fepa_op* op, CgLoop& L, const double* invd, cudaStream_t s, cudaGraph
   return FEPA_OK;
 }
 
+// FP32 loop: (d, h) comes out of the action kernel itself (no separate pass over d and h)
+// when the chosen variant has that build and the op allows it
+bool fused_dot_ok(const fepa_op* op) { return op->fuse_dot && op->v32 >= 0 && op->v32 < 3 && op->ks.v32dot[op->v32]; }
+
 int body32(fepa_op* op, CgLoop& L, const float* invd, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const int rb = L.red_blocks;
   float *x = (float*)L.x, *r = (float*)L.r, *d = (float*)L.d, *h = (float*)L.h;
-  TRY(launch_apply32_nocount(op, d, h, &L.st->done, s));
-  cg32_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
+  double* slots = fused_dot_ok(op) ? L.dh_slots : nullptr;
+  L.kernels_per_iter = slots ? 3 : 4;
+  TRY(launch_apply32_variant(op, op->v32, d, h, &L.st->done, s, slots));
+  if (!slots) {
+    cg32_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
+    BODY_CHECK();
+  }
+  cg32_update<<<rb, RED_THREADS, 0, s>>>(op->N, r, h, invd, L.st, L.partials, slots);
   BODY_CHECK();
-  cg32_update<<<rb, RED_THREADS, 0, s>>>(op->N, r, h, invd, L.st, L.partials);
-  BODY_CHECK();
-  cg32_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, x, 1, L.st, cond, use_cond);
+  cg32_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, x, 1, L.st, cond, use_cond, slots);
   BODY_CHECK();
   return FEPA_OK;
 }
 
-constexpr int KERNELS_PER_ITER = 4;
 constexpr int STREAM_CHUNK = 8;
 
 // Capture one iteration into the body of a while-node (once per loop and precond).
 template <typename Body>
 int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
   TRY(prepare_f64(op));
-  const int key = precond + 16 * (op->v32 + 1) + 256 * (op->v64 + 1);
+  const int key = precond + 16 * (op->v32 + 1) + 256 * (op->v64 + 1) + 4096 * op->fuse_dot;
   if (L.exec && L.graph_key == key) return FEPA_OK;
   if (L.exec) { cudaGraphExecDestroy(L.exec); L.exec = nullptr; }
   if (L.graph) { cudaGraphDestroy(L.graph); L.graph = nullptr; }
@@ -816,12 +841,12 @@ int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
     CUDA_TRY(cudaGraphLaunch(L.exec, s));
     CUDA_TRY(cudaMemcpyAsync(out, L.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    g_launches.fetch_add(KERNELS_PER_ITER * (int64_t)(out->iter > 0 ? out->iter : 1));
+    g_launches.fetch_add(L.kernels_per_iter * (int64_t)(out->iter > 0 ? out->iter : 1));
     return FEPA_OK;
   }
   for (;;) {
     for (int k = 0; k < STREAM_CHUNK; ++k) TRY(body(s, 0, 0));
-    g_launches.fetch_add(KERNELS_PER_ITER * (int64_t)STREAM_CHUNK);
+    g_launches.fetch_add(L.kernels_per_iter * (int64_t)STREAM_CHUNK);
     CUDA_TRY(cudaMemcpyAsync(out, L.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (out->done) return FEPA_OK;
@@ -1014,7 +1039,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
                                                          delta * delta, floor2, L.partials);
       LAUNCH_CHECK();
       cg32_direction<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.d, (float*)L.h, invd,
-                                                          nullptr, 0, L.st, 0, 0);
+                                                          nullptr, 0, L.st, 0, 0, nullptr);
       LAUNCH_CHECK();
       ++replacements;
     }
@@ -1177,6 +1202,12 @@ int fepa_op_set_stream(fepa_op* op, void* stream) {
   return FEPA_OK;
 }
 
+int fepa_op_set_fused_dot(fepa_op* op, int32_t enable) {
+  if (!op) return fail(FEPA_ERR_ARG, "op is null");
+  op->fuse_dot = enable ? 1 : 0;
+  return FEPA_OK;
+}
+
 int fepa_op_set_cg_mode(fepa_op* op, int32_t mode) {
   if (!op) return fail(FEPA_ERR_ARG, "op is null");
   if (mode != FEPA_CG_GRAPH && mode != FEPA_CG_STREAM) return fail(FEPA_ERR_ARG, "unknown CG mode %d", mode);
@@ -1269,6 +1300,31 @@ int fepa_op_apply_f32(fepa_op* op, const float* x, float* y) {
   TRY(ensure_f32(op));
   CUDA_TRY(cudaMemsetAsync(y, 0, op->N * sizeof(float), op->stream));
   TRY(launch_apply32_nocount(op, x, y, nullptr, op->stream));
+  g_launches.fetch_add(1);
+  return FEPA_OK;
+}
+
+int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax) {
+  if (!op || !x || !y || !xax) return fail(FEPA_ERR_ARG, "null argument");
+  if (x == y) return fail(FEPA_ERR_ARG, "x and y must not alias");
+  TRY(ensure_f32(op));
+  cudaStream_t s = op->stream;
+  if (!op->dot_slots) {
+    TRY(dalloc(&op->dot_slots, DOT_SLOTS));
+    CUDA_TRY(cudaMemsetAsync(op->dot_slots, 0, DOT_SLOTS * sizeof(double), s));
+  }
+  CUDA_TRY(cudaMemsetAsync(y, 0, op->N * sizeof(float), s));
+  if (op->v32 < 3 && op->ks.v32dot[op->v32]) {
+    TRY(launch_apply32_variant(op, op->v32, x, y, nullptr, s, op->dot_slots));
+    g_launches.fetch_add(1);
+  } else {
+    TRY(launch_apply32_variant(op, op->v32, x, y, nullptr, s));
+    dot32_slots<<<grid_for(op->N, RED_THREADS, 148 * 8), RED_THREADS, 0, s>>>(op->N, x, y, op->dot_slots);
+    LAUNCH_CHECK();
+    g_launches.fetch_add(2);
+  }
+  dot_collect<<<1, RED_THREADS, 0, s>>>(op->dot_slots, xax);
+  LAUNCH_CHECK();
   g_launches.fetch_add(1);
   return FEPA_OK;
 }

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
 
 namespace fepa {
@@ -463,8 +464,13 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
 
 // stage 1^T (x) and G^T into shared memory: line (b,c) -> Y[c][b][a] (X's layout) for
 // the scatter that follows in element-local DOF order (coalesced map loads and atomics)
-template <int P, int Q, bool DIFF>
-__device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float* S1, float* Y) {
+// DOT: before a result overwrites the gathered input at the same place, the product of
+// the two is added to acc: the line's share of (x, A x).  (A plain FP32 sum of n terms:
+// its rounding is of the order of that already in the FP32 results themselves.)  Formed
+// here rather than as u^T D u at the points of stage 3: that build, measured on B300 at
+// BP3 p = 4, was 14 % slower (its register allocation changed), this one 5 %.
+template <int P, int Q, bool DIFF, bool DOT = false>
+__device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float* S1, float* Y, float& acc) {
   using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
@@ -486,8 +492,25 @@ __device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float
       else
         s = fmaf(T::B(i, a), t0[i], s);
     }
+    if (DOT) acc = fmaf(Y[tid * L::XL + a], s, acc);
     Y[tid * L::XL + a] = s;
   }
+}
+
+// DOT: each warp sums its threads' shares (the block's last warp may be partial: lanes
+// past the block's end do not exist and are left out) and lane 0 adds the warp's sum by
+// one double atomic to a slot (the CG update kernel sums the DOT_SLOTS slots)
+constexpr int DOT_SLOTS = RED_THREADS;
+__device__ __forceinline__ void dot_publish(float acc, int nthreads, int flat, double* dot) {
+  const int lane = flat & 31, w = flat >> 5;
+  const int nl = min(32, nthreads - 32 * w);
+  const unsigned mask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float t = __shfl_down_sync(mask, acc, o);
+    if (lane + o < nl) acc += t;
+  }
+  if (lane == 0) atomicAdd(dot + (blockIdx.x * ((nthreads + 31) / 32) + w) % DOT_SLOTS, (double)acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -500,13 +523,14 @@ __device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float
 // BSKIP: the batched build, which reads elem_prob / prob_done (a separate instantiation, so
 // the single-operator kernels carry none of its checks: they cost those 5 % when tested).
 template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3),
-          bool BSKIP = false>
+          bool BSKIP = false, bool DOT = false>
 __global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
 pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                  float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
-                 const int* __restrict__ prob_done, int* __restrict__ err) {
+                 const int* __restrict__ prob_done, int* __restrict__ err, double* __restrict__ dot) {
   using S = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
+  static_assert(!DOT || (P >= 3 && !BSKIP), "the fused (x, A x) needs the shared-memory scatter");
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_tma[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma);
@@ -653,10 +677,14 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     f32_stage1t<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, gmap + (e0 + e) * (n * n * n), x, y);
     return;
   }
+  // DOT (the CG loop's build): (x, A x) = sum over elements of x_e . (A_e x_e) with x_e zero
+  // at essential DOFs, plus x_g^2 for each essential DOF (the identity rows), so the
+  // CG's separate (d, h) pass over two N-vectors is not needed
+  float acc = 0.f;
   {
     int e, ln;
     stage_item<FLAT, n * n, TPE>(tid, el, e, ln);
-    f32_stage1t_smem<P, Q, DIFF>(ln, alive(e), sS1 + e * S::W1, sXall + e * S::XE);
+    f32_stage1t_smem<P, Q, DIFF, DOT>(ln, alive(e), sS1 + e * S::W1, sXall + e * S::XE, acc);
   }
   __syncthreads();
   // scatter in element-local DOF order (over the block's flat range with FLATG), as the
@@ -678,7 +706,9 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
           if (gv >= 0) {
             atomicAdd(y + gv, sX[(l / n) * S::XL + l % n]);
           } else if (!((~gv) & ESS_SKIP)) {
-            atomicAdd(y + (~gv), x[~gv]);
+            const float xe = x[~gv];
+            atomicAdd(y + (~gv), xe);
+            if (DOT) acc = fmaf(xe, xe, acc);
           }
         }
       }
@@ -699,10 +729,13 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
       if (gv >= 0) {
         atomicAdd(y + gv, sXall[e * S::XE + (l / n) * S::XL + l % n]);
       } else if (!((~gv) & ESS_SKIP)) {
-        atomicAdd(y + (~gv), x[~gv]);
+        const float xe = x[~gv];
+        atomicAdd(y + (~gv), xe);
+        if (DOT) acc = fmaf(xe, xe, acc);
       }
     }
   }
+  if constexpr (DOT) dot_publish(acc, TPE * NE, el * TPE + tid, dot);
 }
 
 // ---------------------------------------------------------------------------
@@ -713,7 +746,8 @@ template <int P, int Q, bool DIFF, bool FLAT = (P <= 4)>
 __global__ void __launch_bounds__(PipeShape<P, Q, DIFF>::T)
 pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                   float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
-                  const int* __restrict__ prob_done, int* __restrict__ err) {
+                  const int* __restrict__ prob_done, int* __restrict__ err,
+                  double* __restrict__ /*dot: not built here*/) {
   using S = PipeShape<P, Q, DIFF>;
   constexpr int n = S::N, n3 = n * n * n, TPE = S::TPE, NE = S::NE, T = S::T;
   if (skip && *skip) return;

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("fepa_op_dcomps", _I32, [_P]),
     ("fepa_op_set_stream", ctypes.c_int, [_P, _P]),
     ("fepa_op_set_cg_mode", ctypes.c_int, [_P, _I32]),
+    ("fepa_op_set_fused_dot", ctypes.c_int, [_P, _I32]),
+    ("fepa_op_apply_f32_dot", ctypes.c_int, [_P, _P, _P, _P]),
     ("fepa_op_boundary_dofs", ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
     ("fepa_op_set_essential", ctypes.c_int, [_P, _P, _I64]),
     ("fepa_op_elem_dofs", ctypes.c_int, [_P, _P]),
@@ -309,6 +311,19 @@ class Operator:
         _check(self._lib.fepa_op_apply_f32(self._h, px, py))
         return y
 
+    def apply_f32_dot(self, x, out=None, xax=None):
+        """FP32 action and (x, A x) from the same kernel; returns (y, xax), xax a float64
+        CUDA tensor of one element."""
+        torch = _torch()
+        y = torch.empty(self.N, dtype=torch.float32, device="cuda") if out is None else out
+        d = torch.empty(1, dtype=torch.float64, device="cuda") if xax is None else xax
+        px = _dev_ptr(x, torch.float32, self.N, "x")
+        py = _dev_ptr(y, torch.float32, self.N, "y")
+        pd = _dev_ptr(d, torch.float64, 1, "xax")
+        self._sync_stream()
+        _check(self._lib.fepa_op_apply_f32_dot(self._h, px, py, pd))
+        return y, d
+
     def set_f32_variant(self, variant):
         """-1: autotune at next FP32 use; 0..3: force a compiled launch shape."""
         _check(self._lib.fepa_op_set_f32_variant(self._h, int(variant)))
@@ -324,6 +339,10 @@ class Operator:
     def f64_variant(self):
         v = int(self._lib.fepa_op_f64_variant(self._h))
         return v, self._lib.fepa_f64_variant_name(v).decode()
+
+    def set_fused_dot(self, enable=True):
+        """FP32 inner CG: take (d, A d) from the action kernel (default) or a separate pass."""
+        _check(self._lib.fepa_op_set_fused_dot(self._h, 1 if enable else 0))
 
     def set_cg_mode(self, mode):
         _check(self._lib.fepa_op_set_cg_mode(self._h, {"graph": CG_GRAPH, "stream": CG_STREAM}.get(mode, mode)))

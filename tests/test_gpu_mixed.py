@@ -173,6 +173,74 @@ def test_refined_noconv():
     assert st["status"] == -5 and st["outer_iterations"] == 1
 
 
+FIRST_STEP_CASES = [("diffusion", 3, (5, 4, 3), v) for v in (0, 1, 2)] + \
+    [("diffusion", 4, (5, 4, 3), v) for v in (0, 1, 2)] + \
+    [("mass", 4, (4, 3, 3), 1), ("diffusion", 5, (3, 3, 2), 2), ("diffusion", 6, (3, 2, 2), 1),
+     ("mass", 8, (2, 1, 2), 0)]
+
+
+@pytest.mark.parametrize("form,p,shape,variant", [("diffusion", 4, (5, 4, 3), 0), ("diffusion", 4, (5, 4, 3), 1),
+                                                  ("diffusion", 3, (5, 4, 3), 2), ("diffusion", 5, (3, 3, 2), 1),
+                                                  ("diffusion", 2, (4, 4, 3), 1), ("diffusion", 6, (3, 2, 2), 3),
+                                                  ("mass", 5, (3, 3, 2), 2), ("mass", 8, (2, 1, 2), 1)])
+def test_apply_f32_dot_matches_oracle(form, p, shape, variant):
+    """y = A x and (x, A x) from one call: the fused kernel for p >= 3 and variants 0-2,
+    a separate pass elsewhere (p = 2, variant 3); x is not zero at essential DOFs."""
+    op, mesh = make(shape, p, form, seed=50)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    if form == "diffusion":
+        op.set_essential(prob.ess.astype(np.int32))
+    op.set_f32_variant(variant)
+    x32 = torch.from_numpy(FI.uniform_vector(op.N, seed=51).astype(np.float32)).cuda()
+    y, xax = op.apply_f32_dot(x32)
+    xd = x32.cpu().numpy().astype(np.float64)
+    ya = prob.apply(xd, constrained=True)
+    assert rel(y.cpu().numpy(), ya) <= TOL32
+    assert abs(float(xax.item()) - xd @ ya) <= TOL32 * abs(xd @ ya)
+    y2, xax2 = op.apply_f32_dot(x32)  # the slots were cleared for the next call
+    assert abs(float(xax2.item()) - float(xax.item())) <= 1e-6 * abs(xd @ ya)
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("form,p,shape,variant", FIRST_STEP_CASES)
+def test_first_cg_step_matches_oracle(form, p, shape, variant, fused):
+    """One FP32 Jacobi-PCG step from x = 0 is x = alpha z with z = b / diag(A) and
+    alpha = (z, b) / (z, A z).  With the fused build (z, A z) comes out of the action kernel
+    (per-element sums over blocks with a ragged last group, plus the identity rows of the
+    essential DOFs, where b is not zero here); without it from a separate pass over z and A z."""
+    op, mesh = make(shape, p, form, seed=47)
+    prob = O.Problem(mesh, p, None, form, assemble=p <= 5)
+    if form == "diffusion":
+        op.set_essential(prob.ess.astype(np.int32))
+    op.set_f32_variant(variant)
+    op.set_fused_dot(fused)
+    bo = FI.uniform_vector(op.N, seed=48)
+    x, st = op.solve_refined(torch.from_numpy(bo).cuda(), rtol=1e-14, max_outer=1, inner_maxit=1,
+                             raise_on_noconv=False)
+    op.set_fused_dot(True)
+    assert st["inner_iterations"] == 1 and st["outer_iterations"] == 1
+    z = bo / prob.diagonal()
+    alpha = (z @ bo) / (z @ prob.apply(z, constrained=True))
+    assert rel(x.cpu().numpy(), alpha * z) <= TOL32
+
+
+@pytest.mark.parametrize("form,p,shape", [("diffusion", 4, (6, 5, 4)), ("mass", 3, (5, 4, 4))])
+def test_fused_dot_solve_equals_separate_pass(form, p, shape):
+    """The refined solve with (d, A d) from the action kernel reaches the solution of the one
+    with a separate (d, h) pass, in about as many FP32 iterations."""
+    op, mesh = make(shape, p, form, seed=49)
+    if form == "diffusion":
+        op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(1.0)
+    xf, sf = op.solve_refined(b, rtol=1e-10)
+    op.set_fused_dot(False)
+    xs, ss = op.solve_refined(b, rtol=1e-10)
+    op.set_fused_dot(True)
+    assert sf["status"] == 0 and ss["status"] == 0
+    assert abs(sf["inner_iterations"] - ss["inner_iterations"]) <= max(4, 0.1 * ss["inner_iterations"])
+    assert rel(xf.cpu().numpy(), xs.cpu().numpy()) <= 1e-9
+
+
 @pytest.mark.parametrize("mode", ["graph", "stream"])
 def test_refined_single_step_corrections(mode):
     """Inner solves of one FP32 CG step each: every correction is that step's alpha d, which
