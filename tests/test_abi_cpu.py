@@ -60,6 +60,8 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.fepa_op_create(1, 1, 1, v.ctypes.data_as(ctypes.c_void_p), 2, 0, 5, None, ctypes.byref(h)) == fepa.ERR_ARG
     assert b"unknown form" in lib.fepa_last_error()
     assert lib.fepa_cg_solve(None, None, None, 1e-10, 10, 1, None) == fepa.ERR_ARG
+    assert lib.fepa_op_set_fused_dot(None, 1) == fepa.ERR_ARG
+    assert lib.fepa_op_apply_f32_dot(None, None, None, None) == fepa.ERR_ARG
 
 
 def test_product_code_never_imports_oracle():
