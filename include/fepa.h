@@ -280,7 +280,8 @@ int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, i
  * Each outer step forms r = b - A x with the FP64 operator and FP64 reductions; when
  * ||r||_2 > rtol ||b||_2 it solves A e = r with the FP32 operator (fepa_op_apply_f32)
  * to relative residual inner_rtol (at most inner_maxit iterations; FP32 vectors, dot
- * products accumulated to FP64 accuracy, FP64 scalars) and updates x += e in FP64.
+ * products accumulated to FP64 accuracy, except (d, A d), which by default comes out of the
+ * FP32 action kernel (fepa_op_set_fused_dot); FP64 scalars) and updates x += e in FP64.
  * When less than inner_rtol is enough to reach rtol (the last correction) the inner
  * tolerance is relaxed to 0.25 rtol ||b|| / ||r||, at most 0.5.
  *   b, x        device, N doubles (x: initial guess in, solution out)
@@ -293,8 +294,8 @@ int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int
 
 /*
  * Mixed-precision CG with reliable updates (residual replacement): a single FP32
- * Jacobi-PCG recurrence (FP32 operator and vectors, dot products to FP64 accuracy, FP64
- * scalars) whose residual is replaced by the FP64 residual b - A x (FP64 operator and
+ * Jacobi-PCG recurrence (FP32 operator and vectors, dot products to FP64 accuracy or, for
+ * (d, A d), fused into the FP32 action (fepa_op_set_fused_dot); FP64 scalars) whose residual is replaced by the FP64 residual b - A x (FP64 operator and
  * reductions) each time it has fallen by the factor delta since the last replacement;
  * the FP32 iterate is added to the FP64 x first.  The search direction and scalars
  * carry over each replacement, so unlike fepa_solve_refined the Krylov space is kept and
