@@ -2,13 +2,18 @@
 
 One step = one pass of the whole hot path over one synthetic problem:
 geometry setup D from the (device-resident) vertices, load vector of the sine
-manufactured solution, matrix-free diagonal, and the solve to a relative FP64
-residual of 1e-10 (every CG iteration applies the fused G^T B^T D B G kernel).
-Two forms of the solve are timed on the same problem: the mixed-precision one (FP64
-iterative refinement around an FP32 Jacobi-PCG; the headline `value`) and the plain
-FP64 Jacobi-PCG (`fp64_plain`); beside them the same solve by mixed-precision CG with reliable
-updates (`mixed_reliable`) and by FP64 CG preconditioned with an FP32 p-multigrid V-cycle
-(`mg_pcg_fp32_vcycle`).
+manufactured solution, matrix-free diagonal, and the solve (every CG iteration
+applies the fused G^T B^T D B G kernel).  Each solver form is run to the same
+accuracy: a solution within --target-err (1e-10, relative l2) of a reference
+solution of the same discrete problem (FP64 CG with an FP64 p-multigrid V-cycle and
+the native binary64 operator, to a residual of 1e-13); its outer tolerance is the
+loosest of --rtol / 3^k that achieves this, found before the timed steps.
+Forms: the mixed-precision one (FP64 iterative refinement around an FP32
+Jacobi-PCG; the headline `value`), the plain FP64 Jacobi-PCG (`fp64_plain`), the
+mixed-precision CG with reliable updates (`mixed_reliable`) and FP64 CG preconditioned
+with an FP32 p-multigrid V-cycle (`mg_pcg_fp32_vcycle`).  A second BP3 case (p=6 on
+32^3 elements, `bp3_p6_n32`) and short runs of the 512-problem batch (`batch`) and of
+the served stream (`serve`) ride on the same line.
 value = N * (CG iterations) / step time, summed over ranks (independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -179,6 +184,8 @@ def cpu_threads():
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands, on this host's cores, on a bounded sample of the BP3
+    workload (same p, recipe and solver on --oracle-n^3 elements instead of --n^3)."""
     if rank != 0:
         return 0
     p, n_s = args.p, args.oracle_n
@@ -191,14 +198,17 @@ def run_reference(args, rank, world):
         tot_t += t
         its.append(it)
     value = tot_dofit / tot_t / 1e9
-    sample = (f"oracle (CSR assembly by quadrature + Jacobi PCG to 1e-10, numpy/scipy) on {n_s}^3 elements, "
-              f"p={p}, N={(p * n_s + 1) ** 3}; timed: assembly, load vector, solve")
+    sample = (f"oracle (CSR assembly by quadrature + Jacobi PCG to 1e-10, numpy/scipy with their default thread "
+              f"pools) on {n_s}^3 elements, p={p}, N={(p * n_s + 1) ** 3}, a bounded sample of the {args.n}^3 "
+              f"workload; timed: assembly, load vector, solve")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(p, args.n, p + 2), "sample": sample},
+            "config": {"workload": workload_name(p, n_s, p + 2) + f" (CPU sample of the {args.n}^3 workload)",
+                       "full_workload": workload_name(p, args.n, p + 2), "sample": sample},
             "iterations": its,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample,
+                             "host_nproc": os.cpu_count(), "host_cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -206,14 +216,17 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- our arm
 
-def run_ours(args, rank, world, dist):
+def bp3_case(args, p, n, rank, world, dist, steps, forms, with_e2e, with_roofline=True):
+    """Time the BP3 sine problem (p, n^3 elements) for the solver forms in `forms` ("mixed",
+    "fp64", "reliable", "mg") on one device.  Each form's outer tolerance is first tightened from
+    --rtol until its solution is within --target-err (relative l2) of a reference solution of the
+    same discrete problem (see reference_solution), so that the forms are compared at equal
+    accuracy; then `steps` steps are timed.  Returns {form: results} and the reference's stats."""
     import torch
 
     import paper_2402_15940_b300 as F
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    p, n = args.p, args.n
     verts_np = FI.perturbed_cube_vertices(n, n, n, seed=rank)
     op = F.Operator(n, n, n, verts_np, p, form="diffusion")
     q, N, E = op.q, op.N, op.E
@@ -238,20 +251,20 @@ def run_ours(args, rank, world, dist):
 
     mg = {}
 
-    def solve(prec):
+    def solve(prec, rtol):
         if prec == "fp64":
-            _, st = op.solve(b, x, rtol=args.rtol, maxit=args.maxit)
+            _, st = op.solve(b, x, rtol=rtol, maxit=args.maxit)
             return st["iterations"], st
         if prec == "mg":
-            _, st = mg["mg"].solve(b, x, rtol=args.rtol, maxit=args.maxit)
+            _, st = mg["mg"].solve(b, x, rtol=rtol, maxit=args.maxit)
             return st["iterations"], st
         if prec == "reliable":
-            _, st = op.solve_reliable(b, x, rtol=args.rtol, delta=args.delta)
+            _, st = op.solve_reliable(b, x, rtol=rtol, delta=args.delta)
             return st["inner_iterations"], st
-        _, st = op.solve_refined(b, x, rtol=args.rtol, inner_rtol=args.inner_rtol)
+        _, st = op.solve_refined(b, x, rtol=rtol, inner_rtol=args.inner_rtol)
         return st["inner_iterations"], st
 
-    def step(prec):
+    def step(prec, rtol):
         op.set_vertices(verts)          # D from the trilinear map (a1)
         if prec == "mg":
             if "mg" not in mg:
@@ -260,11 +273,49 @@ def run_ours(args, rank, world, dist):
                 mg["mg"].update()       # every level follows the mesh: D, diagonals, eigenvalue bounds
         op.rhs_sine(scale, out=b)       # load vector (a11)
         x.zero_()
-        return solve(prec)              # diagonal (a10) + PCG (a9; a2-a8 in every iteration)
+        return solve(prec, rtol)        # diagonal (a10) + PCG (a9; a2-a8 in every iteration)
+
+    def reference_solution():
+        """The same discrete problem solved by another solver in native FP64: CG preconditioned
+        by an FP64 p-multigrid V-cycle, with the DFMA (binary64) operator action, to a relative
+        residual of --ref-rtol.  Its own FP64 residual b - A x_ref is reported beside it."""
+        rop = F.Operator(n, n, n, verts_np, p, form="diffusion")
+        rop.set_essential(rop.boundary_dofs())
+        rop.set_f64_variant(0)
+        rmg = F.Multigrid(rop, smooth_degree=2, coarse_degree=24, precision="fp64")
+        rb = rop.rhs_sine(scale)
+        xr, st = rmg.solve(rb, rtol=args.ref_rtol, maxit=500)
+        res = torch.linalg.norm(rb - rop.apply(xr)) / torch.linalg.norm(rb)
+        info = {"solver": f"FP64 CG + FP64 p-multigrid V-cycle, native binary64 (DFMA) operator, rtol "
+                          f"{args.ref_rtol}", "iterations": st["iterations"], "true_rel_residual": float(res)}
+        del rmg, rop
+        return xr, info
+
+    xref, ref_info = reference_solution() if args.target_err > 0 else (None, None)
+
+    def sol_err():
+        if xref is None:
+            return None
+        return float(torch.linalg.norm(x - xref) / torch.linalg.norm(xref))
+
+    def calibrate(prec):
+        """Loosest outer tolerance (from --rtol down by factors of 3) whose solution error is
+        within --target-err; these solves also warm the form up."""
+        rt = args.rtol
+        tried = []
+        for _ in range(7):
+            step(prec, rt)
+            e = sol_err()
+            tried.append({"rtol": rt, "solution_rel_err": e})
+            if e is None or e <= args.target_err:
+                break
+            rt /= 3.0
+        return rt, tried
 
     def timed(prec):
+        rtol, tried = calibrate(prec)
         for _ in range(args.warmup):
-            step(prec)
+            step(prec, rtol)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -273,8 +324,8 @@ def run_ours(args, rank, world, dist):
         its, stats = [], []
         with ClockSampler(local) as clk:
             ev0.record()
-            for _ in range(args.steps):
-                it, st = step(prec)
+            for _ in range(steps):
+                it, st = step(prec, rtol)
                 its.append(it)
                 stats.append(st)
             ev1.record()
@@ -283,8 +334,9 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         launches = F.launch_count() - l0
         t, work = aggregate(ev0.elapsed_time(ev1) / 1e3, N * sum(its))
-        return {"value": work / t / 1e9, "ms_per_step": 1e3 * t / args.steps, "iterations_per_step": its,
-                "gpu_launches": launches, "clocks": clk.summary(), "stats": stats[-1]}
+        return {"value": work / t / 1e9, "ms_per_step": 1e3 * t / steps, "iterations_per_step": its,
+                "gpu_launches": launches, "clocks": clk.summary(), "stats": stats[-1], "rtol": rtol,
+                "solution_rel_err": sol_err(), "rtol_search": tried}
 
     def kernel_time(prec, reps=20):
         if prec == "fp64":
@@ -310,7 +362,7 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         return k0.elapsed_time(k1) / 1e3 / reps
 
-    def e2e(prec):
+    def e2e(prec, rtol, k):
         vh = torch.from_numpy(verts_np).pin_memory().numpy()
         bh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
         op.set_vertices(verts)
@@ -321,30 +373,27 @@ def run_ours(args, rank, world, dist):
         barrier()
         t0 = time.perf_counter()
         its = 0
-        for _ in range(args.steps):
+        for _ in range(k):
             op.set_vertices(vh)
             xh[:] = 0.0
             if prec == "fp64":
-                _, st = op.solve_host(bh, xh, rtol=args.rtol, maxit=args.maxit)
+                _, st = op.solve_host(bh, xh, rtol=rtol, maxit=args.maxit)
                 its += st["iterations"]
             else:
-                _, st = op.solve_refined_host(bh, xh, rtol=args.rtol, inner_rtol=args.inner_rtol)
+                _, st = op.solve_refined_host(bh, xh, rtol=rtol, inner_rtol=args.inner_rtol)
                 its += st["inner_iterations"]
         torch.cuda.synchronize()
         te, work = aggregate(time.perf_counter() - t0, N * its)
         return {"value": work / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(vh.nbytes + 2 * bh.nbytes),
-                "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": 1e3 * te / args.steps}
+                "d2h_bytes_per_step": int(xh.nbytes), "ms_per_step": 1e3 * te / k, "steps": k}
 
     hbm_peak, hbm_src = peaks()
     results = {}
-    if args.multigrid:
-        results["mg"] = timed("mg")
-    if args.reliable:
-        results["reliable"] = timed("reliable")
-    for prec in ("mixed", "fp64"):
-        if args.precision not in (prec, "both"):
-            continue
+    for prec in forms:
         r = timed(prec)
+        results[prec] = r
+        if prec not in ("mixed", "fp64") or not with_roofline:
+            continue
         t_apply = kernel_time(prec)
         if prec == "fp64":
             fl = flops_per_elem(p + 1, q, "diffusion") * E
@@ -373,6 +422,8 @@ def run_ours(args, rank, world, dist):
             r["dfma_kernel"] = {"kernel": f"pa_apply<double,{p},{q},diffusion>", "apply_ms": 1e3 * t_dfma,
                                 "achieved": fl / t_dfma / 1e9, "unit": "GFLOP/s",
                                 "frac_of_fp64_pipe": fl / t_dfma / 1e9 / FP64_PEAK_GFLOPS}
+            r["arithmetic"] = ("FP64-accurate double-float on the FP32 pipe (autotuned)" if v64 == 1 else
+                               "native binary64 (DFMA, autotuned)")
         else:
             by = bytes_per_elem(p + 1, q, "diffusion", p, n, word=4) * E
             ach = by / t_apply / 1e9
@@ -390,15 +441,86 @@ def run_ours(args, rank, world, dist):
                              "frac_of_nominal_8tbs": ach / 8000.0,
                              "fp32_tflops": fl / t_apply / 1e12}
         r["apply_gdofs"] = N / t_apply / 1e9
-        r["e2e"] = None if args.no_e2e else e2e(prec)
-        results[prec] = r
+        if with_e2e:
+            # the headline form end to end every step; the FP64 form on a few steps (its solves are long)
+            k = steps if prec == "mixed" else min(steps, 3)
+            r["e2e"] = e2e(prec, r["rtol"], k)
+    del op, mg
+    torch.cuda.empty_cache()
+    return results, ref_info, (N, E, q)
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_cpu_baseline(p, n_s):
+    """The oracle as it stands on this host: once limited to one thread and once with its
+    libraries' default thread pools (all cores; numpy's BLAS parallelises the element
+    matrices, scipy's sparse products stay on one thread)."""
+    out = {}
+    try:
+        from threadpoolctl import threadpool_limits
+    except Exception:
+        threadpool_limits = None
+    for label, lim in (("single_thread", 1), ("all_cores", None)):
+        if threadpool_limits is not None and lim is not None:
+            with threadpool_limits(limits=lim):
+                d, t, it = oracle_sample(p, n_s)
+                th = 1
+        else:
+            d, t, it = oracle_sample(p, n_s)
+            th = cpu_threads()
+        out[label] = {"value": d / t / 1e9, "seconds": t, "threads": th, "iterations": it}
+    return out
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import paper_2402_15940_b300 as F
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    p, n = args.p, args.n
+    forms = [f for f in ("mg", "reliable", "mixed", "fp64")
+             if (f != "mg" or args.multigrid) and (f != "reliable" or args.reliable)
+             and (f not in ("mixed", "fp64") or args.precision in (f, "both"))]
+    results, ref_info, (N, E, q) = bp3_case(args, p, n, rank, world, dist, args.steps, forms,
+                                            with_e2e=not args.no_e2e)
+    second = None
+    if args.p2 > 0:
+        k2 = min(args.steps, args.steps2)
+        res2, ref2, (N2, E2, q2) = bp3_case(args, args.p2, args.n2, rank, world, dist, k2,
+                                            [f for f in ("mixed", "fp64") if f in forms], with_e2e=False)
+        second = {"workload": workload_name(args.p2, args.n2, q2), "steps": k2, "reference": ref2}
+        for f, r in res2.items():
+            second[f] = {k: r.get(k) for k in ("value", "ms_per_step", "iterations_per_step", "rtol",
+                                                 "solution_rel_err", "roofline", "apply_gdofs", "gpu_launches",
+                                                 "clocks", "arithmetic")}
+        if "mixed" in res2 and "fp64" in res2:
+            second["time_to_solution_speedup_vs_fp64"] = res2["fp64"]["ms_per_step"] / res2["mixed"]["ms_per_step"]
+
+    extras = {}
+    if args.extras and world == 1:
+        extras["batch"] = run_batch(args, rank, world, dist, steps=min(args.steps, 2), warmup=1, quiet=True)
+        extras["serve"] = run_serve(args, rank, world, dist, rates=[float(args.serve_rate)], quiet=True)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        d, tcpu, it = oracle_sample(p, args.oracle_n)
-        cpu = {"value": d / tcpu / 1e9, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+        cb = oracle_cpu_baseline(p, args.oracle_n)
+        allc = cb["all_cores"]
+        cpu = {"value": allc["value"], "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
                "sample": f"oracle CSR assembly + Jacobi PCG to 1e-10 on {args.oracle_n}^3 elements, p={p}, "
-                         f"N={(p * args.oracle_n + 1) ** 3}, {it} iterations, {tcpu:.1f} s"}
+                         f"N={(p * args.oracle_n + 1) ** 3}, {allc['iterations']} iterations, "
+                         f"{allc['seconds']:.1f} s with the libraries' default thread pools",
+               "single_thread": cb["single_thread"], "host_nproc": os.cpu_count(), "host_cpu": cpu_model()}
 
     if rank == 0:
         head = results.get("mixed") or results["fp64"]
@@ -411,14 +533,17 @@ def run_ours(args, rank, world, dist):
                 "data": "synthetic",
                 "config": {"workload": workload_name(p, n, q),
                            "precision": "mixed+refine" if mixed else "fp64",
-                           "solver": (f"FP64 iterative refinement to rtol {args.rtol} around FP32 Jacobi-PCG "
-                                      f"(inner rtol {args.inner_rtol})") if mixed else
-                                     f"FP64 Jacobi-PCG to rtol {args.rtol}",
+                           "solver": (f"FP64 iterative refinement around FP32 Jacobi-PCG (inner rtol "
+                                      f"{args.inner_rtol}), outer rtol {head['rtol']:.3g}: the loosest of "
+                                      f"{args.rtol:g}/3^k whose solution is within {args.target_err:g} of the "
+                                      f"reference solution") if mixed else f"FP64 Jacobi-PCG to rtol {head['rtol']:.3g}",
+                           "accuracy_target": {"solution_rel_err": args.target_err, "reference": ref_info},
                            "cg_loop": args.cg_mode,
                            "l2": "inputs larger than L2 (D alone is %.2f GB)" % (E * 6 * q ** 3 * 8 / 1e9),
                            "parallelism": "independent replicas, one per GPU" if world > 1 else "single GPU"},
                 "iterations_per_step": head["iterations_per_step"], "roofline": head["roofline"],
-                "cpu_baseline": cpu, "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+                "solution_rel_err": head["solution_rel_err"],
+                "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
                 "clocks": head["clocks"]}
         if mixed:
             line["refine_stats"] = head["stats"]
@@ -429,7 +554,8 @@ def run_ours(args, rank, world, dist):
                           "coarsest degree 24) run in FP32; set-up (levels' D, diagonals, eigenvalue bounds) "
                           "inside every step",
                 "ms_per_step": m["ms_per_step"], "iterations_per_step": m["iterations_per_step"],
-                "gdofs_per_cg_iter": m["value"], "gpu_launches": m["gpu_launches"]}
+                "gdofs_per_cg_iter": m["value"], "gpu_launches": m["gpu_launches"], "rtol": m["rtol"],
+                "solution_rel_err": m["solution_rel_err"]}
             if "fp64" in results:
                 line["mg_pcg_fp32_vcycle"]["time_to_solution_speedup_vs_fp64"] = (
                     results["fp64"]["ms_per_step"] / m["ms_per_step"])
@@ -440,32 +566,41 @@ def run_ours(args, rank, world, dist):
                           f"falls by {args.delta} (reliable updates; direction and scalars kept)",
                 "ms_per_step": m["ms_per_step"], "iterations_per_step": m["iterations_per_step"],
                 "gdofs_per_cg_iter": m["value"], "gpu_launches": m["gpu_launches"],
-                "replacements": m["stats"]["outer_iterations"], "rel_residual": m["stats"]["rel_residual"]}
+                "replacements": m["stats"]["outer_iterations"], "rel_residual": m["stats"]["rel_residual"],
+                "rtol": m["rtol"], "solution_rel_err": m["solution_rel_err"]}
             if "fp64" in results:
                 line["mixed_reliable"]["time_to_solution_speedup_vs_fp64"] = (
                     results["fp64"]["ms_per_step"] / m["ms_per_step"])
         if mixed and "fp64" in results:
             f64 = results["fp64"]
-            line["fp64_plain"] = {k: f64[k] for k in ("value", "ms_per_step", "iterations_per_step", "roofline",
-                                                       "dfma_kernel", "e2e", "apply_gdofs", "gpu_launches",
-                                                       "clocks")}
+            line["fp64_plain"] = {k: f64.get(k) for k in ("value", "ms_per_step", "iterations_per_step", "roofline",
+                                                           "dfma_kernel", "e2e", "apply_gdofs", "gpu_launches",
+                                                           "clocks", "rtol", "solution_rel_err", "arithmetic")}
             line["time_to_solution_speedup_vs_fp64"] = f64["ms_per_step"] / head["ms_per_step"]
+            line["speedup_note"] = "both forms at solution error <= %g against the reference" % args.target_err
+        if second is not None:
+            line["bp3_p%d_n%d" % (args.p2, args.n2)] = second
+        for k, v in extras.items():
+            line[k] = v
         print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batch(args, rank, world, dist):
+def run_batch(args, rank, world, dist, steps=None, warmup=None, quiet=False):
     """512 independent problems (mass or diffusion with probability 1/2, p uniform in
     1..6, elements per direction uniform in 2..24, seeded perturbed cubes, random nodal
     right-hand sides with zero boundary rows for diffusion) solved together by FP64
     Jacobi-PCG to 1e-10 in one graph-driven batch.  One step = one batched solve
-    (diagonal + PCG); the batch set-up (maps, D) is timed separately."""
+    (diagonal + PCG); the batch set-up (maps, D) is timed separately.  With quiet=True the
+    line is returned (for the default run's extra key) instead of printed."""
     import torch
 
     import paper_2402_15940_b300 as F
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    steps = steps if steps is None else steps
+    warmup = warmup if warmup is None else warmup
     mix = FI.problem_mix(args.batch_count, seed=rank)
     probs = [{"n": m["n"], "p": m["p"], "form": m["form"],
               "vertices": FI.perturbed_cube_vertices(*m["n"], seed=m["mesh_seed"])} for m in mix]
@@ -490,7 +625,7 @@ def run_batch(args, rank, world, dist):
         _, st = bt.solve(b, x, rtol=args.rtol, maxit=args.maxit)
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     if dist is not None:
@@ -500,7 +635,7 @@ def run_batch(args, rank, world, dist):
     dofit, maxits = 0.0, []
     with ClockSampler(local) as clk:
         ev0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             st = step()
             dofit += st["dof_iterations"]
             maxits.append(int(st["max_iterations"]))
@@ -515,7 +650,7 @@ def run_batch(args, rank, world, dist):
         _, st = bt.solve_refined(b, x, rtol=args.rtol, inner_rtol=args.inner_rtol)
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step_refined()
     torch.cuda.synchronize()
     if dist is not None:
@@ -524,7 +659,7 @@ def run_batch(args, rank, world, dist):
     dofit32, maxin, outer = 0.0, [], []
     with ClockSampler(local) as clk32:
         ev0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             st = step_refined()
             dofit32 += st["dof_iterations"]
             maxin.append(int(st["max_inner_iterations"]))
@@ -539,7 +674,7 @@ def run_batch(args, rank, world, dist):
         _, st = bt.solve_reliable(b, x, rtol=args.rtol, delta=args.delta)
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step_reliable()
     torch.cuda.synchronize()
     if dist is not None:
@@ -548,7 +683,7 @@ def run_batch(args, rank, world, dist):
     dofitr, maxr, repl = 0.0, [], []
     with ClockSampler(local) as clkr:
         ev0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             st = step_reliable()
             dofitr += st["dof_iterations"]
             maxr.append(int(st["max_inner_iterations"]))
@@ -558,29 +693,31 @@ def run_batch(args, rank, world, dist):
     tr, workr = reduce_max_sum(ev0.elapsed_time(ev1) / 1e3, dofitr, dist, device="cuda")
     reliable = {"solver": "batched FP32 Jacobi-PCG recurrences with FP64 residual replacement each time they "
                           f"fall by {args.delta} (reliable updates), one CUDA-graph loop per segment",
-                "ms_per_step": 1e3 * tr / args.steps, "solves_per_s": args.batch_count * world * args.steps / tr,
+                "ms_per_step": 1e3 * tr / steps, "solves_per_s": args.batch_count * world * steps / tr,
                 "gdofs_per_fp32_iter": workr / tr / 1e9, "max_inner_iterations_per_step": maxr,
                 "replacements_per_step": repl, "time_to_solution_speedup_vs_fp64": t / tr,
                 "gpu_launches": F.launch_count() - l2, "clocks": clkr.summary()}
     refined = {"solver": "FP64 iterative refinement (per-problem FP64 residual and stop) around batched FP32 "
                          f"Jacobi-PCG corrections (inner rtol {args.inner_rtol}), one CUDA-graph loop per step",
-               "ms_per_step": 1e3 * t32 / args.steps, "solves_per_s": args.batch_count * world * args.steps / t32,
+               "ms_per_step": 1e3 * t32 / steps, "solves_per_s": args.batch_count * world * steps / t32,
                "gdofs_per_fp32_iter": work32 / t32 / 1e9, "max_inner_iterations_per_step": maxin,
                "outer_iterations_per_step": outer, "time_to_solution_speedup_vs_fp64": t / t32,
                "gpu_launches": F.launch_count() - l1, "clocks": clk32.summary()}
     if rank == 0:
         line = {"metric": "batched BP1/BP3 solves: GDOF/s per CG iter", "value": work / t / 1e9, "unit": UNIT,
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+                "n_gpus": world, "steps": steps, "warmup": warmup,
+                "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{args.batch_count} independent problems, form mass|diffusion (p=0.5), "
                                        "p~U{1..6}, n_d~U{2..24}, perturbed cubes, random nodal RHS, "
                                        "FP64 Jacobi-PCG to 1e-10, one CUDA-graph batch",
                            "total_dofs": bt.N, "groups": bt.groups},
-                "solves_per_s": args.batch_count * world * args.steps / t,
+                "solves_per_s": args.batch_count * world * steps / t,
                 "max_iterations_per_step": maxits, "setup_s": setup_s,
                 "gpu_launches": launches64, "clocks": clk.summary(), "mixed_refined": refined,
                 "mixed_reliable": reliable}
+        if quiet:
+            return line
         print(json.dumps(line), flush=True)
     return 0
 
@@ -664,7 +801,7 @@ def run_sweep(args, rank, world, dist):
     return 0
 
 
-def run_serve(args, rank, world, dist):
+def run_serve(args, rank, world, dist, rates=None, quiet=False):
     """Served solve stream: for each arrival rate, `--requests` requests (mass or
     diffusion, p uniform in 1..8, DOFs log-uniform in 1e3..5e6, FP64 or mixed with
     refinement to 1e-10, seeded perturbed cubes, sine RHS) arrive as a Poisson process
@@ -677,7 +814,7 @@ def run_serve(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     vf = lambda n, seed: FI.perturbed_cube_vertices(*n, seed=seed)  # noqa: E731
-    rates = [float(r) for r in args.rates.split(",")]
+    rates = [float(r) for r in args.rates.split(",")] if rates is None else rates
     per_rate = []
     l0 = launch_count()
     with ClockSampler(local) as clk:
@@ -702,6 +839,8 @@ def run_serve(args, rank, world, dist):
                                        "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
                            "tick_iters": args.tick_iters},
                 "per_rate": per_rate, "gpu_launches": launch_count() - l0, "clocks": clk.summary()}
+        if quiet:
+            return line
         print(json.dumps(line), flush=True)
     return 0
 
@@ -740,6 +879,16 @@ def main():
     ap.add_argument("--tick-iters", type=int, default=32)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--target-err", type=float, default=1e-10,
+                    help="solution error (relative l2, against the reference solve) every BP3 form is run to; "
+                         "0: stop at --rtol without a reference")
+    ap.add_argument("--ref-rtol", type=float, default=1e-13, help="relative residual of the reference solve")
+    ap.add_argument("--p2", type=int, default=6, help="second BP3 case: order (0 skips it)")
+    ap.add_argument("--n2", type=int, default=32, help="second BP3 case: elements per direction")
+    ap.add_argument("--steps2", type=int, default=5, help="second BP3 case: at most this many timed steps")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the short batch and serve runs of the default line")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrival rate of the default line's serve run")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

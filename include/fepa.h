@@ -37,7 +37,12 @@
  *   - All device work is enqueued on the op's stream (given at creation, may be 0 for
  *     the legacy default stream) and is asynchronous with respect to the host unless
  *     a call says otherwise.
- *   - Floating point is IEEE binary64 unless a call says otherwise.
+ *   - Values in memory are IEEE binary64 unless a call says otherwise (the FP32 calls take
+ *     binary32).  The arithmetic of the "FP64" action (fepa_op_apply and the FP64 solves)
+ *     is chosen per op by fepa_op_set_f64_variant: native binary64, or double-float pairs
+ *     on the FP32 pipe (about 48 significant bits, relative error far below the 1e-12 of the
+ *     action's contract) where the op's data lies in that arithmetic's exponent range
+ *     (checked by the library; outside it the native kernel is used).
  */
 #ifndef FEPA_H
 #define FEPA_H
@@ -57,6 +62,8 @@ extern "C" {
 #define FEPA_ERR_NOCONV (-5)      /* CG reached maxit before the tolerance */
 #define FEPA_ERR_TIMEOUT (-6)     /* a kernel's bounded wait for staged data expired (no fault) */
 #define FEPA_ERR_UNSUPPORTED (-7) /* order / quadrature outside the compiled range */
+#define FEPA_ERR_NONFINITE (-8)   /* a solve's residual norm became NaN or infinite (non-finite b, x or
+                                     operator data); the loop stops at once instead of running to maxit */
 
 #define FEPA_BUSY 1               /* fepa_solver_poll: work still in flight */
 
@@ -79,7 +86,7 @@ typedef struct fepa_op fepa_op; /* opaque: mesh + H1 space + form + stored D */
 
 typedef struct fepa_cg_stats {
   int32_t iterations;     /* operator applications inside the loop */
-  int32_t status;         /* FEPA_OK or FEPA_ERR_NOCONV */
+  int32_t status;         /* FEPA_OK, FEPA_ERR_NOCONV or FEPA_ERR_NONFINITE */
   double rel_residual;    /* ||r_k||_2 / ||b||_2 at exit */
   double precond_norm;    /* sqrt(z_k . r_k) at exit (preconditioned residual norm) */
   double b_norm;          /* ||b||_2 */
@@ -88,7 +95,7 @@ typedef struct fepa_cg_stats {
 typedef struct fepa_refine_stats {
   int32_t outer_iterations;  /* FP64 residual corrections applied */
   int32_t inner_iterations;  /* FP32 CG iterations, summed over the corrections */
-  int32_t status;            /* FEPA_OK or FEPA_ERR_NOCONV */
+  int32_t status;            /* FEPA_OK, FEPA_ERR_NOCONV or FEPA_ERR_NONFINITE */
   double rel_residual;       /* ||b - A x||_2 / ||b||_2 with the FP64 operator, at exit */
   double b_norm;             /* ||b||_2 */
 } fepa_refine_stats;
@@ -186,8 +193,10 @@ int fepa_op_apply(fepa_op* op, const double* x, double* y);
  * The first call builds an FP32 copy of D (4 bytes per stored value, each component
  * padded to a multiple of 4 values).  The kernel stages each block's D with one TMA
  * bulk copy; if that copy's bounded wait expires the block skips its work and sets an
- * error word that the next blocking call on this op (fepa_solve_refined) reports as
- * FEPA_ERR_TIMEOUT.
+ * error word that the next blocking call on this op (fepa_solve_refined, fepa_solve_reliable,
+ * fepa_solver_poll at the end of a refined solve, fepa_mg_solve with an FP32 V-cycle) reports
+ * as FEPA_ERR_TIMEOUT.  The word is cleared when it is reported, so each expiry is reported
+ * once.
  */
 int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
 
@@ -197,7 +206,9 @@ int fepa_op_apply_f32(fepa_op* op, const float* x, float* y);
  * at each essential DOF: the fused (d, A d) of the FP32 CG (fepa_op_set_fused_dot), the
  * dot product of Sec. 2.3 formed inside the operator kernel.  Where the op's FP32 variant
  * has no such build (p < 3, variant 3) the product is a separate pass over x and y.
- * Enqueued on the op's stream; *xax is valid when that work completes.
+ * Enqueued on the op's stream; *xax is valid when that work completes.  Calls on one op
+ * share its (x, A x) accumulators: they must not overlap on the GPU (for instance two calls
+ * on different streams after fepa_op_set_stream while the first is still running).
  */
 int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax);
 
@@ -524,6 +535,16 @@ int fepa_mg_solve(fepa_mg* mg, const double* b, double* x, double rtol, int32_t 
 #define FEPA_NOALLOC_MAX_DOFS 131072
 int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, double rtol, int32_t maxit, int32_t precond,
                           fepa_cg_stats* stats);
+
+/*
+ * Testing only.  Poll limit of the FIRST bounded wait in the FP32 action kernels that stage
+ * D by TMA (variants 0 and 3): the wait of each block for its D copy.  iterations < 0 restores
+ * the default (2^22 polls).  With 0 the wait gives up at once: the block skips its work, sets
+ * the op's error word and still waits, with the full limit, for its copy in flight before it
+ * exits, so the timeout path (FEPA_ERR_TIMEOUT) runs without a fault or a hang.  Applies
+ * process-wide to kernels launched on the current device after the call; synchronous.
+ */
+int fepa_test_set_first_wait_limit(int32_t iterations);
 
 #ifdef __cplusplus
 }

@@ -87,8 +87,8 @@ bcg_init(ChunkTable t, const double* __restrict__ b, double* __restrict__ r, dou
       q.maxit = maxit;
       q.alpha = q.beta = 0.0;
       q.converged = (s[1] <= q.tol2) ? 1 : 0;
-      pdone[j] = q.converged;
-      return !q.converged;
+      pdone[j] = q.converged || !isfinite(s[1]) || !isfinite(s[2]);  // NaN/inf: stop at once
+      return !pdone[j];
     });
     if (threadIdx.x == 0) {
       gs->active = active;
@@ -150,7 +150,7 @@ bcg_update(ChunkTable t, double* __restrict__ x, double* __restrict__ r, const d
       if (s[1] <= q.tol2) {
         q.converged = 1;
         stop = 1;
-      } else if (q.iter >= q.maxit) {
+      } else if (q.iter >= q.maxit || !isfinite(q.rr)) {
         stop = 1;
       }
       q.beta = s[0] / q.rho;
@@ -334,7 +334,7 @@ bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const f
       if (s[1] <= q.tol2) {
         q.converged = 1;
         stop = 1;
-      } else if (q.iter >= q.maxit) {
+      } else if (q.iter >= q.maxit || !isfinite(q.rr)) {
         stop = 1;
       }
       q.beta = s[0] / q.rho;

@@ -119,7 +119,7 @@ cg_init(int64_t N, const double* __restrict__ b, double* __restrict__ r, double*
       st->iter = 0;
       st->maxit = maxit;
       st->converged = (tot[1] <= st->tol2) ? 1 : 0;
-      st->done = st->converged;
+      st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->alpha = st->beta = 0.0;
       st->tick_limit = 0x7fffffff;
       st->ticket = 0;
@@ -173,7 +173,7 @@ cg_update(int64_t N, double* __restrict__ x, double* __restrict__ r, const doubl
       if (tot[1] <= st->tol2) {
         st->converged = 1;
         st->done = 1;
-      } else if (st->iter >= st->maxit) {
+      } else if (st->iter >= st->maxit || !isfinite(st->rr)) {
         st->done = 1;
       }
       st->beta = tot[0] / st->rho;
@@ -272,7 +272,7 @@ cg32_init(int64_t N, const float* __restrict__ b, float* __restrict__ x, float* 
       st->iter = 0;
       st->maxit = maxit;
       st->converged = (tot[1] <= st->tol2) ? 1 : 0;
-      st->done = st->converged;
+      st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->alpha = st->beta = 0.0;
       st->tick_limit = 0x7fffffff;
       st->ticket = 0;
@@ -360,7 +360,7 @@ cg32_update(int64_t N, float* __restrict__ r, const float* __restrict__ h, const
       if (tot[1] <= st->tol2) {
         st->converged = 1;
         st->done = 1;
-      } else if (st->iter >= st->maxit) {
+      } else if (st->iter >= st->maxit || !isfinite(st->rr)) {
         st->done = 1;
       }
       st->beta = tot[0] / st->rho;

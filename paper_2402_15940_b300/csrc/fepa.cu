@@ -268,7 +268,8 @@ struct CgLoop {
   cudaGraphExec_t exec = nullptr;
   int graph_key = -1;  // preconditioner and kernel variants the cached graph was captured with
   double* dh_slots = nullptr;  // FP32 loop: (d, h) accumulated by the fused action
-  int kernels_per_iter = 4;    // launches per iteration of the captured body
+  int kernels_per_iter = 4;    // launches per iteration of the body last built (stream mode)
+  int graph_kernels_per_iter = 4;  // launches per iteration of the cached graph's body
 };
 
 }  // namespace
@@ -754,12 +755,16 @@ int compute_geometry(fepa_op* op) {
   return FEPA_OK;
 }
 
-// FEPA_ERR_TIMEOUT if a kernel of this op gave up a bounded wait (checked at sync points)
+// FEPA_ERR_TIMEOUT if a kernel of this op gave up a bounded wait since the last check
+// (checked at sync points); the word is cleared once read, so each expiry is reported once
 int check_err(fepa_op* op) {
   int h = 0;
   CUDA_TRY(cudaMemcpyAsync(&h, op->err, sizeof(int), cudaMemcpyDeviceToHost, op->stream));
   CUDA_TRY(cudaStreamSynchronize(op->stream));
-  if (h) return fail(FEPA_ERR_TIMEOUT, "a kernel's bounded wait for its staged data expired");
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), op->stream));
+    return fail(FEPA_ERR_TIMEOUT, "a kernel's bounded wait for its staged data expired");
+  }
   return FEPA_OK;
 }
 
@@ -828,6 +833,7 @@ int build_while_graph(fepa_op* op, CgLoop& L, int precond, Body body) {
   if (ce != cudaSuccess) return fail(FEPA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
   CUDA_TRY(cudaGraphInstantiate(&L.exec, L.graph, 0));
   L.graph_key = key;
+  L.graph_kernels_per_iter = L.kernels_per_iter;  // set by the body just captured
   return FEPA_OK;
 }
 
@@ -841,7 +847,7 @@ int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
     CUDA_TRY(cudaGraphLaunch(L.exec, s));
     CUDA_TRY(cudaMemcpyAsync(out, L.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    g_launches.fetch_add(L.kernels_per_iter * (int64_t)(out->iter > 0 ? out->iter : 1));
+    g_launches.fetch_add(L.graph_kernels_per_iter * (int64_t)(out->iter > 0 ? out->iter : 1));
     return FEPA_OK;
   }
   for (;;) {
@@ -853,10 +859,18 @@ int run_loop(fepa_op* op, CgLoop& L, int precond, Body body, CgState* out) {
   }
 }
 
+// the loop stopped on a NaN or infinite ||r||^2 or ||b||^2 (non-finite input or breakdown)
+bool nonfinite(const CgState& h) { return !std::isfinite(h.rr) || !std::isfinite(h.bb); }
+
+int fail_nonfinite(const char* what) {
+  return fail(FEPA_ERR_NONFINITE, "%s: a residual norm became NaN or infinite (non-finite b, x or operator data)",
+              what);
+}
+
 void fill_stats(const CgState& h, fepa_cg_stats* stats) {
   if (!stats) return;
   stats->iterations = h.iter;
-  stats->status = h.converged ? FEPA_OK : FEPA_ERR_NOCONV;
+  stats->status = h.converged ? FEPA_OK : (nonfinite(h) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
   stats->b_norm = sqrt(h.bb);
   stats->rel_residual = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
   stats->precond_norm = sqrt(fabs(h.rho));
@@ -892,6 +906,7 @@ int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int 
   CUDA_TRY(cudaStreamSynchronize(s));
   const CgState h = *op->st_host;
   fill_stats(h, stats);
+  if (nonfinite(h)) return fail_nonfinite("CG");
   if (!h.converged && rtol > 0.0)
     return fail(FEPA_ERR_NOCONV, "CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)", rtol, h.iter,
                 h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0);
@@ -943,7 +958,8 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     href = *op->st_host;
     bnorm = sqrt(href.bb);
     rel = href.bb > 0 ? sqrt(href.rr / href.bb) : 0.0;
-    if (rel <= rtol || outer >= max_outer) break;
+    if (!std::isfinite(href.rr) || !std::isfinite(href.bb)) rel = NAN;
+    if (rel <= rtol || outer >= max_outer || std::isnan(rel)) break;
     // FP32 correction: A e = r with relative tolerance inner_rtol (relaxed on the last step)
     const double tol = inner_tol(inner_rtol, rtol, rel);
     cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
@@ -964,8 +980,9 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     stats->inner_iterations = inner_total;
     stats->rel_residual = rel;
     stats->b_norm = bnorm;
-    stats->status = rel <= rtol ? FEPA_OK : FEPA_ERR_NOCONV;
+    stats->status = rel <= rtol ? FEPA_OK : (std::isnan(rel) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
   }
+  if (std::isnan(rel)) return fail_nonfinite("refinement");
   if (rel > rtol)
     return fail(FEPA_ERR_NOCONV, "refinement did not reach rtol %.3g in %d outer steps (rel. residual %.3e)", rtol,
                 outer, rel);
@@ -1013,6 +1030,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
     CUDA_TRY(cudaStreamSynchronize(s));
     *bb = op->st_host->bb;
     *rel = op->st_host->bb > 0 ? sqrt(op->st_host->rr / op->st_host->bb) : 0.0;
+    if (nonfinite(*op->st_host)) *rel = NAN;
     return FEPA_OK;
   };
   double rel = 0.0, bb = 0.0;
@@ -1020,7 +1038,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
   const double rr0 = rel * rel * bb;
   const double floor2 = 0.25 * rtol * rtol * bb;  // a segment need not go below half the target
   int replacements = 0, iters = 0;
-  if (rel > rtol) {
+  if (rel > rtol) {  // (false for NaN: nothing to iterate on)
     const double first = rr0 > 0.0 && floor2 / rr0 > delta * delta ? floor2 / rr0 : delta * delta;
     cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
                                                     (float*)L.h, invd, L.st, first, maxit, L.partials);
@@ -1034,7 +1052,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
       refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
       LAUNCH_CHECK();
       TRY(residual(&rel, &bb));
-      if (rel <= rtol || iters >= maxit) break;
+      if (rel <= rtol || iters >= maxit || std::isnan(rel)) break;
       cg32_replace<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, invd, L.st,
                                                          delta * delta, floor2, L.partials);
       LAUNCH_CHECK();
@@ -1050,8 +1068,9 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
     stats->inner_iterations = iters;
     stats->rel_residual = rel;
     stats->b_norm = sqrt(bb);
-    stats->status = rel <= rtol ? FEPA_OK : FEPA_ERR_NOCONV;
+    stats->status = rel <= rtol ? FEPA_OK : (std::isnan(rel) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
   }
+  if (std::isnan(rel)) return fail_nonfinite("reliable-update CG");
   if (rel > rtol)
     return fail(FEPA_ERR_NOCONV, "reliable-update CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)",
                 rtol, iters, rel);
@@ -1199,6 +1218,13 @@ int32_t fepa_op_dcomps(const fepa_op* op) { return op ? (op->form == FEPA_DIFFUS
 int fepa_op_set_stream(fepa_op* op, void* stream) {
   if (!op) return fail(FEPA_ERR_ARG, "op is null");
   op->stream = (cudaStream_t)stream;
+  return FEPA_OK;
+}
+
+int fepa_test_set_first_wait_limit(int32_t iterations) {
+  const int v = iterations < 0 ? WAIT_LIMIT : iterations;
+  CUDA_TRY(cudaMemcpyToSymbol(c_first_wait_limit, &v, sizeof(int)));
+  CUDA_TRY(cudaDeviceSynchronize());
   return FEPA_OK;
 }
 
@@ -1533,11 +1559,12 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
   }
   if (stats) {
     stats->iterations = hs.iter;
-    stats->status = hs.converged ? FEPA_OK : FEPA_ERR_NOCONV;
+    stats->status = hs.converged ? FEPA_OK : (nonfinite(hs) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
     stats->b_norm = sqrt(hs.bb);
     stats->rel_residual = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
     stats->precond_norm = sqrt(fabs(hs.rho));
   }
+  if (nonfinite(hs)) return fail_nonfinite("CG");
   if (!hs.converged && rtol > 0.0)
     return fail(FEPA_ERR_NOCONV, "CG did not reach rtol %.3g in %d iterations (rel. residual %.3e)", rtol, hs.iter,
                 hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0);

@@ -410,7 +410,7 @@ pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, doubl
       st->iter = 0;
       st->maxit = maxit;
       st->converged = tot[0] <= st->tol2 ? 1 : 0;
-      st->done = st->converged;
+      st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->rho = 0.0;
       st->alpha = st->beta = 0.0;
       st->tick_limit = 0x7fffffff;
@@ -477,7 +477,7 @@ pcg_update(int64_t N, double* __restrict__ x, double* __restrict__ r, const doub
       if (tot[0] <= st->tol2) {
         st->converged = 1;
         st->done = 1;
-      } else if (st->iter >= st->maxit) {
+      } else if (st->iter >= st->maxit || !isfinite(st->rr)) {
         st->done = 1;
       }
       st->ticket = 0;

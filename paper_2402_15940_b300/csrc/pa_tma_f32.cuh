@@ -197,9 +197,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+constexpr int WAIT_LIMIT = 1 << 22;  // try_wait polls before a bounded wait gives up
+
+// Poll limit of the first wait of a block for its staged D (fepa_test_set_first_wait_limit
+// lowers it to make the timeout path run; the drain waits after a timeout keep WAIT_LIMIT).
+__constant__ int c_first_wait_limit = WAIT_LIMIT;
+
 // Bounded wait for the given phase parity of the barrier: false if it did not complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity = 0) {
-  for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity = 0, int limit = WAIT_LIMIT) {
+  for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -627,7 +633,7 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   }
   if (STAGE_D) {
     // D must have landed before stage 3; every thread observes the barrier (bounded)
-    const bool ok = mbar_wait_bounded(mbar);
+    const bool ok = mbar_wait_bounded(mbar, 0, c_first_wait_limit);
     if (__syncthreads_or(!ok)) {
       if (tid == 0 && el == 0) {
         atomicOr(err, 1);
@@ -841,7 +847,7 @@ pa_apply_f32_pipe(int E, const int* __restrict__ gmap, const float* __restrict__
     }
     if (has_next) gather(gn, nxt, r);
     const uint32_t pc = cur ? ph1 : ph0, pn = cur ? ph0 : ph1;
-    const bool ok = mbar_wait_bounded(&mbar[cur], pc);
+    const bool ok = mbar_wait_bounded(&mbar[cur], pc, c_first_wait_limit);
     if (cur) ph1 ^= 1u; else ph0 ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (flat == 0) {

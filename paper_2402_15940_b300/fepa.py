@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfepa.so")
 
 OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_MESH, ERR_NOCONV, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+ERR_NONFINITE = -8
 MASS, DIFFUSION = 0, 1
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
 MAX_ORDER = 8
@@ -141,6 +142,7 @@ SIGNATURES = [
     ("fepa_mg_vcycle", ctypes.c_int, [_P, _P, _P]),
     ("fepa_mg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_test_set_first_wait_limit", ctypes.c_int, [_I32]),
 ]
 NOALLOC_MAX_DOFS = 131072
 
@@ -177,6 +179,11 @@ def _check(rc: int):
 
 def launch_count() -> int:
     return int(load_library().fepa_launch_count())
+
+
+def test_set_first_wait_limit(iterations: int):
+    """Testing only: poll limit of the FP32 TMA kernels' first bounded wait (-1: default)."""
+    _check(load_library().fepa_test_set_first_wait_limit(int(iterations)))
 
 
 def _torch():

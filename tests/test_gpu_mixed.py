@@ -340,3 +340,27 @@ def test_reliable_noconv_and_arguments():
     for bad in (0.0, 1.0, -0.5):
         with pytest.raises(Exception):
             op.solve_reliable(b, delta=bad)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_fused_dot_on_a_smooth_vector(variant):
+    """(x, A x) from the fused FP32 action on a smooth, low-energy x (the sine interpolant,
+    zero on the boundary): per element the terms x_l (A_e x)_l nearly cancel, the case where
+    summing them in FP32 loses the most.  Compared with the FP64 oracle's x . A x and with the
+    separate pass (the persistent variant has no fused build, so there (x, A x) is a
+    double-float dot of x and the FP32 y)."""
+    shape, p = (6, 5, 4), 4
+    op, mesh = make(shape, p, "diffusion", seed=52)
+    prob = O.Problem(mesh, p, None, O.DIFFUSION)
+    op.set_essential(prob.ess.astype(np.int32))
+    xd = O.sine_solution(O.node_coords(mesh, p)).astype(np.float32).astype(np.float64)
+    x32 = torch.from_numpy(xd.astype(np.float32)).cuda()
+    exact = xd @ prob.apply(xd, constrained=True)
+    op.set_f32_variant(variant)
+    _, fused = op.apply_f32_dot(x32)
+    op.set_f32_variant(3)
+    _, sep = op.apply_f32_dot(x32)
+    e_fused = abs(float(fused.item()) - exact) / exact
+    e_sep = abs(float(sep.item()) - exact) / exact
+    print(f"smooth x: (x, A x) rel. error fused {e_fused:.2e}, separate pass {e_sep:.2e}")
+    assert e_fused <= 1e-5 and e_sep <= 1e-5

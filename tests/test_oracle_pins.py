@@ -237,19 +237,6 @@ def test_cg_matches_dense_solve(form):
     assert np.linalg.norm(x - xd) <= 1e-11 * np.linalg.norm(xd)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
-def test_l2_convergence_rate(p):
-    errs = []
-    ns = (2, 4, 8) if p < 3 else (2, 4, 6)
-    for n in ns:
-        mesh = perturbed(n, n, n, seed=31)
-        prob = O.Problem(mesh, p, None, O.DIFFUSION)
-        x, it, res = prob.solve(prob.sine_rhs(), rtol=1e-12)
-        errs.append(O.l2_error(mesh, p, x, O.sine_solution))
-    rate = math.log(errs[-2] / errs[-1]) / math.log(ns[-1] / ns[-2])
-    assert rate > p + 1 - 0.35, (errs, rate)
-
-
 def test_planted_transpose_mistake_is_caught(monkeypatch):
     # Using J^{-T} J^{-1} in place of J^{-1} J^{-T} (a transposed Jacobian) must fail the
     # linear patch test on a perturbed mesh: the pins are sensitive to it.
@@ -334,3 +321,83 @@ def test_pmg_vcycle_two_levels_reduces_error_and_is_symmetric():
     ev = np.sort(np.linalg.eigvals(Mi @ Ai).real)
     evj = np.sort(np.linalg.eigvals(Ai / np.diag(Ai)[:, None]).real)
     assert ev[0] > 0 and ev[-1] / ev[0] < 0.1 * evj[-1] / evj[0]
+
+
+# ---------------------------------------------------------------- L2 norm of the error
+
+def _l2_pins(p, mesh):
+    """The values l2_error must give on a perturbed unit cube, each fixed in closed form:
+    with u_h = 0 it is ||u||, so ||1|| = 1 (|Omega| = 1), ||x|| = 1/sqrt(3) and
+    ||sin(pi x) sin(pi y) sin(pi z)|| = (1/2)^(3/2) (each factor integrates sin^2 to 1/2);
+    the nodal interpolant of a polynomial of total degree <= p in physical coordinates is in
+    the space (its pull-back by a trilinear map is in Q_p), so its error is zero; and the
+    interpolant of x against u = 0 gives ||x|| again.  Returns the deviations."""
+    N = O.num_dofs(mesh, p)
+    zero = np.zeros(N)
+    xyz = O.node_coords(mesh, p)
+    poly = lambda X: (0.3 + X[..., 0] - 2.0 * X[..., 1] + 0.5 * X[..., 2]) ** p  # noqa: E731
+    nil = lambda X: np.zeros(X.shape[:-1])  # noqa: E731
+    return {
+        "one": abs(O.l2_error(mesh, p, zero, lambda X: np.ones(X.shape[:-1])) - 1.0),
+        "x": abs(O.l2_error(mesh, p, zero, lambda X: X[..., 0]) - 1.0 / math.sqrt(3.0)),
+        "sine": abs(O.l2_error(mesh, p, zero, O.sine_solution) - 0.5 ** 1.5),
+        "interpolant": O.l2_error(mesh, p, poly(xyz), poly),
+        "interp_x": abs(O.l2_error(mesh, p, xyz[:, 0], nil) - 1.0 / math.sqrt(3.0)),
+    }
+
+
+# the sine is integrated by the p+5 rule, not exactly: 5e-12 holds its error for p = 1..3 on
+# this mesh (5.8e-13 at p = 1) while the operator's own p+2 rule misses by 1e-10 .. 1e-6
+_L2_TOL = {"one": 1e-13, "x": 1e-13, "sine": 5e-12, "interpolant": 1e-13, "interp_x": 1e-13}
+
+
+def _l2_mesh():
+    return perturbed(2, 3, 2, seed=37)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_error_closed_forms(p):
+    dev = _l2_pins(p, _l2_mesh())
+    for k, v in dev.items():
+        assert v <= _L2_TOL[k], (k, v)
+
+
+def _some_l2_pin_fails():
+    return any(any(v > _L2_TOL[k] for k, v in _l2_pins(p, _l2_mesh()).items()) for p in (1, 2))
+
+
+def test_l2_error_planted_missing_sqrt_is_caught(monkeypatch):
+    monkeypatch.setattr(O.fem_oracle, "math", type("M", (), {"sqrt": staticmethod(lambda v: v)}))
+    assert _some_l2_pin_fails()
+
+
+def test_l2_error_planted_missing_detj_is_caught(monkeypatch):
+    orig = O.fem_oracle.qp_factors
+
+    def weights_only(X, R, form):
+        F = orig(X, R, form)
+        return np.broadcast_to(R.w[None, :], F.shape).copy() if form == O.MASS else F
+
+    monkeypatch.setattr(O.fem_oracle, "qp_factors", weights_only)
+    assert _some_l2_pin_fails()
+
+
+def test_l2_error_planted_operator_rule_is_caught(monkeypatch):
+    orig = O.fem_oracle.rule
+    monkeypatch.setattr(O.fem_oracle, "rule", lambda p, q: orig(p, p + 2))
+    assert _some_l2_pin_fails()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_convergence_rate_two_sided(p):
+    # the discrete solution's L2 error falls at rate p+1, neither slower nor faster (a
+    # missing square root would double the observed rate)
+    errs = []
+    ns = (2, 4, 8) if p < 3 else (2, 4, 6)
+    for n in ns:
+        mesh = perturbed(n, n, n, seed=31)
+        prob = O.Problem(mesh, p, None, O.DIFFUSION)
+        x, it, res = prob.solve(prob.sine_rhs(), rtol=1e-12)
+        errs.append(O.l2_error(mesh, p, x, O.sine_solution))
+    rate = math.log(errs[-2] / errs[-1]) / math.log(ns[-1] / ns[-2])
+    assert p + 1 - 0.35 < rate < p + 1 + 0.35, (errs, rate)
