@@ -44,10 +44,10 @@ METRIC = "BP3 GDOF/s per CG iter (FP64 vs mixed+refine)"
 UNIT = "GDOF/s"
 
 
-def workload_name(p, n, q):
+def workload_name(p, n, q, stop="solution within 1e-10 (relative l2) of a reference solve"):
     N = (p * n + 1) ** 3
     return (f"BP3 diffusion, p={p}, q={q}, {n}^3 perturbed trilinear hexes (+-0.1h), N={N} DOFs, "
-            f"sine manufactured RHS, homogeneous Dirichlet, Jacobi PCG to 1e-10")
+            f"sine manufactured RHS, homogeneous Dirichlet, {stop}")
 
 
 def flops_per_elem(n, q, form):
@@ -204,7 +204,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(p, n_s, p + 2) + f" (CPU sample of the {args.n}^3 workload)",
+            "config": {"workload": workload_name(p, n_s, p + 2, "Jacobi PCG to a 1e-10 residual")
+                                   + f" (CPU sample of the {args.n}^3 workload)",
                        "full_workload": workload_name(p, args.n, p + 2), "sample": sample},
             "iterations": its,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample,
@@ -299,18 +300,22 @@ def bp3_case(args, p, n, rank, world, dist, steps, forms, with_e2e, with_rooflin
         return float(torch.linalg.norm(x - xref) / torch.linalg.norm(xref))
 
     def calibrate(prec):
-        """Loosest outer tolerance (from --rtol down by factors of 3) whose solution error is
-        within --target-err; these solves also warm the form up."""
-        rt = args.rtol
+        """The loosest outer tolerance, of --rtol * 10^(k/2) for k = --rtol-search, ..., 1, 0, -1, ...,
+        whose solution is within --target-err of the reference (each form at the accuracy the
+        target asks for, no tighter); these solves also warm the form up."""
+        if xref is None:
+            step(prec, args.rtol)
+            return args.rtol, []
         tried = []
-        for _ in range(7):
+        k = args.rtol_search
+        while True:
+            rt = args.rtol * 10.0 ** (k / 2.0)
             step(prec, rt)
             e = sol_err()
             tried.append({"rtol": rt, "solution_rel_err": e})
-            if e is None or e <= args.target_err:
-                break
-            rt /= 3.0
-        return rt, tried
+            if e <= args.target_err or k <= -8:
+                return rt, tried
+            k -= 1
 
     def timed(prec):
         rtol, tried = calibrate(prec)
@@ -462,18 +467,18 @@ def cpu_model():
 
 def oracle_cpu_baseline(p, n_s):
     """The oracle as it stands on this host: once limited to one thread and once with its
-    libraries' default thread pools (all cores; numpy's BLAS parallelises the element
-    matrices, scipy's sparse products stay on one thread)."""
+    libraries' thread pools opened to every core (numpy's BLAS parallelises the element
+    matrices; scipy's sparse products stay on one thread)."""
     out = {}
     try:
         from threadpoolctl import threadpool_limits
     except Exception:
         threadpool_limits = None
-    for label, lim in (("single_thread", 1), ("all_cores", None)):
-        if threadpool_limits is not None and lim is not None:
+    for label, lim in (("single_thread", 1), ("all_cores", os.cpu_count() or 1)):
+        if threadpool_limits is not None:
             with threadpool_limits(limits=lim):
+                th = cpu_threads()
                 d, t, it = oracle_sample(p, n_s)
-                th = 1
         else:
             d, t, it = oracle_sample(p, n_s)
             th = cpu_threads()
@@ -519,7 +524,7 @@ def run_ours(args, rank, world, dist):
         cpu = {"value": allc["value"], "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
                "sample": f"oracle CSR assembly + Jacobi PCG to 1e-10 on {args.oracle_n}^3 elements, p={p}, "
                          f"N={(p * args.oracle_n + 1) ** 3}, {allc['iterations']} iterations, "
-                         f"{allc['seconds']:.1f} s with the libraries' default thread pools",
+                         f"{allc['seconds']:.1f} s with the libraries' thread pools opened to all cores",
                "single_thread": cb["single_thread"], "host_nproc": os.cpu_count(), "host_cpu": cpu_model()}
 
     if rank == 0:
@@ -535,7 +540,7 @@ def run_ours(args, rank, world, dist):
                            "precision": "mixed+refine" if mixed else "fp64",
                            "solver": (f"FP64 iterative refinement around FP32 Jacobi-PCG (inner rtol "
                                       f"{args.inner_rtol}), outer rtol {head['rtol']:.3g}: the loosest of "
-                                      f"{args.rtol:g}/3^k whose solution is within {args.target_err:g} of the "
+                                      f"{args.rtol:g}*10^(k/2) whose solution is within {args.target_err:g} of the "
                                       f"reference solution") if mixed else f"FP64 Jacobi-PCG to rtol {head['rtol']:.3g}",
                            "accuracy_target": {"solution_rel_err": args.target_err, "reference": ref_info},
                            "cg_loop": args.cg_mode,
@@ -883,6 +888,8 @@ def main():
                     help="solution error (relative l2, against the reference solve) every BP3 form is run to; "
                          "0: stop at --rtol without a reference")
     ap.add_argument("--ref-rtol", type=float, default=1e-13, help="relative residual of the reference solve")
+    ap.add_argument("--rtol-search", type=int, default=6,
+                    help="the tolerance search starts at --rtol * 10^(k/2) with this k and tightens by sqrt(10)")
     ap.add_argument("--p2", type=int, default=6, help="second BP3 case: order (0 skips it)")
     ap.add_argument("--n2", type=int, default=32, help="second BP3 case: elements per direction")
     ap.add_argument("--steps2", type=int, default=5, help="second BP3 case: at most this many timed steps")

@@ -4,7 +4,11 @@ This module holds no finite-element arithmetic: it only draws numbers.  Both the
 library side and the oracle receive the arrays produced here and build their own
 meshes, numberings and operators from them.
 
-Mesh: the unit cube split into nx*ny*nz hexahedra.  Vertices sit on a structured
+Meshes: the unit cube split into nx*ny*nz hexahedra (structured vertex grid, or the same
+mesh as vertices + element connectivity with its structure hidden), and an unstructured
+hexahedral mesh of the unit cube (tiles of five quadrilaterals, extruded).
+
+Structured mesh: the unit cube split into nx*ny*nz hexahedra.  Vertices sit on a structured
 (nx+1)x(ny+1)x(nz+1) grid, numbered lexicographically with x fastest.  Each vertex
 is moved by a uniform random offset in [-amp*h_d, amp*h_d] along direction d
 (h_d = 1/n_d), except along directions normal to a boundary plane the vertex lies
@@ -18,6 +22,9 @@ import numpy as np
 
 __all__ = [
     "perturbed_cube_vertices",
+    "grid_connectivity",
+    "scrambled_hex_mesh",
+    "tiled_unstructured_cube",
     "uniform_vector",
     "problem_mix",
     "serve_requests",
@@ -40,6 +47,109 @@ def perturbed_cube_vertices(nx: int, ny: int, nz: int, seed: int = 0, amp: float
     xyz = xyz + np.where(interior, delta, 0.0)
     # boundary coordinates are set exactly (0 or 1), interior ones carry the offset
     return np.ascontiguousarray(xyz, dtype=np.float64)
+
+
+def grid_connectivity(nx: int, ny: int, nz: int) -> np.ndarray:
+    """(nx*ny*nz, 8) int32 vertex ids of the structured grid's elements, element
+    ex + nx*(ey + ny*ez), corner (i, j, k) at column i + 2j + 4k (vertex ids as in
+    perturbed_cube_vertices)."""
+    ez, ey, ex = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ex, ey, ez = ex.ravel(), ey.ravel(), ez.ravel()
+    out = np.empty((nx * ny * nz, 8), dtype=np.int32)
+    for c in range(8):
+        i, j, k = c & 1, (c >> 1) & 1, (c >> 2) & 1
+        out[:, c] = (ex + i) + (nx + 1) * ((ey + j) + (ny + 1) * (ez + k))
+    return out
+
+
+def _cube_rotations() -> list:
+    """The 24 rotations of the cube as permutations of its corners: rot[c'] = c means the
+    corner at position c' after the rotation is the one that was at c."""
+    import itertools
+    rots = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=int)
+            for r in range(3):
+                R[r, perm[r]] = signs[r]
+            if round(np.linalg.det(R)) != 1:
+                continue
+            table = []
+            for cn in range(8):   # new corner cn at centred position s' = R s
+                sp = np.array([2 * ((cn >> d) & 1) - 1 for d in range(3)])
+                so = R.T @ sp
+                table.append(int(sum(((so[d] + 1) // 2) << d for d in range(3))))
+            rots.append(table)
+    return rots
+
+
+def scrambled_hex_mesh(nx: int, ny: int, nz: int, seed: int = 0, amp: float = 0.1):
+    """The perturbed cube mesh of perturbed_cube_vertices as (vertices, conn) with its
+    structure hidden: vertex ids randomly permuted, elements in random order, and each
+    element's corners listed in one of the 24 rotated tensor-product orders (orientation
+    kept, so det J stays positive)."""
+    verts = perturbed_cube_vertices(nx, ny, nz, seed=seed, amp=amp)
+    conn = grid_connectivity(nx, ny, nz)
+    rng = np.random.default_rng(seed + 7919)
+    vperm = rng.permutation(len(verts))          # old id -> new id
+    new_verts = np.empty_like(verts)
+    new_verts[vperm] = verts
+    conn = vperm[conn]
+    conn = conn[rng.permutation(len(conn))]
+    rots = _cube_rotations()
+    pick = rng.integers(0, len(rots), size=len(conn))
+    out = np.empty_like(conn)
+    for e in range(len(conn)):
+        out[e] = conn[e][rots[pick[e]]]
+    return np.ascontiguousarray(new_verts), np.ascontiguousarray(out.astype(np.int32))
+
+
+def tiled_unstructured_cube(m: int, nz: int, seed: int = 0, inner: float = 0.3, jitter: float = 0.05,
+                            scramble: bool = True):
+    """An unstructured hexahedral mesh of the unit cube: the unit square is cut into m x m
+    tiles, each tile into 5 quadrilaterals (an inner square with corners at `inner` and
+    1 - `inner` of the tile, jittered by +-jitter of the tile size, and the 4 trapezoids
+    between it and the tile's sides), and that 2D mesh is extruded through nz layers.  The
+    inner corners have 3 quadrilaterals around them (edges of 3 hexahedra), which a
+    structured grid never has.  With scramble, vertex ids, element order and each element's
+    corner order are randomised as in scrambled_hex_mesh.  Returns (vertices, conn)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / m
+    pts = [(i * h, j * h) for j in range(m + 1) for i in range(m + 1)]   # tile corners
+    quads = []
+    for ty in range(m):
+        for tx in range(m):
+            o = [tx + (m + 1) * ty, tx + 1 + (m + 1) * ty, tx + 1 + (m + 1) * (ty + 1), tx + (m + 1) * (ty + 1)]
+            base = len(pts)
+            for (a, b) in ((inner, inner), (1 - inner, inner), (1 - inner, 1 - inner), (inner, 1 - inner)):
+                da, db = rng.uniform(-jitter, jitter, size=2)
+                pts.append(((tx + a + da) * h, (ty + b + db) * h))
+            i0, i1, i2, i3 = base, base + 1, base + 2, base + 3
+            # counter-clockwise quadrilaterals
+            quads += [[i0, i1, i2, i3], [o[0], o[1], i1, i0], [o[1], o[2], i2, i1], [o[2], o[3], i3, i2],
+                      [o[3], o[0], i0, i3]]
+    pts = np.asarray(pts)
+    n2 = len(pts)
+    z = np.linspace(0.0, 1.0, nz + 1)
+    verts = np.concatenate([np.column_stack([pts, np.full(n2, zk)]) for zk in z])
+    conn = []
+    for k in range(nz):
+        for q0, q1, q2, q3 in quads:
+            lo, hi = k * n2, (k + 1) * n2
+            # tensor order: (0,0)=q0, (1,0)=q1, (0,1)=q3, (1,1)=q2, then the upper layer
+            conn.append([lo + q0, lo + q1, lo + q3, lo + q2, hi + q0, hi + q1, hi + q3, hi + q2])
+    conn = np.asarray(conn, dtype=np.int32)
+    if not scramble:
+        return verts, conn
+    vperm = rng.permutation(len(verts))
+    new_verts = np.empty_like(verts)
+    new_verts[vperm] = verts
+    conn = vperm[conn]
+    conn = conn[rng.permutation(len(conn))]
+    rots = _cube_rotations()
+    pick = rng.integers(0, len(rots), size=len(conn))
+    out = np.array([conn[e][rots[pick[e]]] for e in range(len(conn))], dtype=np.int32)
+    return np.ascontiguousarray(new_verts), np.ascontiguousarray(out)
 
 
 def uniform_vector(n: int, seed: int = 0, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

@@ -19,9 +19,12 @@
  * oracle's readings):
  *   - reference element [0,1]^3; Lagrange basis of order p on the Gauss-Lobatto-
  *     Legendre nodes; Gauss-Legendre quadrature with q points per direction;
- *   - mesh: structured grid of (nx+1)(ny+1)(nz+1) vertices at arbitrary positions
- *     (x index fastest), element (ex,ey,ez) = ex + nx*(ey + ny*ez), trilinear map;
- *   - global DOFs: the (p*nx+1)(p*ny+1)(p*nz+1) node grid, x fastest; element-local
+ *   - mesh: a conforming hexahedral mesh given by its vertices and element connectivity
+ *     (fepa_op_create_hex), or a structured grid of (nx+1)(ny+1)(nz+1) vertices at
+ *     arbitrary positions (x index fastest), element (ex,ey,ez) = ex + nx*(ey + ny*ez)
+ *     (fepa_op_create); each element is the trilinear map of its 8 corners;
+ *   - global DOFs: on a structured grid the (p*nx+1)(p*ny+1)(p*nz+1) node grid, x
+ *     fastest; on a connectivity mesh the numbering of fepa_hex_numbering; element-local
  *     DOF a + (p+1)*(b + (p+1)*c);
  *   - mass: D = w*det(J); diffusion: D = w*adj(J)adj(J)^T/det(J) (symmetric 3x3,
  *     6 stored components xx, xy, xz, yy, yz, zz);
@@ -126,8 +129,47 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
                    int32_t form, void* stream, fepa_op** out);
 
 /*
- * Move the mesh: replace the vertex coordinates (same nx, ny, nz) and rebuild D.
- *   vertices     ((nx+1)*(ny+1)*(nz+1)) x 3 doubles, host or device memory
+ * Create an operator on a conforming hexahedral mesh given by its element connectivity, on
+ * the current CUDA device: the problem statement of Fig. "fig_feod" (Sec. 3.5), where the mesh
+ * defines the global (L-vector) numbering and so G.
+ *   nverts, vertices   host, nverts x 3 doubles (row-major)
+ *   nelems, conn       host int32 [nelems][8]: the vertex ids of each element in tensor-product
+ *                      corner order, corner (i, j, k) of the reference cube at entry i + 2j + 4k
+ *                      (i along the first reference direction); any element order, any vertex
+ *                      numbering, any orientation of each element (det J > 0 required)
+ *   p, q1d, form, stream as fepa_op_create
+ * The DOFs are numbered on the host by fepa_hex_numbering's rule; the boundary (for
+ * fepa_op_boundary_dofs) is every node on a face that only one element holds.  Returns
+ * FEPA_ERR_MESH for a vertex id out of range, an element with a repeated vertex, a face held by
+ * more than two elements, two elements whose four common vertices form different
+ * quadrilaterals, or det J <= 0 at a quadrature point.  Blocks until D is built.  Every other
+ * call takes an op made here as it takes a structured one; fepa_op_set_vertices then takes
+ * nverts x 3 doubles.
+ */
+int fepa_op_create_hex(int64_t nverts, const double* vertices, int64_t nelems, const int32_t* conn, int32_t p,
+                       int32_t q1d, int32_t form, void* stream, fepa_op** out);
+
+/*
+ * Host only (no device work): the global DOF numbering fepa_op_create_hex uses for order p on
+ * the connectivity mesh (nverts, nelems, conn as there), so a caller can map its own data to
+ * the op's DOFs.  Each element's local node (a, b, c) is classed as a vertex, edge, face or
+ * interior node.  Shared edge and face nodes are placed in a frame every element agrees on:
+ * along an edge from its smaller global vertex id; on a face from its smallest-id vertex, the
+ * first axis toward the smaller-id of that vertex's two neighbours on the face.  Numbers are
+ * handed out vertex by vertex, edge by edge (p-1 each), face by face ((p-1)^2 each) and element
+ * interior by element interior ((p-1)^3 each), in the order the elements (in the given order,
+ * nodes in local order) first reach them.
+ *   elem_dofs   host int32 [nelems][(p+1)^3] receiving G, or null
+ *   ndofs       receives the number of global DOFs
+ * Errors as fepa_op_create_hex (FEPA_ERR_MESH for an invalid connectivity).
+ */
+int fepa_hex_numbering(int64_t nverts, int64_t nelems, const int32_t* conn, int32_t p, int32_t* elem_dofs,
+                       int64_t* ndofs);
+
+/*
+ * Move the mesh: replace the vertex coordinates (same mesh topology) and rebuild D.
+ *   vertices     the op's vertex count x 3 doubles (structured: (nx+1)*(ny+1)*(nz+1)),
+ *                host or device memory
  *   on_device    0: vertices is a host pointer; 1: a device pointer
  * Blocks until D is rebuilt; returns FEPA_ERR_MESH (D then undefined) if any
  * det(J) <= 0.  Invalidates the cached diagonal.
@@ -161,9 +203,10 @@ int fepa_op_set_cg_mode(fepa_op* op, int32_t mode);
  * rounding of the element results, not bitwise.  Returns FEPA_ERR_ARG for a null op. */
 int fepa_op_set_fused_dot(fepa_op* op, int32_t enable);
 
-/* Boundary DOFs of the node grid, ascending, written to dofs (host, capacity
- * entries); *count receives the total (which may exceed capacity: then nothing
- * is written and FEPA_ERR_ARG is returned). dofs may be null to query the count. */
+/* Boundary DOFs (structured: of the node grid; connectivity mesh: on faces held by one
+ * element), ascending, written to dofs (host, capacity entries); *count receives the total
+ * (which may exceed capacity: then nothing is written and FEPA_ERR_ARG is returned). dofs
+ * may be null to query the count. */
 int fepa_op_boundary_dofs(const fepa_op* op, int32_t* dofs, int64_t capacity, int64_t* count);
 
 /* Set the essential (Dirichlet) DOF list (host, count entries, each in [0,N)).

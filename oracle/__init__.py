@@ -9,7 +9,7 @@ tests/test_oracle_pins.py against closed forms, invariants, brute force or
 convergence rates; none is "parity unpinned".
 """
 from .fem_oracle import *  # noqa: F401,F403
-from .fem_oracle import (MASS, DIFFUSION, HexGridMesh, Problem, Rule3D, rule, gauss_legendre, gll_points,
+from .fem_oracle import (MASS, DIFFUSION, HexGridMesh, HexMesh, hex_numbering, Problem, Rule3D, rule, gauss_legendre, gll_points,
                          lagrange, elem_dofs, boundary_dofs, num_dofs, node_coords, trilinear, qp_factors,
                          element_matrices, assemble_csr, constrain, action_elementwise, action_rows,
                          diagonal_elementwise, qp_coords, rhs_from_qp, sine_solution, sine_source, jacobi_pcg,

@@ -142,12 +142,85 @@ class HexGridMesh:
         return out
 
 
-def num_dofs(mesh: HexGridMesh, p: int) -> int:
+class HexMesh:
+    """Conforming hexahedral mesh given by its vertices (nverts, 3) and element connectivity
+    (E, 8): the vertex ids of each element, corner (i, j, k) of the reference cube at column
+    i + 2j + 4k.  The global DOF numbering is hex_numbering's (reading R3 for this input)."""
+
+    def __init__(self, vertices: np.ndarray, conn: np.ndarray):
+        self.vertices = np.asarray(vertices, dtype=np.float64)
+        self.conn = np.asarray(conn, dtype=np.int64)
+        if self.vertices.ndim != 2 or self.vertices.shape[1] != 3 or self.conn.ndim != 2 or self.conn.shape[1] != 8:
+            raise ValueError("vertices must be (nverts, 3) and conn (E, 8)")
+        self._numbering = {}
+
+    @property
+    def num_elements(self) -> int:
+        return self.conn.shape[0]
+
+    def element_corners(self) -> np.ndarray:
+        """(E, 8, 3) corner coordinates."""
+        return self.vertices[self.conn]
+
+
+def _face_nodes(p: int, d0: int, side: int):
+    """Element-local indices of the nodes on the local face where coordinate d0 is side*p."""
+    n = p + 1
+    return [a + n * (b + n * c) for c in range(n) for b in range(n) for a in range(n)
+            if (a, b, c)[d0] == side * p]
+
+
+def hex_numbering(mesh: HexMesh, p: int):
+    """Global DOFs of order p on a connectivity mesh, built from a node's place in the mesh
+    rather than from any element's frame: local node (a, b, c) of an element is the point whose
+    trilinear weight on corner (i, j, k) is proportional to the integer
+    (a or p-a) * (b or p-b) * (c or p-c) (a if i = 1 else p - a, and so on), and the node's key is
+    the set of (global vertex id, weight) pairs with nonzero weight.  Elements that share a
+    vertex, edge or face give the shared GLL nodes the same key (the GLL points are symmetric, so
+    index t from one end is index p - t from the other); interior nodes carry all 8 vertices of
+    their element.  DOFs are numbered in sorted key order.  Boundary DOFs: the nodes of every face
+    held by one element.  Returns (elem_dofs (E, (p+1)^3), N, boundary DOFs sorted)."""
+    if p in mesh._numbering:
+        return mesh._numbering[p]
+    n = p + 1
+    loc = [(a, b, c) for c in range(n) for b in range(n) for a in range(n)]
+    wts = np.array([[(a if (cr & 1) else p - a) * (b if (cr >> 1) & 1 else p - b) * (c if (cr >> 2) & 1 else p - c)
+                     for cr in range(8)] for (a, b, c) in loc], dtype=np.int64)
+    keys = []
+    for e in range(mesh.num_elements):
+        vid = mesh.conn[e]
+        for l in range(len(loc)):
+            nz = wts[l] != 0
+            keys.append(tuple(sorted(zip(vid[nz].tolist(), wts[l][nz].tolist()))))
+    uniq = sorted(set(keys))
+    index = {k: i for i, k in enumerate(uniq)}
+    dofs = np.array([index[k] for k in keys], dtype=np.int64).reshape(mesh.num_elements, len(loc))
+    count = {}
+    for e in range(mesh.num_elements):
+        for d0 in range(3):
+            for side in (0, 1):
+                fv = tuple(sorted(mesh.conn[e][[cr for cr in range(8) if ((cr >> d0) & 1) == side]].tolist()))
+                count.setdefault(fv, []).append((e, d0, side))
+    bdr = set()
+    for fv, holders in count.items():
+        if len(holders) == 1:
+            e, d0, side = holders[0]
+            bdr.update(dofs[e, _face_nodes(p, d0, side)].tolist())
+    out = (dofs, len(uniq), np.array(sorted(bdr), dtype=np.int64))
+    mesh._numbering[p] = out
+    return out
+
+
+def num_dofs(mesh, p: int) -> int:
+    if isinstance(mesh, HexMesh):
+        return hex_numbering(mesh, p)[1]
     return (p * mesh.nx + 1) * (p * mesh.ny + 1) * (p * mesh.nz + 1)
 
 
-def elem_dofs(mesh: HexGridMesh, p: int) -> np.ndarray:
+def elem_dofs(mesh, p: int) -> np.ndarray:
     """(E, (p+1)^3) global DOF of each element-local node (reading R3): the map G."""
+    if isinstance(mesh, HexMesh):
+        return hex_numbering(mesh, p)[0]
     n = p + 1
     Nx, Ny = p * mesh.nx + 1, p * mesh.ny + 1
     ez, ey, ex = np.meshgrid(np.arange(mesh.nz), np.arange(mesh.ny), np.arange(mesh.nx), indexing="ij")
@@ -160,8 +233,11 @@ def elem_dofs(mesh: HexGridMesh, p: int) -> np.ndarray:
     return (gx + Nx * (gy + Ny * gz)).astype(np.int64)
 
 
-def boundary_dofs(mesh: HexGridMesh, p: int) -> np.ndarray:
-    """Sorted global DOFs on the boundary of the node grid."""
+def boundary_dofs(mesh, p: int) -> np.ndarray:
+    """Sorted global DOFs on the boundary of the node grid (connectivity mesh: on the faces
+    held by one element)."""
+    if isinstance(mesh, HexMesh):
+        return hex_numbering(mesh, p)[2]
     Nx, Ny, Nz = p * mesh.nx + 1, p * mesh.ny + 1, p * mesh.nz + 1
     gz, gy, gx = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
     on = (gx == 0) | (gx == Nx - 1) | (gy == 0) | (gy == Ny - 1) | (gz == 0) | (gz == Nz - 1)

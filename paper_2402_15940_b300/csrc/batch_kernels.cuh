@@ -86,7 +86,7 @@ bcg_init(ChunkTable t, const double* __restrict__ b, double* __restrict__ r, dou
       q.iter = 0;
       q.maxit = maxit;
       q.alpha = q.beta = 0.0;
-      q.converged = (s[1] <= q.tol2) ? 1 : 0;
+      q.converged = (s[1] <= q.tol2 && isfinite(q.tol2)) ? 1 : 0;
       pdone[j] = q.converged || !isfinite(s[1]) || !isfinite(s[2]);  // NaN/inf: stop at once
       return !pdone[j];
     });

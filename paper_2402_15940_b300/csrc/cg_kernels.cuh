@@ -118,7 +118,7 @@ cg_init(int64_t N, const double* __restrict__ b, double* __restrict__ r, double*
       st->tol2 = rtol2 * tot[2];
       st->iter = 0;
       st->maxit = maxit;
-      st->converged = (tot[1] <= st->tol2) ? 1 : 0;
+      st->converged = (tot[1] <= st->tol2 && isfinite(st->tol2)) ? 1 : 0;
       st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->alpha = st->beta = 0.0;
       st->tick_limit = 0x7fffffff;
@@ -271,7 +271,7 @@ cg32_init(int64_t N, const float* __restrict__ b, float* __restrict__ x, float* 
       st->tol2 = rtol2 * tot[2];
       st->iter = 0;
       st->maxit = maxit;
-      st->converged = (tot[1] <= st->tol2) ? 1 : 0;
+      st->converged = (tot[1] <= st->tol2 && isfinite(st->tol2)) ? 1 : 0;
       st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->alpha = st->beta = 0.0;
       st->tick_limit = 0x7fffffff;

@@ -20,6 +20,7 @@
 
 #include "../../include/fepa.h"
 #include "basis1d.hpp"
+#include "hex_mesh.hpp"
 #include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
 #include "pa_tma_f32.cuh"
@@ -108,7 +109,7 @@ struct KernelSet {
   int df_smem, df_ne;
   void (*diag_df)(int, const int*, const float2*, double*);
   int diag_df_smem, diag_df_ne;
-  void (*rhs_df)(int, int, int, const float2*, const int*, const double*, double, double*);
+  void (*rhs_df)(int64_t, int, int, const int*, const float2*, const int*, const double*, double, double*);
   int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
   Apply32Variant v32_batch;  // variant 2 built to skip the elements of converged batch problems
@@ -275,8 +276,13 @@ struct CgLoop {
 }  // namespace
 
 struct fepa_op {
-  int nx, ny, nz, p, q, n, form;
+  int nx, ny, nz, p, q, n, form;  // nx, ny, nz: structured grid (unused when hex)
   int64_t E, N;
+  int64_t nverts;                 // vertices of the mesh
+  bool hex = false;               // built from element connectivity (fepa_op_create_hex)
+  int* econn = nullptr;           // hex: device [E][8] corner vertex ids
+  std::vector<int32_t> conn_host; // hex: the connectivity (for derived ops, e.g. multigrid levels)
+  std::vector<int32_t> bdr_host;  // hex: DOFs on faces held by one element, ascending
   int device;
   int cg_mode = FEPA_CG_GRAPH;
   int fuse_dot = 1;  // FP32 CG: (d, h) from the action kernel where it has that build
@@ -348,7 +354,7 @@ void free_op(fepa_op* op) {
   cudaStreamSynchronize(op->stream);
   free_loop(op->cg64);
   free_loop(op->cg32);
-  for (void* p : {(void*)op->verts, (void*)op->verts_df, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
+  for (void* p : {(void*)op->verts, (void*)op->verts_df, (void*)op->econn, (void*)op->gmap, (void*)op->qd, (void*)op->B, (void*)op->G, (void*)op->pts,
                   (void*)op->wts, (void*)op->ess, (void*)op->flag, (void*)op->qd32, (void*)op->qddf, (void*)op->err,
                   (void*)op->inv_diag, (void*)op->xw, (void*)op->bw, (void*)op->xio, (void*)op->h64,
                   (void*)op->st_ref, (void*)op->partials_ref, (void*)op->dot_slots})
@@ -714,40 +720,37 @@ int ensure_f32(fepa_op* op) {
 
 // D from the vertices (double-float geometry kernel), also refreshing the (hi, lo) and
 // FP32 copies of D when they exist.  Sets op->flag if a det J <= 0.
+// E elements; corners from econn [E][8] if given, else the structured grid of nx x ny
+// elements per layer
 template <int Q>
-void launch_geom_q(int nx, int ny, int nz, const float2* vdf, int diffusion, double* qd, float2* qddf, float* qd32,
-                   int d32stride, int* bad, cudaStream_t s) {
+void launch_geom_q(int64_t E, int nx, int ny, const int* econn, const float2* vdf, int diffusion, double* qd,
+                   float2* qddf, float* qd32, int d32stride, int* bad, cudaStream_t s) {
   using G = GeoShape<Q>;
-  const int64_t E = (int64_t)nx * ny * nz;
   const int grid = (int)((E + G::NE - 1) / G::NE);
-  geom_df<Q><<<grid, dim3(G::TPE, G::NE), 0, s>>>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad);
+  geom_df<Q><<<grid, dim3(G::TPE, G::NE), 0, s>>>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad);
 }
 
 // the geometry kernel of q (2..10); false if q has none
-bool launch_geom(int q, int nx, int ny, int nz, const float2* vdf, int diffusion, double* qd, float2* qddf,
-                 float* qd32, int d32stride, int* bad, cudaStream_t s) {
+bool launch_geom(int q, int64_t E, int nx, int ny, const int* econn, const float2* vdf, int diffusion, double* qd,
+                 float2* qddf, float* qd32, int d32stride, int* bad, cudaStream_t s) {
+#define GEOM_CASE(Q) \
+  case Q: launch_geom_q<Q>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
   switch (q) {
-    case 2: launch_geom_q<2>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 3: launch_geom_q<3>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 4: launch_geom_q<4>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 5: launch_geom_q<5>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 6: launch_geom_q<6>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 7: launch_geom_q<7>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 8: launch_geom_q<8>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 9: launch_geom_q<9>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
-    case 10: launch_geom_q<10>(nx, ny, nz, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+    GEOM_CASE(2) GEOM_CASE(3) GEOM_CASE(4) GEOM_CASE(5) GEOM_CASE(6) GEOM_CASE(7) GEOM_CASE(8) GEOM_CASE(9)
+    GEOM_CASE(10)
     default: return false;
   }
+#undef GEOM_CASE
 }
 
 int compute_geometry(fepa_op* op) {
   cudaStream_t s = op->stream;
-  const int64_t nv3 = 3 * (int64_t)(op->nx + 1) * (op->ny + 1) * (op->nz + 1);
+  const int64_t nv3 = 3 * op->nverts;
   if (!op->verts_df) TRY(dalloc(&op->verts_df, nv3));
   split_pairs<<<grid_for(nv3, 256, 148 * 8), 256, 0, s>>>(nv3, op->verts, op->verts_df);
   LAUNCH_CHECK();
-  if (!launch_geom(op->q, op->nx, op->ny, op->nz, op->verts_df, op->form == FEPA_DIFFUSION, op->qd, op->qddf,
-                   op->qd32, op->ks.d32_stride, op->flag, s))
+  if (!launch_geom(op->q, op->E, op->nx, op->ny, op->econn, op->verts_df, op->form == FEPA_DIFFUSION, op->qd,
+                   op->qddf, op->qd32, op->ks.d32_stride, op->flag, s))
     return fail(FEPA_ERR_UNSUPPORTED, "q1d %d has no geometry kernel", op->q);
   LAUNCH_CHECK();
   op->qddf_valid = op->qddf != nullptr;
@@ -870,7 +873,7 @@ int fail_nonfinite(const char* what) {
 void fill_stats(const CgState& h, fepa_cg_stats* stats) {
   if (!stats) return;
   stats->iterations = h.iter;
-  stats->status = h.converged ? FEPA_OK : (nonfinite(h) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
+  stats->status = nonfinite(h) ? FEPA_ERR_NONFINITE : (h.converged ? FEPA_OK : FEPA_ERR_NOCONV);
   stats->b_norm = sqrt(h.bb);
   stats->rel_residual = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
   stats->precond_norm = sqrt(fabs(h.rho));
@@ -1107,38 +1110,34 @@ const char* fepa_last_error(void) { return g_err.c_str(); }
 
 int64_t fepa_launch_count(void) { return g_launches.load(); }
 
-int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, int32_t p, int32_t q1d, int32_t form,
-                   void* stream, fepa_op** out) {
-  if (!out) return fail(FEPA_ERR_ARG, "out is null");
-  *out = nullptr;
-  if (!vertices) return fail(FEPA_ERR_ARG, "vertices is null");
-  if (nx < 1 || ny < 1 || nz < 1) return fail(FEPA_ERR_ARG, "element counts must be >= 1");
+}  // extern "C"
+
+namespace {
+
+// The part of op creation both mesh front ends share: checks of p, q and form, the 1D
+// tables, device arrays, the vertex copy, G (written by build_map on the op's stream) and D.
+// hex: the connectivity front end (conn_host and bdr_host already filled by the caller).
+int create_common(fepa_op* op, int32_t p, int32_t q1d, int32_t form, void* stream, int64_t E, int64_t N,
+                  int64_t nverts, const double* vertices, const std::function<int(fepa_op*)>& build_map) {
   if (p < 1 || p > FEPA_MAX_ORDER) return fail(FEPA_ERR_UNSUPPORTED, "order %d outside 1..%d", p, FEPA_MAX_ORDER);
   const int q = q1d == 0 ? p + 2 : q1d;
   if (q != p + 1 && q != p + 2) return fail(FEPA_ERR_UNSUPPORTED, "q1d %d not compiled for p=%d (p+1 or p+2)", q, p);
   if (form != FEPA_MASS && form != FEPA_DIFFUSION) return fail(FEPA_ERR_ARG, "unknown form %d", form);
-  const int64_t E = (int64_t)nx * ny * nz;
   const int n = p + 1;
-  const int64_t N = ((int64_t)p * nx + 1) * ((int64_t)p * ny + 1) * ((int64_t)p * nz + 1);
   if (N >= (int64_t)ESS_SKIP || E * n * n * n >= ((int64_t)1 << 31) || E >= ((int64_t)1 << 31))
     return fail(FEPA_ERR_ARG, "mesh too large for 32-bit DOF indices");
-
-  fepa_op* op = new fepa_op();
-  op->nx = nx; op->ny = ny; op->nz = nz; op->p = p; op->q = q; op->n = n; op->form = form;
-  op->E = E; op->N = N;
+  op->p = p; op->q = q; op->n = n; op->form = form;
+  op->E = E; op->N = N; op->nverts = nverts;
   op->stream = (cudaStream_t)stream;
   op->ks = kernels().t[p][q - p - 1][form];
-  auto bail = [&](int rc) { free_op(op); return rc; };
-  if (cudaGetDevice(&op->device) != cudaSuccess) return bail(fail(FEPA_ERR_CUDA, "no CUDA device"));
+  if (cudaGetDevice(&op->device) != cudaSuccess) return fail(FEPA_ERR_CUDA, "no CUDA device");
   if (cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(FEPA_ERR_CUDA, "stream creation failed"));
-  int rc;
-  if ((rc = allow_smem((const void*)op->ks.apply, op->ks.apply_smem)) ||
-      (rc = allow_smem((const void*)op->ks.apply_df, op->ks.df_smem)) ||
-      (rc = allow_smem((const void*)op->ks.diag_df, op->ks.diag_df_smem)) ||
-      (rc = allow_smem((const void*)op->ks.diag, op->ks.diag_smem)) ||
-      (rc = allow_smem((const void*)op->ks.rhs_df, op->ks.rhs_df_smem)))
-    return bail(rc);
+    return fail(FEPA_ERR_CUDA, "stream creation failed");
+  TRY(allow_smem((const void*)op->ks.apply, op->ks.apply_smem));
+  TRY(allow_smem((const void*)op->ks.apply_df, op->ks.df_smem));
+  TRY(allow_smem((const void*)op->ks.diag_df, op->ks.diag_df_smem));
+  TRY(allow_smem((const void*)op->ks.diag, op->ks.diag_smem));
+  TRY(allow_smem((const void*)op->ks.rhs_df, op->ks.rhs_df_smem));
 
   // host tables
   std::vector<long double> nodes = basis::gll_nodes(p), gx, gw;
@@ -1150,38 +1149,105 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
   std::vector<double> ph(q), wh(q);
   for (int i = 0; i < q; ++i) { ph[i] = (double)gx[i]; wh[i] = (double)gw[i]; }
 
-  const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int ncomp = form == FEPA_DIFFUSION ? 6 : 1;
   const int64_t q3 = (int64_t)q * q * q;
-  op->verts_host.assign(vertices, vertices + 3 * nv);
-  if ((rc = dalloc(&op->verts, 3 * nv)) || (rc = dalloc(&op->gmap, E * n * n * n)) ||
-      (rc = dalloc(&op->qd, E * ncomp * q3)) || (rc = dalloc(&op->B, (size_t)q * n)) ||
-      (rc = dalloc(&op->G, (size_t)q * n)) || (rc = dalloc(&op->pts, q)) || (rc = dalloc(&op->wts, q)) ||
-      (rc = dalloc(&op->flag, 1)) || (rc = dalloc(&op->err, 1)))
-    return bail(rc);
+  op->verts_host.assign(vertices, vertices + 3 * nverts);
+  TRY(dalloc(&op->verts, 3 * nverts));
+  TRY(dalloc(&op->gmap, E * n * n * n));
+  TRY(dalloc(&op->qd, E * ncomp * q3));
+  TRY(dalloc(&op->B, (size_t)q * n));
+  TRY(dalloc(&op->G, (size_t)q * n));
+  TRY(dalloc(&op->pts, q));
+  TRY(dalloc(&op->wts, q));
+  TRY(dalloc(&op->flag, 1));
+  TRY(dalloc(&op->err, 1));
   cudaStream_t s = op->stream;
-#define CREATE_TRY(call)                                                                        \
-  do {                                                                                          \
-    cudaError_t e_ = (call);                                                                    \
-    if (e_ != cudaSuccess) return bail(fail(FEPA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
-  } while (0)
-  CREATE_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s));
-  CREATE_TRY(cudaMemcpyAsync(op->B, Bh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
-  CREATE_TRY(cudaMemcpyAsync(op->G, Gh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
-  if ((rc = upload_df_tables(p, q, Bh, Gh, s))) return bail(rc);
-  CREATE_TRY(cudaMemcpyAsync(op->pts, ph.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
-  CREATE_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
-  CREATE_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
-  CREATE_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
-  CREATE_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
-  build_gmap<<<grid_for(E * n * n * n, 256, 148 * 32), 256, 0, s>>>(nx, ny, nz, p, 0, op->gmap);
-  g_launches.fetch_add(1);
-  if ((rc = upload_gauss_df(q, gx, gw, s)) || (rc = compute_geometry(op))) return bail(rc);
-  CREATE_TRY(cudaGetLastError());
-  CREATE_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CREATE_TRY(cudaStreamSynchronize(s));
-  if (*op->st_host_flag) return bail(fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point"));
-#undef CREATE_TRY
+  CUDA_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nverts * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(op->B, Bh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(op->G, Gh.data(), q * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  TRY(upload_df_tables(p, q, Bh, Gh, s));
+  CUDA_TRY(cudaMemcpyAsync(op->pts, ph.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
+  TRY(build_map(op));
+  TRY(upload_gauss_df(q, gx, gw, s));
+  TRY(compute_geometry(op));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
+  return FEPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, int32_t p, int32_t q1d, int32_t form,
+                   void* stream, fepa_op** out) {
+  if (!out) return fail(FEPA_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!vertices) return fail(FEPA_ERR_ARG, "vertices is null");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(FEPA_ERR_ARG, "element counts must be >= 1");
+  const int64_t E = (int64_t)nx * ny * nz;
+  const int64_t N = ((int64_t)p * nx + 1) * ((int64_t)p * ny + 1) * ((int64_t)p * nz + 1);
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  fepa_op* op = new fepa_op();
+  op->nx = nx; op->ny = ny; op->nz = nz;
+  // G of the lexicographic node grid, built on the device
+  auto grid_map = [](fepa_op* o) -> int {
+    const int64_t slots = o->E * o->n * o->n * o->n;
+    build_gmap<<<grid_for(slots, 256, 148 * 32), 256, 0, o->stream>>>(o->nx, o->ny, o->nz, o->p, 0, o->gmap);
+    LAUNCH_CHECK();
+    return FEPA_OK;
+  };
+  const int rc = create_common(op, p, q1d, form, stream, E, N, nv, vertices, grid_map);
+  if (rc != FEPA_OK) { free_op(op); return rc; }
+  *out = op;
+  return FEPA_OK;
+}
+
+int fepa_hex_numbering(int64_t nverts, int64_t nelems, const int32_t* conn, int32_t p, int32_t* elem_dofs,
+                       int64_t* ndofs) {
+  if (!conn || !ndofs) return fail(FEPA_ERR_ARG, "null argument");
+  if (p < 1 || p > FEPA_MAX_ORDER) return fail(FEPA_ERR_UNSUPPORTED, "order %d outside 1..%d", p, FEPA_MAX_ORDER);
+  hexmesh::Numbering num;
+  if (!hexmesh::number_dofs(nverts, nelems, conn, p, num, (int64_t)ESS_SKIP - 1))
+    return fail(FEPA_ERR_MESH, "%s", num.error.c_str());
+  *ndofs = num.ndofs;
+  if (elem_dofs) std::copy(num.gmap.begin(), num.gmap.end(), elem_dofs);
+  return FEPA_OK;
+}
+
+int fepa_op_create_hex(int64_t nverts, const double* vertices, int64_t nelems, const int32_t* conn, int32_t p,
+                       int32_t q1d, int32_t form, void* stream, fepa_op** out) {
+  if (!out) return fail(FEPA_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!vertices || !conn) return fail(FEPA_ERR_ARG, "null argument");
+  if (nverts < 1 || nelems < 1 || nverts >= ((int64_t)1 << 31)) return fail(FEPA_ERR_ARG, "bad mesh sizes");
+  if (p < 1 || p > FEPA_MAX_ORDER) return fail(FEPA_ERR_UNSUPPORTED, "order %d outside 1..%d", p, FEPA_MAX_ORDER);
+  hexmesh::Numbering num;
+  if (!hexmesh::number_dofs(nverts, nelems, conn, p, num, (int64_t)ESS_SKIP - 1))
+    return fail(FEPA_ERR_MESH, "%s", num.error.c_str());
+  fepa_op* op = new fepa_op();
+  op->hex = true;
+  op->nx = 1; op->ny = 1; op->nz = 1;
+  op->conn_host.assign(conn, conn + 8 * nelems);
+  op->bdr_host = std::move(num.boundary);
+  const std::vector<int32_t>& gm = num.gmap;
+  // G from the host numbering, and the connectivity the geometry kernels read
+  auto copy_map = [&gm](fepa_op* o) -> int {
+    TRY(dalloc(&o->econn, 8 * o->E));
+    CUDA_TRY(cudaMemcpyAsync(o->econn, o->conn_host.data(), 8 * o->E * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             o->stream));
+    CUDA_TRY(cudaMemcpyAsync(o->gmap, gm.data(), gm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, o->stream));
+    CUDA_TRY(cudaStreamSynchronize(o->stream));  // gm is a host temporary
+    return FEPA_OK;
+  };
+  const int rc = create_common(op, p, q1d, form, stream, nelems, num.ndofs, nverts, vertices, copy_map);
+  if (rc != FEPA_OK) { free_op(op); return rc; }
   *out = op;
   return FEPA_OK;
 }
@@ -1189,7 +1255,7 @@ int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, i
 int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device) {
   if (!op || !vertices) return fail(FEPA_ERR_ARG, "null argument");
   cudaStream_t s = op->stream;
-  const int64_t nv = (int64_t)(op->nx + 1) * (op->ny + 1) * (op->nz + 1);
+  const int64_t nv = op->nverts;
   CUDA_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nv * sizeof(double),
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   if (on_device) {
@@ -1243,6 +1309,15 @@ int fepa_op_set_cg_mode(fepa_op* op, int32_t mode) {
 
 int fepa_op_boundary_dofs(const fepa_op* op, int32_t* dofs, int64_t capacity, int64_t* count) {
   if (!op || !count) return fail(FEPA_ERR_ARG, "null argument");
+  if (op->hex) {
+    const int64_t total = (int64_t)op->bdr_host.size();
+    *count = total;
+    if (!dofs) return FEPA_OK;
+    if (capacity < total)
+      return fail(FEPA_ERR_ARG, "capacity %lld < %lld boundary DOFs", (long long)capacity, (long long)total);
+    std::copy(op->bdr_host.begin(), op->bdr_host.end(), dofs);
+    return FEPA_OK;
+  }
   const int64_t Nx = (int64_t)op->p * op->nx + 1, Ny = (int64_t)op->p * op->ny + 1, Nz = (int64_t)op->p * op->nz + 1;
   const int64_t total = Nx * Ny * Nz - (Nx - 2) * (Ny - 2) * (Nz - 2);
   *count = total;
@@ -1268,14 +1343,30 @@ int fepa_op_set_essential(fepa_op* op, const int32_t* dofs, int64_t count) {
   unsigned char* dmask = nullptr;
   TRY(dalloc(&dmask, op->N));
   cudaError_t e = cudaMemcpyAsync(dmask, mask.data(), op->N, cudaMemcpyHostToDevice, s);
+  int* first = nullptr;  // unstructured mesh: first slot of every DOF, its owner when essential
+  if (e == cudaSuccess && op->hex) {
+    if (dalloc(&first, op->N) != FEPA_OK) {
+      cudaFree(dmask);
+      return FEPA_ERR_OOM;
+    }
+    e = cudaMemsetAsync(first, 0x7f, op->N * sizeof(int), s);
+  }
   if (e == cudaSuccess) {
     const int64_t total = op->E * op->n * op->n * op->n;
-    flag_gmap<<<grid_for(total, 256, 148 * 32), 256, 0, s>>>(op->nx, op->ny, op->nz, op->p, dmask, op->gmap);
-    g_launches.fetch_add(1);
+    const int grid = grid_for(total, 256, 148 * 32);
+    if (op->hex) {
+      gmap_first_slot<<<grid, 256, 0, s>>>(total, op->gmap, first);
+      flag_gmap_first<<<grid, 256, 0, s>>>(total, dmask, first, op->gmap);
+      g_launches.fetch_add(2);
+    } else {
+      flag_gmap<<<grid, 256, 0, s>>>(op->nx, op->ny, op->nz, op->p, dmask, op->gmap);
+      g_launches.fetch_add(1);
+    }
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(dmask);
+  if (first) cudaFree(first);
   if (e != cudaSuccess) return fail(FEPA_ERR_CUDA, "set_essential: %s", cudaGetErrorString(e));
   if (op->ess) { cudaFree(op->ess); op->ess = nullptr; }
   op->ess_count = 0;
@@ -1307,8 +1398,8 @@ int fepa_op_qdata(const fepa_op* op, double* out) {
 int fepa_op_qp_coords(const fepa_op* op, double* out) {
   if (!op || !out) return fail(FEPA_ERR_ARG, "null argument");
   const int64_t total = op->E * op->q * op->q * op->q;
-  qp_coords_kernel<<<grid_for(total, 256, 148 * 32), 256, 0, op->stream>>>(op->nx, op->ny, op->nz, op->q, op->verts,
-                                                                         op->pts, out);
+  qp_coords_kernel<<<grid_for(total, 256, 148 * 32), 256, 0, op->stream>>>(op->E, op->nx, op->ny, op->econn, op->q,
+                                                                         op->verts, op->pts, out);
   LAUNCH_CHECK();
   return FEPA_OK;
 }
@@ -1400,8 +1491,8 @@ static int rhs_common(fepa_op* op, const double* f_qp, double scale, double* b) 
   CUDA_TRY(cudaMemsetAsync(b, 0, op->N * sizeof(double), s));
   const KernelSet& k = op->ks;
   const int grid = (int)((op->E + k.rhs_df_ne - 1) / k.rhs_df_ne);
-  k.rhs_df<<<grid, dim3(op->q * op->q, k.rhs_df_ne), k.rhs_df_smem, s>>>(op->nx, op->ny, op->nz, op->verts_df,
-                                                                         op->gmap, f_qp, scale, b);
+  k.rhs_df<<<grid, dim3(op->q * op->q, k.rhs_df_ne), k.rhs_df_smem, s>>>(op->E, op->nx, op->ny, op->econn,
+                                                                         op->verts_df, op->gmap, f_qp, scale, b);
   LAUNCH_CHECK();
   return FEPA_OK;
 }
@@ -1559,7 +1650,7 @@ extern "C" int fepa_cg_solve_noalloc(fepa_op* op, const double* b, double* x, do
   }
   if (stats) {
     stats->iterations = hs.iter;
-    stats->status = hs.converged ? FEPA_OK : (nonfinite(hs) ? FEPA_ERR_NONFINITE : FEPA_ERR_NOCONV);
+    stats->status = nonfinite(hs) ? FEPA_ERR_NONFINITE : (hs.converged ? FEPA_OK : FEPA_ERR_NOCONV);
     stats->b_norm = sqrt(hs.bb);
     stats->rel_residual = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
     stats->precond_norm = sqrt(fabs(hs.rho));

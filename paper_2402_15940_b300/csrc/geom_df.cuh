@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "pa_df64.cuh"
+#include "pa_kernels.cuh"  // corner_vertex
 
 namespace fepa {
 
@@ -38,25 +39,24 @@ struct GeoShape {
   static constexpr int NE = (256 / TPE) > 0 ? (256 / TPE) : 1;
 };
 
-// vdf: vertex coordinates as (hi, lo) pairs [(nx+1)(ny+1)(nz+1)][3].  qd: FP64 D
-// [E][comp][q^3]; qddf (optional): the same as (hi, lo) pairs; qd32 (optional): FP32 D
-// with each component padded to d32stride values.
+// vdf: vertex coordinates as (hi, lo) pairs [nverts][3]; the corners of element e come from
+// econn [E][8] when given (unstructured mesh), else from the structured vertex grid of nx x ny
+// elements per layer (corner_vertex).  qd: FP64 D [E][comp][q^3]; qddf (optional): the same
+// as (hi, lo) pairs; qd32 (optional): FP32 D with each component padded to d32stride values.
 template <int Q>
 __global__ void __launch_bounds__(GeoShape<Q>::TPE * GeoShape<Q>::NE)
-geom_df(int nx, int ny, int nz, const float2* __restrict__ vdf, int diffusion, double* __restrict__ qd,
-        float2* __restrict__ qddf, float* __restrict__ qd32, int d32stride, int* __restrict__ bad) {
+geom_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* __restrict__ vdf, int diffusion,
+        double* __restrict__ qd, float2* __restrict__ qddf, float* __restrict__ qd32, int d32stride,
+        int* __restrict__ bad) {
   constexpr int TPE = GeoShape<Q>::TPE, NE = GeoShape<Q>::NE, Q3 = Q * Q * Q;
   __shared__ dfl sX[NE][8][3];
   const int tid = threadIdx.x, el = threadIdx.y;
-  const int64_t E = (int64_t)nx * ny * nz;
   const int64_t e = (int64_t)blockIdx.x * NE + el;
   const bool live = e < E;
   if (live) {
-    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     for (int l = tid; l < 24; l += TPE) {  // 24 corner coordinates (q^2 may be fewer threads)
       const int c = l / 3, d = l - 3 * c;
-      const int64_t v =
-          (ex + (c & 1)) + (int64_t)(nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(ny + 1) * (ez + ((c >> 2) & 1)));
+      const int64_t v = corner_vertex(econn, nx, ny, e, c);
       const float2 xv = vdf[3 * v + d];
       sX[el][c][d] = dfl{xv.x, xv.y};
     }
@@ -255,8 +255,8 @@ struct RhsDfShape {
 
 template <int P, int Q>
 __global__ void __launch_bounds__(RhsDfShape<P, Q>::TPE * RhsDfShape<P, Q>::NE)
-pa_rhs_df(int nx, int ny, int nz, const float2* __restrict__ vdf, const int* __restrict__ gmap,
-          const double* __restrict__ f_qp, double scale, double* __restrict__ b) {
+pa_rhs_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* __restrict__ vdf,
+          const int* __restrict__ gmap, const double* __restrict__ f_qp, double scale, double* __restrict__ b) {
   using S = RhsDfShape<P, Q>;
   using T = TabDf<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
@@ -266,15 +266,12 @@ pa_rhs_df(int nx, int ny, int nz, const float2* __restrict__ vdf, const int* __r
   dfl* sX = base + el * (S::PER + 24);  // corners [8][3]
   dfl* S2 = sX + 24;
   dfl* S1 = S2 + n * TPE;
-  const int64_t E = (int64_t)nx * ny * nz;
   const int64_t e = (int64_t)blockIdx.x * NE + el;
   const bool live = e < E;
   if (live) {
-    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     for (int l = tid; l < 24; l += TPE) {
       const int c = l / 3, d = l - 3 * c;
-      const int64_t v =
-          (ex + (c & 1)) + (int64_t)(nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(ny + 1) * (ez + ((c >> 2) & 1)));
+      const int64_t v = corner_vertex(econn, nx, ny, e, c);
       const float2 xv = vdf[3 * v + d];
       sX[l] = dfl{xv.x, xv.y};
     }

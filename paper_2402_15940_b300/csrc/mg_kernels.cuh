@@ -216,6 +216,19 @@ __global__ void mg_inv_multiplicity(int nx, int ny, int nz, int p, T* __restrict
   }
 }
 
+// Any mesh: count[g] += 1 per element-local slot holding DOF g (count zeroed first) ...
+__global__ void gmap_count(int64_t total, const int* __restrict__ gmap, int* __restrict__ count) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(count + gmap_dof(gmap[t]), 1);
+}
+
+// ... then 1 / count, the inverse multiplicity used by the restriction
+template <typename T>
+__global__ void inv_count(int64_t N, const int* __restrict__ count, T* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = T(1) / T(count[t]);
+}
+
 // Chebyshev-accelerated Jacobi, from x = 0: start x = 0, r = b, d = D^{-1} b / theta, h = 0
 template <typename T>
 __global__ void cheb_start(int64_t N, const T* __restrict__ b, const T* __restrict__ invd, T inv_theta,
@@ -409,7 +422,7 @@ pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, doubl
       st->tol2 = rtol2 * tot[1];
       st->iter = 0;
       st->maxit = maxit;
-      st->converged = tot[0] <= st->tol2 ? 1 : 0;
+      st->converged = (tot[0] <= st->tol2 && isfinite(st->tol2)) ? 1 : 0;
       st->done = st->converged || !isfinite(st->rr) || !isfinite(st->bb);  // NaN/inf: stop at once
       st->rho = 0.0;
       st->alpha = st->beta = 0.0;

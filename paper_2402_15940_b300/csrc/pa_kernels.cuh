@@ -29,28 +29,36 @@ __device__ __forceinline__ int gmap_dof(int g) { return g >= 0 ? g : ((~g) & ESS
 // [e][comp][q^3], point i + q*(j + q*k) (computed by geom_df.cuh); the corners of an
 // element, for the quadrature-point coordinates
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void element_corners(const double* __restrict__ verts, int nx, int ny, int64_t e,
-                                                double X[8][3]) {
+// vertex of corner c = i + 2j + 4k of element e: from the connectivity econn [E][8] of an
+// unstructured mesh, else on the structured grid of nx x ny elements per layer (x fastest)
+__device__ __forceinline__ int64_t corner_vertex(const int* __restrict__ econn, int nx, int ny, int64_t e, int c) {
+  if (econn) return econn[8 * e + c];
   const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+  return (ex + (c & 1)) + (int64_t)(nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(ny + 1) * (ez + ((c >> 2) & 1)));
+}
+
+__device__ __forceinline__ void element_corners(const double* __restrict__ verts, const int* __restrict__ econn,
+                                                int nx, int ny, int64_t e, double X[8][3]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int64_t v = (ex + (c & 1)) + (int64_t)(nx + 1) * ((ey + ((c >> 1) & 1)) + (int64_t)(ny + 1) * (ez + ((c >> 2) & 1)));
+    const int64_t v = corner_vertex(econn, nx, ny, e, c);
     X[c][0] = verts[3 * v + 0];
     X[c][1] = verts[3 * v + 1];
     X[c][2] = verts[3 * v + 2];
   }
 }
 
-__global__ void qp_coords_kernel(int nx, int ny, int nz, int q, const double* __restrict__ verts,
-                                 const double* __restrict__ pts, double* __restrict__ out) {
+__global__ void qp_coords_kernel(int64_t E, int nx, int ny, const int* __restrict__ econn, int q,
+                                 const double* __restrict__ verts, const double* __restrict__ pts,
+                                 double* __restrict__ out) {
   const int64_t q3 = (int64_t)q * q * q;
-  const int64_t total = (int64_t)nx * ny * nz * q3;
+  const int64_t total = E * q3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = t / q3;
     const int qp = (int)(t - e * q3);
     const double s = pts[qp % q], tt = pts[(qp / q) % q], u = pts[qp / (q * q)];
     double X[8][3];
-    element_corners(verts, nx, ny, e, X);
+    element_corners(verts, econn, nx, ny, e, X);
     double x[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -97,6 +105,23 @@ __global__ void flag_gmap(int nx, int ny, int nz, int p, const unsigned char* __
     const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
     const bool own = (a < p || ex == nx - 1) && (b < p || ey == ny - 1) && (c < p || ez == nz - 1);
     gmap[t] = own ? ~g : ~(g | ESS_SKIP);
+  }
+}
+
+// Any mesh: first[g] = the smallest element-local slot e (p+1)^3 + l holding DOF g (first
+// initialised to INT_MAX); that occurrence is the owner of an essential DOF.
+__global__ void gmap_first_slot(int64_t total, const int* __restrict__ gmap, int* __restrict__ first) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    atomicMin(first + gmap_dof(gmap[t]), (int)t);
+}
+
+// Any mesh: re-encode gmap for the essential mask with the owners of gmap_first_slot.
+__global__ void flag_gmap_first(int64_t total, const unsigned char* __restrict__ ess_mask,
+                                const int* __restrict__ first, int* __restrict__ gmap) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int g = gmap_dof(gmap[t]);
+    if (!ess_mask[g]) { gmap[t] = g; continue; }
+    gmap[t] = first[g] == (int)t ? ~g : ~(g | ESS_SKIP);
   }
 }
 

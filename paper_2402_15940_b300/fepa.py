@@ -80,6 +80,8 @@ SIGNATURES = [
     ("fepa_last_error", ctypes.c_char_p, []),
     ("fepa_launch_count", _I64, []),
     ("fepa_op_create", ctypes.c_int, [_I32, _I32, _I32, _P, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    ("fepa_op_create_hex", ctypes.c_int, [_I64, _P, _I64, _P, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    ("fepa_hex_numbering", ctypes.c_int, [_I64, _I64, _P, _I32, _P, ctypes.POINTER(_I64)]),
     ("fepa_op_set_vertices", ctypes.c_int, [_P, _P, _I32]),
     ("fepa_op_destroy", None, [_P]),
     ("fepa_op_ndofs", _I64, [_P]),
@@ -206,8 +208,23 @@ def _dev_ptr(t, dtype, numel, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def hex_numbering(nverts, conn, p):
+    """(elem_dofs [E][(p+1)^3] int32, N): the DOF numbering fepa_op_create_hex uses for order p
+    on a connectivity mesh (host computation in the library; no device needed)."""
+    lib = load_library()
+    c = np.ascontiguousarray(conn, dtype=np.int32)
+    if c.ndim != 2 or c.shape[1] != 8:
+        raise ValueError("conn must have shape (E, 8)")
+    out = np.empty((c.shape[0], (int(p) + 1) ** 3), dtype=np.int32)
+    nd = ctypes.c_int64()
+    _check(lib.fepa_hex_numbering(int(nverts), c.shape[0], c.ctypes.data_as(ctypes.c_void_p), int(p),
+                                  out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nd)))
+    return out, int(nd.value)
+
+
 class Operator:
-    """A partial-assembly operator: structured hex mesh + H1 space of order p + form + D."""
+    """A partial-assembly operator: hex mesh (structured grid, or vertices + element
+    connectivity through Operator.from_hex) + H1 space of order p + form + D."""
 
     def __init__(self, nx, ny, nz, vertices, p, form="diffusion", q=0):
         torch = _torch()
@@ -217,11 +234,39 @@ class Operator:
             raise ValueError("vertices must have shape ((nx+1)(ny+1)(nz+1), 3)")
         self._lib = lib
         self.nx, self.ny, self.nz, self.p = int(nx), int(ny), int(nz), int(p)
+        self.nverts = v.shape[0]
         self.form = _FORMS[form]
         h = ctypes.c_void_p()
         stream = torch.cuda.current_stream().cuda_stream
         _check(lib.fepa_op_create(self.nx, self.ny, self.nz, v.ctypes.data_as(ctypes.c_void_p), self.p, int(q),
                                   self.form, ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._init_handle(h)
+
+    @classmethod
+    def from_hex(cls, vertices, conn, p, form="diffusion", q=0):
+        """Operator on a conforming hexahedral mesh: vertices (nverts, 3), conn (E, 8) with the
+        corners of each element in tensor-product order (corner (i, j, k) at i + 2j + 4k)."""
+        torch = _torch()
+        lib = load_library()
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        c = np.ascontiguousarray(conn, dtype=np.int32)
+        if v.ndim != 2 or v.shape[1] != 3 or c.ndim != 2 or c.shape[1] != 8:
+            raise ValueError("vertices must have shape (nverts, 3) and conn (E, 8)")
+        self = cls.__new__(cls)
+        self._lib = lib
+        self.nx = self.ny = self.nz = None
+        self.p, self.nverts = int(p), v.shape[0]
+        self.form = _FORMS[form]
+        h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream().cuda_stream
+        _check(lib.fepa_op_create_hex(v.shape[0], v.ctypes.data_as(ctypes.c_void_p), c.shape[0],
+                                      c.ctypes.data_as(ctypes.c_void_p), self.p, int(q), self.form,
+                                      ctypes.c_void_p(stream), ctypes.byref(h)))
+        self._init_handle(h)
+        return self
+
+    def _init_handle(self, h):
+        lib = self._lib
         self._h = h
         self.N = int(lib.fepa_op_ndofs(h))
         self.E = int(lib.fepa_op_nelems(h))
@@ -252,7 +297,7 @@ class Operator:
     def set_vertices(self, vertices):
         """New vertex positions (numpy host array or CUDA float64 tensor); rebuilds D."""
         torch = _torch()
-        nv = (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
+        nv = self.nverts
         self._sync_stream()
         if isinstance(vertices, torch.Tensor):
             ptr = _dev_ptr(vertices, torch.float64, 3 * nv, "vertices")
