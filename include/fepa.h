@@ -44,8 +44,12 @@
  *     binary32).  The arithmetic of the "FP64" action (fepa_op_apply and the FP64 solves)
  *     is chosen per op by fepa_op_set_f64_variant: native binary64, or double-float pairs
  *     on the FP32 pipe (about 48 significant bits, relative error far below the 1e-12 of the
- *     action's contract) where the op's data lies in that arithmetic's exponent range
- *     (checked by the library; outside it the native kernel is used).
+ *     action's contract).  That action rescales its input by exact powers of two wherever
+ *     the values or their products with D would leave the float exponent range, so it holds
+ *     for any finite FP64 input.  The set-up (geometry, D, diagonal, load vector) is also
+ *     double-float: an element of extent h must satisfy h >= 2^-20, |coordinates| <= 2^20 and
+ *     |coordinates| <= 2^10 h (D then accurate to ~2^-48 |x|/h, 1e-13 on unit-cube meshes up to
+ *     256 elements per side); outside that range creation returns FEPA_ERR_UNSUPPORTED.
  */
 #ifndef FEPA_H
 #define FEPA_H
@@ -123,7 +127,8 @@ int64_t fepa_launch_count(void);
  *   stream        cudaStream_t (as void*) on which all work of this op is enqueued
  * Builds G (element->DOF map), the 1D tables of B, and D (Sec. 2.2, partial
  * assembly: the quadrature-point data is computed once and stored).  Blocks until D
- * is built and returns FEPA_ERR_MESH if any det(J) <= 0.  No essential DOFs are set.
+ * is built and returns FEPA_ERR_MESH if any det(J) <= 0, FEPA_ERR_UNSUPPORTED if an element
+ * is outside the set-up's range (see the conventions above).  No essential DOFs are set.
  */
 int fepa_op_create(int32_t nx, int32_t ny, int32_t nz, const double* vertices, int32_t p, int32_t q1d,
                    int32_t form, void* stream, fepa_op** out);
@@ -172,7 +177,8 @@ int fepa_hex_numbering(int64_t nverts, int64_t nelems, const int32_t* conn, int3
  *                host or device memory
  *   on_device    0: vertices is a host pointer; 1: a device pointer
  * Blocks until D is rebuilt; returns FEPA_ERR_MESH (D then undefined) if any
- * det(J) <= 0.  Invalidates the cached diagonal.
+ * det(J) <= 0, FEPA_ERR_UNSUPPORTED (D undefined) outside the set-up's range.  Invalidates
+ * the cached diagonal.
  */
 int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device);
 
@@ -276,8 +282,10 @@ const char* fepa_f32_variant_name(int32_t variant);
  * the FP64 one, 8 bytes per value), every contraction step is an accurate dot-product
  * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative error),
  * and the element result is recombined in FP64 -- error far inside the FP64 action's
- * tolerance; valid while values stay within the float exponent range less the low
- * word's 24 bits (about 1e-30 .. 3e38), outside it force variant 0.  This library's own
+ * tolerance.  Each block checks the exponents of its gathered x against D's largest
+ * exponent (found by the geometry kernel) and, where the products would leave the
+ * float range less the low word's 24 bits, re-gathers x times an exact power of two and
+ * scales the results back (a second pass over the block's x, rare).  This library's own
  * design for a GPU whose FP64 rate is a small fraction of its FP32 rate; the paper's
  * FP64 kernels have no counterpart.  By default (-1) the first FP64 use times both on
  * this op's mesh and keeps the faster; cached per device, (p, q, form) and mesh size
@@ -294,6 +302,7 @@ int fepa_op_diagonal(fepa_op* op, double* diag);
 
 /* b = G^T B^T (w det(J) f): load vector of f given at the quadrature points.
  *   f_qp  device double [E][q^3]; b device, N doubles (overwritten).
+ * Computed in double-float: |f| w det J should stay within 2^-70 .. 2^100 where it matters.
  * Essential rows are left as computed (the caller sets boundary values). */
 int fepa_op_rhs(fepa_op* op, const double* f_qp, double* b);
 

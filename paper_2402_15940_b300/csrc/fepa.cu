@@ -95,7 +95,7 @@ using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
 constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
 using ApplyDfFn = void (*)(int, const int*, const float2*, const double*, double*, const int*, const int*,
-                          const int*);
+                          const int*, int);
 
 struct Apply32Variant {
   Apply32Fn fn;
@@ -109,7 +109,7 @@ struct KernelSet {
   int df_smem, df_ne;
   void (*diag_df)(int, const int*, const float2*, double*);
   int diag_df_smem, diag_df_ne;
-  void (*rhs_df)(int64_t, int, int, const int*, const float2*, const int*, const double*, double, double*);
+  void (*rhs_df)(int64_t, int, int, const int*, const float2*, const int*, const double*, double, double, double*);
   int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
   Apply32Variant v32_batch;  // variant 2 built to skip the elements of converged batch problems
@@ -303,7 +303,8 @@ struct fepa_op {
   double* wts = nullptr;
   int* ess = nullptr;
   int64_t ess_count = 0;
-  int* flag = nullptr;  // device int used for mesh checks
+  int* flag = nullptr;  // device ints: [0] mesh check bits, [1] largest exponent of D
+  int dexp = 0;         // largest binary exponent of D (from the last geometry pass)
   // FP32 operator data (built on first use): padded FP32 D; tables in constant memory
   float* qd32 = nullptr;
   bool qd32_valid = false;
@@ -383,7 +384,7 @@ int launch_apply64_variant(fepa_op* op, int v, const double* x, double* y, const
   if (v == 1) {
     const int grid = (int)((op->E + k.df_ne - 1) / k.df_ne);
     k.apply_df<<<grid, dim3(k.apply_tpe, k.df_ne), k.df_smem, s>>>((int)op->E, op->gmap, op->qddf, x, y, skip,
-                                                                   nullptr, nullptr);
+                                                                   nullptr, nullptr, op->dexp);
   } else {
     const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
     k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x,
@@ -724,17 +725,20 @@ int ensure_f32(fepa_op* op) {
 // elements per layer
 template <int Q>
 void launch_geom_q(int64_t E, int nx, int ny, const int* econn, const float2* vdf, int diffusion, double* qd,
-                   float2* qddf, float* qd32, int d32stride, int* bad, cudaStream_t s) {
+                   float2* qddf, float* qd32, int d32stride, int* bad, int* dexp, cudaStream_t s) {
   using G = GeoShape<Q>;
   const int grid = (int)((E + G::NE - 1) / G::NE);
-  geom_df<Q><<<grid, dim3(G::TPE, G::NE), 0, s>>>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad);
+  geom_df<Q><<<grid, dim3(G::TPE, G::NE), 0, s>>>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad,
+                                                   dexp);
 }
 
-// the geometry kernel of q (2..10); false if q has none
+// the geometry kernel of q (2..10); false if q has none.  bad[0]: flag bits (1: det J <= 0,
+// 2: outside the double-float set-up's range); dexp (may be null): raised to the largest
+// exponent of D
 bool launch_geom(int q, int64_t E, int nx, int ny, const int* econn, const float2* vdf, int diffusion, double* qd,
-                 float2* qddf, float* qd32, int d32stride, int* bad, cudaStream_t s) {
+                 float2* qddf, float* qd32, int d32stride, int* bad, int* dexp, cudaStream_t s) {
 #define GEOM_CASE(Q) \
-  case Q: launch_geom_q<Q>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad, s); return true;
+  case Q: launch_geom_q<Q>(E, nx, ny, econn, vdf, diffusion, qd, qddf, qd32, d32stride, bad, dexp, s); return true;
   switch (q) {
     GEOM_CASE(2) GEOM_CASE(3) GEOM_CASE(4) GEOM_CASE(5) GEOM_CASE(6) GEOM_CASE(7) GEOM_CASE(8) GEOM_CASE(9)
     GEOM_CASE(10)
@@ -749,12 +753,27 @@ int compute_geometry(fepa_op* op) {
   if (!op->verts_df) TRY(dalloc(&op->verts_df, nv3));
   split_pairs<<<grid_for(nv3, 256, 148 * 8), 256, 0, s>>>(nv3, op->verts, op->verts_df);
   LAUNCH_CHECK();
+  CUDA_TRY(cudaMemsetAsync(op->flag + 1, 0x80, sizeof(int), s));  // D's largest exponent: from -inf
   if (!launch_geom(op->q, op->E, op->nx, op->ny, op->econn, op->verts_df, op->form == FEPA_DIFFUSION, op->qd,
-                   op->qddf, op->qd32, op->ks.d32_stride, op->flag, s))
+                   op->qddf, op->qd32, op->ks.d32_stride, op->flag, op->flag + 1, s))
     return fail(FEPA_ERR_UNSUPPORTED, "q1d %d has no geometry kernel", op->q);
   LAUNCH_CHECK();
   op->qddf_valid = op->qddf != nullptr;
   op->qd32_valid = op->qd32 != nullptr;
+  return FEPA_OK;
+}
+
+// After the geometry kernel: FEPA_ERR_MESH for det J <= 0, FEPA_ERR_UNSUPPORTED outside the
+// double-float set-up's range; records the largest exponent of D for the action's range test.
+int read_mesh_flags(fepa_op* op) {
+  CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, op->stream));
+  CUDA_TRY(cudaStreamSynchronize(op->stream));
+  const int bits = op->st_host_flag[0];
+  op->dexp = op->st_host_flag[1];
+  if (bits & 1) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
+  if (bits & 2)
+    return fail(FEPA_ERR_UNSUPPORTED, "an element lies outside the range of the double-float set-up (extent >= 2^-20, "
+                                      "|coordinates| <= 2^20 and <= 2^10 x extent): translate or rescale the mesh");
   return FEPA_OK;
 }
 
@@ -1159,7 +1178,7 @@ int create_common(fepa_op* op, int32_t p, int32_t q1d, int32_t form, void* strea
   TRY(dalloc(&op->G, (size_t)q * n));
   TRY(dalloc(&op->pts, q));
   TRY(dalloc(&op->wts, q));
-  TRY(dalloc(&op->flag, 1));
+  TRY(dalloc(&op->flag, 2));  // [0] mesh flags, [1] largest exponent of D
   TRY(dalloc(&op->err, 1));
   cudaStream_t s = op->stream;
   CUDA_TRY(cudaMemcpyAsync(op->verts, vertices, 3 * nverts * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1168,17 +1187,14 @@ int create_common(fepa_op* op, int32_t p, int32_t q1d, int32_t form, void* strea
   TRY(upload_df_tables(p, q, Bh, Gh, s));
   CUDA_TRY(cudaMemcpyAsync(op->pts, ph.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(op->wts, wh.data(), q * sizeof(double), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMallocHost((void**)&op->st_host_flag, sizeof(int)));
+  CUDA_TRY(cudaMallocHost((void**)&op->st_host_flag, 2 * sizeof(int)));
   CUDA_TRY(cudaMemsetAsync(op->flag, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(op->err, 0, sizeof(int), s));
   TRY(build_map(op));
   TRY(upload_gauss_df(q, gx, gw, s));
   TRY(compute_geometry(op));
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
-  return FEPA_OK;
+  return read_mesh_flags(op);
 }
 
 }  // namespace
@@ -1268,10 +1284,7 @@ int fepa_op_set_vertices(fepa_op* op, const double* vertices, int32_t on_device)
   TRY(compute_geometry(op));  // refreshes D and its existing copies
   op->inv_diag_valid = false;
   op->inv32_valid = false;
-  CUDA_TRY(cudaMemcpyAsync(op->st_host_flag, op->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (*op->st_host_flag) return fail(FEPA_ERR_MESH, "non-positive Jacobian determinant at a quadrature point");
-  return FEPA_OK;
+  return read_mesh_flags(op);
 }
 
 void fepa_op_destroy(fepa_op* op) { free_op(op); }
@@ -1491,8 +1504,13 @@ static int rhs_common(fepa_op* op, const double* f_qp, double scale, double* b) 
   CUDA_TRY(cudaMemsetAsync(b, 0, op->N * sizeof(double), s));
   const KernelSet& k = op->ks;
   const int grid = (int)((op->E + k.rhs_df_ne - 1) / k.rhs_df_ne);
+  // the sine's amplitude enters as m 2^k (m in [0.5, 1)): m in the kernel, 2^k on the FP64 result, so any
+  // FP64 amplitude keeps the double-float products in range
+  int k2 = 0;
+  const double m = scale != 0.0 && std::isfinite(scale) ? frexp(scale, &k2) : scale;
   k.rhs_df<<<grid, dim3(op->q * op->q, k.rhs_df_ne), k.rhs_df_smem, s>>>(op->E, op->nx, op->ny, op->econn,
-                                                                         op->verts_df, op->gmap, f_qp, scale, b);
+                                                                         op->verts_df, op->gmap, f_qp, m,
+                                                                         ldexp(1.0, k2), b);
   LAUNCH_CHECK();
   return FEPA_OK;
 }

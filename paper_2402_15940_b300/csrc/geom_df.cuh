@@ -33,6 +33,11 @@ __device__ __forceinline__ dfl gauss_wt(int q, int i) {
   return {c_gauss_df[k], c_gauss_df[k + 1]};
 }
 
+// Range of the double-float set-up (geometry, diagonal, load vector), checked per element by
+// geom_df: element extent h >= 2^-20, coordinates |x| <= 2^20 and |x| <= 2^10 h.  Within it D is
+// FP64-accurate to ~2^-38 at worst (~1e-13 on unit-cube meshes of up to 256 elements per side).
+constexpr float GEOM_DF_HMIN = 1.0f / (1 << 20), GEOM_DF_RMAX = (float)(1 << 20), GEOM_DF_RATIO = 1024.f;
+
 template <int Q>
 struct GeoShape {
   static constexpr int TPE = Q * Q;
@@ -43,11 +48,15 @@ struct GeoShape {
 // econn [E][8] when given (unstructured mesh), else from the structured vertex grid of nx x ny
 // elements per layer (corner_vertex).  qd: FP64 D [E][comp][q^3]; qddf (optional): the same
 // as (hi, lo) pairs; qd32 (optional): FP32 D with each component padded to d32stride values.
+// bad: bit 0 set if det J <= 0 somewhere; bit 1 if an element lies outside the range where this
+// double-float arithmetic keeps D to ~1e-13 (GEOM_DF_* below).  dexp (optional): atomically
+// raised to the largest binary exponent of a stored D value (the double-float action's range
+// check uses it).
 template <int Q>
 __global__ void __launch_bounds__(GeoShape<Q>::TPE * GeoShape<Q>::NE)
 geom_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* __restrict__ vdf, int diffusion,
         double* __restrict__ qd, float2* __restrict__ qddf, float* __restrict__ qd32, int d32stride,
-        int* __restrict__ bad) {
+        int* __restrict__ bad, int* __restrict__ dexp) {
   constexpr int TPE = GeoShape<Q>::TPE, NE = GeoShape<Q>::NE, Q3 = Q * Q * Q;
   __shared__ dfl sX[NE][8][3];
   const int tid = threadIdx.x, el = threadIdx.y;
@@ -63,6 +72,19 @@ geom_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* 
   }
   __syncthreads();
   if (!live) return;
+  if (tid == 0) {
+    // The Jacobian comes from differences of corner coordinates held to ~2^-48 of their
+    // magnitude R, so its relative error is ~2^-48 R / h for an element of extent h; det J ~ h^3
+    // and adj(J) adj(J)^T ~ h^4 must also keep their low words in float range.
+    float R = 0.f, h = 0.f;
+    for (int c = 0; c < 8; ++c)
+      for (int d = 0; d < 3; ++d) {
+        R = fmaxf(R, fabsf(sX[el][c][d].h));
+        h = fmaxf(h, fabsf(sX[el][c][d].h - sX[el][0][d].h));
+      }
+    if (!(h >= GEOM_DF_HMIN && R <= GEOM_DF_RMAX && R <= GEOM_DF_RATIO * h)) atomicOr(bad, 2);
+  }
+  int emax = -100000;  // largest exponent of this thread's D values
   const int i = tid % Q, j = tid / Q;
   const dfl one = {1.f, 0.f};
   const dfl s = gauss_pt(Q, i), t = gauss_pt(Q, j);
@@ -135,6 +157,7 @@ geom_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* 
     const int qp = tid + k * TPE;
     if (!diffusion) {
       const dfl v = df_mul(w, det);
+      if (v.h != 0.f) emax = max(emax, ilogbf(v.h));
       qd[e * Q3 + qp] = df_to(v);
       if (qddf) qddf[e * Q3 + qp] = make_float2(v.h, v.l);
       if (qd32) qd32[e * (int64_t)d32stride + qp] = v.h;
@@ -147,12 +170,19 @@ geom_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* 
 #pragma unroll
         for (int c = 0; c < 3; ++c) df_fma(g, A[ra[m]][c], A[rb[m]][c]);
         const dfl v = df_mul(f, df_norm(g));
+        if (v.h != 0.f) emax = max(emax, ilogbf(v.h));
         const int64_t o = (e * 6 + m) * Q3 + qp;
         qd[o] = df_to(v);
         if (qddf) qddf[o] = make_float2(v.h, v.l);
         if (qd32) qd32[(e * 6 + m) * (int64_t)d32stride + qp] = v.h;
       }
     }
+  }
+  if (dexp) {
+    const unsigned mask = __activemask();
+    const int wmax = __reduce_max_sync(mask, emax);
+    if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == __ffs(mask) - 1 && wmax > *(volatile int*)dexp)
+      atomicMax(dexp, wmax);
   }
 }
 
@@ -256,7 +286,8 @@ struct RhsDfShape {
 template <int P, int Q>
 __global__ void __launch_bounds__(RhsDfShape<P, Q>::TPE * RhsDfShape<P, Q>::NE)
 pa_rhs_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2* __restrict__ vdf,
-          const int* __restrict__ gmap, const double* __restrict__ f_qp, double scale, double* __restrict__ b) {
+          const int* __restrict__ gmap, const double* __restrict__ f_qp, double scale, double bscale,
+          double* __restrict__ b) {
   using S = RhsDfShape<P, Q>;
   using T = TabDf<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
@@ -374,7 +405,7 @@ pa_rhs_df(int64_t E, int nx, int ny, const int* __restrict__ econn, const float2
       dfl s = df_zero();
 #pragma unroll
       for (int i = 0; i < Q; ++i) df_fma(s, T::B(i, a), S1[cb * Q + i]);
-      atomicAdd(b + gmap_dof(g[w]), df_to(s));
+      atomicAdd(b + gmap_dof(g[w]), df_to(s) * bscale);
     }
   }
 }

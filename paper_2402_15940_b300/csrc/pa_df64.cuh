@@ -28,6 +28,14 @@ struct __align__(8) dfl {
   float h, l;
 };
 
+// binary exponents for the double-float action's range test (pa_apply_df): a product of
+// exponent e has error terms near 2^(e-48) that must stay normal floats (e >= -70 keeps 8
+// exponents to spare), sums must not overflow (e <= 100), and the gathered values' own low
+// words must stay normal (exponent >= -90)
+constexpr int DF_EXP_LO = -70, DF_EXP_HI = 100, DF_XEXP_LO = -90;
+constexpr int DF_EXP_NONE = -100000;  // no nonzero value seen
+constexpr int DF_EXP_CLAMP = 5000;    // (infinities and NaN clamp here and propagate as such)
+
 __device__ __forceinline__ dfl df_from(double d) {
   const float h = __double2float_rn(d);
   return {h, __double2float_rn(d - (double)h)};
@@ -204,7 +212,7 @@ template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU =
 __global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
 pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
             double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
-            const int* __restrict__ prob_done) {
+            const int* __restrict__ prob_done, int dexp) {
   using S = DfShape<P, Q, DIFF>;
   using L = typename S::L;
   using T = TabDf<P, Q>;
@@ -237,9 +245,17 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   dfl* S1 = sWall + el * L::WORK;
   dfl* S2 = S1 + L::NC1 * L::S1C;
   const int* g = gmap + (e0 + el) * (n * n * n);
+  constexpr int GR = (n * n * n + TPE - 1) / TPE;
+  // Exponent range: a double-float value keeps ~48 bits only while its low word and the
+  // error terms of its products stay normal floats.  The block's largest |x| (exponent bx)
+  // is found with the gather; if bx, or the products' scale bx + dexp (dexp: D's largest
+  // exponent), leaves the DF_EXP_* range, x is re-gathered times 2^-(bx + dexp) and the element
+  // results are multiplied back by 2^(bx + dexp) in FP64 -- exact powers of two.
+  constexpr int NW = (TPE * NE + 31) / 32;
+  __shared__ int s_wexp[NW];
+  int bx_thread = DF_EXP_NONE;
   if (live) {
     // gather: all map loads first, then all x loads, so the dependent pairs overlap
-    constexpr int GR = (n * n * n + TPE - 1) / TPE;
     int gi[GR];
     double xv[GR];
 #pragma unroll
@@ -253,9 +269,38 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     for (int r = 0; r < GR; ++r) {
       const int l = tid + r * TPE;
       if (l < n * n * n) sX[(l / n) * L::XL + l % n] = df_from(xv[r]);
+      if (xv[r] != 0.0) bx_thread = max(bx_thread, min(ilogb(xv[r]), DF_EXP_CLAMP));
     }
   }
+  {
+    const int lin = tid + TPE * el, wbase = lin & ~31;  // (the last warp may be partial)
+    const unsigned wmask = (TPE * NE - wbase >= 32) ? 0xffffffffu : ((1u << (TPE * NE - wbase)) - 1u);
+    const int wx = __reduce_max_sync(wmask, bx_thread);
+    if ((lin & 31) == 0) s_wexp[lin >> 5] = wx;
+  }
   __syncthreads();
+  double yscale = 1.0;  // element results times this
+  {
+    int bx = DF_EXP_NONE;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) bx = max(bx, s_wexp[w]);
+    const int sh = bx + dexp;
+    if (bx != DF_EXP_NONE && (sh > DF_EXP_HI || sh < DF_EXP_LO || bx > DF_EXP_HI || bx < DF_XEXP_LO)) {
+      // rare: rescale (uniform over the block, so the barrier below is reached by all)
+      yscale = ldexp(1.0, sh);
+      if (live) {
+#pragma unroll
+        for (int r = 0; r < GR; ++r) {
+          const int l = tid + r * TPE;
+          if (l < n * n * n) {
+            const int gg = __ldg(g + l);  // (essential DOFs enter as 0, as in the gather above)
+            sX[(l / n) * L::XL + l % n] = df_from(gg >= 0 ? ldexp(__ldg(x + gg), -sh) : 0.0);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
 
   // stage 1 (x): line (b,c) -> S1[m][c][b][i]
   if (live && tid < n * n) {
@@ -658,7 +703,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
       const dfl s = ys[a];
       const int gi = g[a + n * tid];
       if (gi >= 0) {
-        atomicAdd(y + gi, df_to(s));
+        atomicAdd(y + gi, df_to(s) * yscale);
       } else if (!((~gi) & ESS_SKIP)) {
         atomicAdd(y + (~gi), x[~gi]);
       }
