@@ -346,7 +346,9 @@ int fepa_cg_iterations(fepa_op* op, const double* b, double* x, int32_t iters, i
  * products accumulated to FP64 accuracy, except (d, A d), which by default comes out of the
  * FP32 action kernel (fepa_op_set_fused_dot); FP64 scalars) and updates x += e in FP64.
  * When less than inner_rtol is enough to reach rtol (the last correction) the inner
- * tolerance is relaxed to 0.25 rtol ||b|| / ||r||, at most 0.5.
+ * tolerance is relaxed to 0.25 rtol ||b|| / ||r||, at most 0.5.  A residual whose norm has a
+ * binary exponent beyond +-20 enters the FP32 solve scaled by an exact power of two (and the
+ * correction is scaled back), so problems of any FP64 magnitude keep the FP32 loop in range.
  *   b, x        device, N doubles (x: initial guess in, solution out)
  *   rtol        outer stopping rule on the FP64 residual
  *   max_outer   limit on corrections; FEPA_ERR_NOCONV (stats filled) if reached
@@ -369,7 +371,9 @@ int fepa_solve_refined(fepa_op* op, const double* b, double* x, double rtol, int
  *           BP3 (0.03 best); below 1e-3 the FP32 recurrence drifts and convergence stalls
  *   maxit   limit on FP32 iterations in total; FEPA_ERR_NOCONV (stats filled) if reached
  * Stops when ||b - A x||_2 <= rtol ||b||_2 with the FP64 operator.  stats: outer_iterations
- * = replacements, inner_iterations = FP32 iterations.  Blocks until done.
+ * = replacements, inner_iterations = FP32 iterations.  The FP32 recurrence works in units of
+ * a power of two fixed at the first residual (as fepa_solve_refined scales its residuals).
+ * Blocks until done.
  */
 int fepa_solve_reliable(fepa_op* op, const double* b, double* x, double rtol, double delta, int32_t maxit,
                         int32_t precond, fepa_refine_stats* stats);
@@ -499,7 +503,9 @@ typedef struct fepa_batch_refine_stats {
  * inner_maxit iterations, in one CUDA-graph loop over the batch, and x_i += e_i.
  *   b, x        device, total DOFs (x: initial guesses in, solutions out, updated in place)
  *   iterations  host int32 [count]: FP32 iterations of each problem over all steps (may be null)
- * The first call builds an FP32 copy of every group's D (half the FP64 D's size).
+ * The first call builds an FP32 copy of every group's D (half the FP64 D's size).  Unlike
+ * fepa_solve_refined the residuals enter the FP32 loop unscaled: each problem's residual
+ * entries and their products should stay within the float range (about 1e-18 .. 1e18).
  * FEPA_ERR_NOCONV if a problem has not reached rtol after max_outer steps;
  * FEPA_ERR_TIMEOUT if an FP32 action kernel gave up its bounded wait.
  */

@@ -504,9 +504,18 @@ cg32_replace(int64_t N, const float* __restrict__ r, float* __restrict__ e, cons
 }
 
 // x += e (FP64 accumulation of the FP32 correction)
-__global__ void refine_correct(int64_t N, double* __restrict__ x, const float* __restrict__ e) {
+// x += escale e (escale: the power of two the residual was scaled down by, or 1)
+__global__ void refine_correct(int64_t N, double* __restrict__ x, const float* __restrict__ e, double escale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)e[i];
+    x[i] += escale * (double)e[i];
+}
+
+// The residual handed to the FP32 inner solve again, r32 = (b - h) rscale, when its norm is so
+// small or large that FP32 products of it would leave the float range (rscale: a power of two)
+__global__ void refine_rescale(int64_t N, const double* __restrict__ b, const double* __restrict__ h,
+                               float* __restrict__ r32, double rscale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    r32[i] = (float)((b[i] - h[i]) * rscale);
 }
 
 __global__ void to_f32(int64_t N, const double* __restrict__ a, float* __restrict__ out) {

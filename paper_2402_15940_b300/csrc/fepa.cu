@@ -335,6 +335,7 @@ struct fepa_op {
   int sv_status = 0;
   int sv_seen_iter = 0;  // iterations already counted in the launch counter
   double sv_rtol = 0.0, sv_inner_rtol = 0.0, sv_rel = 0.0;
+  double sv_rscale = 1.0;  // power of two the current inner solve's residual was scaled by
   const double* sv_b = nullptr;
   double* sv_x = nullptr;
   cudaEvent_t sv_event = nullptr;
@@ -938,6 +939,16 @@ int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int 
 // Mixed-precision solve: FP64 iterative refinement around an FP32 Jacobi-PCG (the inner
 // tolerance of each step: inner_tol in cg_kernels.cuh).
 
+// Power of two the FP64 residual of norm sqrt(rr) is scaled by before it enters the FP32 inner
+// solve: 1 while its exponent is within +-20 (the common case: nothing to do), else the
+// inverse of 2^exponent, so that FP32 products of the residual stay far from the float range's
+// ends; the correction is scaled back exactly.
+double residual_scale(double rr) {
+  if (!(rr > 0.0) || !std::isfinite(rr)) return 1.0;
+  const int k = ilogb(sqrt(rr));
+  return (k > 20 || k < -20) ? ldexp(1.0, -k) : 1.0;
+}
+
 int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_outer, double inner_rtol,
                 int inner_maxit, int precond, fepa_refine_stats* stats) {
   TRY(check_solve_args(op, b, x, rtol, max_outer, precond));
@@ -983,6 +994,11 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     if (!std::isfinite(href.rr) || !std::isfinite(href.bb)) rel = NAN;
     if (rel <= rtol || outer >= max_outer || std::isnan(rel)) break;
     // FP32 correction: A e = r with relative tolerance inner_rtol (relaxed on the last step)
+    const double rs = residual_scale(href.rr);
+    if (rs != 1.0) {
+      refine_rescale<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, b, op->h64, (float*)L.r, rs);
+      LAUNCH_CHECK();
+    }
     const double tol = inner_tol(inner_rtol, rtol, rel);
     cg32_init<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, (float*)L.r, (float*)L.d,
                                                     (float*)L.h, invd, L.st, tol * tol, inner_maxit, L.partials);
@@ -992,7 +1008,7 @@ int run_refined(fepa_op* op, const double* b, double* x, double rtol, int max_ou
     inner_total += hin.iter;
     cg32_flush<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, (float*)L.x, (const float*)L.d, L.st);
     LAUNCH_CHECK();
-    refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
+    refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x, 1.0 / rs);
     LAUNCH_CHECK();
     ++outer;
   }
@@ -1042,6 +1058,7 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
   auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond, int use_cond) {
     return body32(op, L, invd, bs, cond, use_cond);
   };
+  double rs = 0.0;  // scale of the FP32 recurrence's units, fixed at the first residual
   auto residual = [&](double* rel, double* bb) -> int {  // FP64 r = b - A x into the FP32 loop's r
     CUDA_TRY(cudaMemsetAsync(op->h64, 0, op->N * sizeof(double), s));
     TRY(launch_apply(op, x, op->h64, nullptr, s));
@@ -1053,6 +1070,11 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
     *bb = op->st_host->bb;
     *rel = op->st_host->bb > 0 ? sqrt(op->st_host->rr / op->st_host->bb) : 0.0;
     if (nonfinite(*op->st_host)) *rel = NAN;
+    if (rs == 0.0) rs = residual_scale(op->st_host->rr);
+    if (rs != 1.0) {
+      refine_rescale<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, b, op->h64, (float*)L.r, rs);
+      LAUNCH_CHECK();
+    }
     return FEPA_OK;
   };
   double rel = 0.0, bb = 0.0;
@@ -1071,12 +1093,12 @@ int run_reliable(fepa_op* op, const double* b, double* x, double rtol, double de
       iters = hin.iter;
       cg32_flush<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, (float*)L.x, (const float*)L.d, L.st);
       LAUNCH_CHECK();
-      refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x);
+      refine_correct<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, x, (const float*)L.x, 1.0 / rs);
       LAUNCH_CHECK();
       TRY(residual(&rel, &bb));
       if (rel <= rtol || iters >= maxit || std::isnan(rel)) break;
       cg32_replace<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.x, invd, L.st,
-                                                         delta * delta, floor2, L.partials);
+                                                         delta * delta, floor2 * rs * rs, L.partials);
       LAUNCH_CHECK();
       cg32_direction<<<L.red_blocks, RED_THREADS, 0, s>>>(op->N, (const float*)L.r, (float*)L.d, (float*)L.h, invd,
                                                           nullptr, 0, L.st, 0, 0, nullptr);
@@ -1507,7 +1529,7 @@ static int rhs_common(fepa_op* op, const double* f_qp, double scale, double* b) 
   // the sine's amplitude enters as m 2^k (m in [0.5, 1)): m in the kernel, 2^k on the FP64 result, so any
   // FP64 amplitude keeps the double-float products in range
   int k2 = 0;
-  const double m = scale != 0.0 && std::isfinite(scale) ? frexp(scale, &k2) : scale;
+  const double m = !f_qp && scale != 0.0 && std::isfinite(scale) ? frexp(scale, &k2) : scale;
   k.rhs_df<<<grid, dim3(op->q * op->q, k.rhs_df_ne), k.rhs_df_smem, s>>>(op->E, op->nx, op->ny, op->econn,
                                                                          op->verts_df, op->gmap, f_qp, m,
                                                                          ldexp(1.0, k2), b);
