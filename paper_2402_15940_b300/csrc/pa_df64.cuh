@@ -33,8 +33,11 @@ struct __align__(8) dfl {
 // exponents to spare), sums must not overflow (e <= 100), and the gathered values' own low
 // words must stay normal (exponent >= -90)
 constexpr int DF_EXP_LO = -70, DF_EXP_HI = 100, DF_XEXP_LO = -90;
-constexpr int DF_EXP_NONE = -100000;  // no nonzero value seen
-constexpr int DF_EXP_CLAMP = 5000;    // (infinities and NaN clamp here and propagate as such)
+
+// biased binary exponent field of a double (0 for zero and subnormals, 2047 for inf/NaN)
+__device__ __forceinline__ int f64_exp_field(double v) {
+  return (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff;
+}
 
 __device__ __forceinline__ dfl df_from(double d) {
   const float h = __double2float_rn(d);
@@ -253,7 +256,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   // results are multiplied back by 2^(bx + dexp) in FP64 -- exact powers of two.
   constexpr int NW = (TPE * NE + 31) / 32;
   __shared__ int s_wexp[NW];
-  int bx_thread = DF_EXP_NONE;
+  int bx_thread = 0;  // largest biased exponent field of this thread's x values (0: none)
   if (live) {
     // gather: all map loads first, then all x loads, so the dependent pairs overlap
     int gi[GR];
@@ -269,7 +272,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     for (int r = 0; r < GR; ++r) {
       const int l = tid + r * TPE;
       if (l < n * n * n) sX[(l / n) * L::XL + l % n] = df_from(xv[r]);
-      if (xv[r] != 0.0) bx_thread = max(bx_thread, min(ilogb(xv[r]), DF_EXP_CLAMP));
+      bx_thread = max(bx_thread, f64_exp_field(xv[r]));
     }
   }
   {
@@ -279,13 +282,15 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
     if ((lin & 31) == 0) s_wexp[lin >> 5] = wx;
   }
   __syncthreads();
-  double yscale = 1.0;  // element results times this
+  double yscale = 1.0;     // element results times this ...
+  bool rescaled = false;   // ... when the block rescaled x (block-uniform)
   {
-    int bx = DF_EXP_NONE;
+    int bf = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) bx = max(bx, s_wexp[w]);
-    const int sh = bx + dexp;
-    if (bx != DF_EXP_NONE && (sh > DF_EXP_HI || sh < DF_EXP_LO || bx > DF_EXP_HI || bx < DF_XEXP_LO)) {
+    for (int w = 0; w < NW; ++w) bf = max(bf, s_wexp[w]);
+    const int bx = bf - 1023, sh = bx + dexp;
+    if (bf != 0 && (sh > DF_EXP_HI || sh < DF_EXP_LO || bx > DF_EXP_HI || bx < DF_XEXP_LO)) {
+      rescaled = true;
       // rare: rescale (uniform over the block, so the barrier below is reached by all)
       yscale = ldexp(1.0, sh);
       if (live) {
@@ -703,7 +708,7 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
       const dfl s = ys[a];
       const int gi = g[a + n * tid];
       if (gi >= 0) {
-        atomicAdd(y + gi, df_to(s) * yscale);
+        atomicAdd(y + gi, rescaled ? df_to(s) * yscale : df_to(s));
       } else if (!((~gi) & ESS_SKIP)) {
         atomicAdd(y + (~gi), x[~gi]);
       }
