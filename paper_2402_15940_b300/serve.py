@@ -60,6 +60,15 @@ def device_bytes(req: Request) -> int:
     return int(by * 1.05) + (1 << 20)
 
 
+def estimated_work(req: Request) -> float:
+    """Rough GPU cost of a request for scheduling (not a measurement): DOFs times the Jacobi-PCG
+    iteration count, which grows like p times the elements per side, with an FP32 iteration of
+    the mixed solve counted at a quarter of an FP64 one (the FP32 action moves half the bytes and
+    avoids the FP64-accurate arithmetic)."""
+    its = 4.4 * req.p * max(req.n)
+    return req.ndofs * its * (0.25 if req.precision == "mixed" else 1.0)
+
+
 @dataclasses.dataclass
 class Outcome:
     rid: int
@@ -82,7 +91,13 @@ class Server:
     """Continuous-batching scheduler over an executor (GpuExecutor or FakeExecutor)."""
 
     def __init__(self, executor, hbm_budget: float = 150e9, tick_iters: int = 32, max_active: int = 256,
-                 keep_results: bool = False, clock: Callable[[], float] = time.perf_counter):
+                 keep_results: bool = False, clock: Callable[[], float] = time.perf_counter, policy: str = "fifo"):
+        """policy: "fifo" admits waiting requests in arrival order; "sjf" admits the waiting request
+        with the least estimated work first (shorter waits for short requests when slots or memory
+        are scarce; a request that can never fit is rejected either way)."""
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
         self.ex = executor
         self.budget = float(hbm_budget)
         self.tick_iters = int(tick_iters)
@@ -99,6 +114,8 @@ class Server:
         self.max_concurrent = 0
 
     def _admit(self, now: float):
+        if self.policy == "sjf" and len(self.pending) > 1:
+            self.pending = deque(sorted(self.pending, key=lambda r: (estimated_work(r), r.arrival, r.rid)))
         while self.pending and len(self.active) < self.max_active:
             req = self.pending[0]
             need = device_bytes(req)
@@ -107,7 +124,7 @@ class Server:
                 self.rejected.append(req.rid)
                 continue
             if self.in_use + need > self.budget:
-                break                          # wait for memory to free up (arrival order kept)
+                break                          # wait for memory to free up (queue order kept)
             self.pending.popleft()
             handle = self.ex.start(req)
             self.in_use += need
@@ -154,7 +171,11 @@ class Server:
     def report(self):
         lat = np.array([o.latency for o in self.done]) if self.done else np.zeros(1)
         work = sum(o.ndofs * o.iterations for o in self.done)
+        mem = getattr(self.ex, "measured", [])
         return {"completed": len(self.done), "rejected": len(self.rejected), "makespan_s": self.makespan,
+                "policy": self.policy,
+                "device_bytes_check": {"requests": len(mem),
+                                       "max_measured_over_estimate": max((m / e for m, e in mem), default=None)},
                 "solves_per_s": len(self.done) / self.makespan if self.makespan > 0 else 0.0,
                 "gdofs_per_cg_iter": work / self.makespan / 1e9 if self.makespan > 0 else 0.0,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
@@ -174,18 +195,27 @@ def poisson_arrivals(requests, rate: float, seed: int = 0):
 # ----------------------------------------------------------------------------- executors
 
 class GpuExecutor:
-    """Runs each request as a resident library op on its own CUDA stream."""
+    """Runs each request as a resident library op on its own CUDA stream.  With priorities, a
+    request whose estimated work is below short_work runs on a high-priority stream, so the GPU
+    dispatches its small kernels ahead of the long requests' (shorter latency for short requests;
+    the long ones take the rest of the machine).  Each start measures the device memory the
+    request took (free memory before and after) against device_bytes' estimate."""
 
-    def __init__(self, vertices_fn, inner_rtol: float = 1e-4):
+    def __init__(self, vertices_fn, inner_rtol: float = 1e-4, priorities: bool = True, short_work: float = 5e9):
         import torch
         self.torch = torch
         self.vertices_fn = vertices_fn      # (n, seed) -> vertex array
         self.inner_rtol = inner_rtol
+        self.priorities = priorities
+        self.short_work = short_work
+        self.measured = []                  # (device bytes taken, device_bytes estimate) per request
 
     def start(self, req: Request):
         from .fepa import Operator
         torch = self.torch
-        stream = torch.cuda.Stream()
+        high = self.priorities and estimated_work(req) < self.short_work
+        stream = torch.cuda.Stream(priority=-1 if high else 0)
+        free0 = torch.cuda.mem_get_info()[0]   # (allocations are synchronous: no device sync needed)
         with torch.cuda.stream(stream):
             op = Operator(*req.n, self.vertices_fn(req.n, req.mesh_seed), req.p, form=req.form)
             if req.form == "diffusion":
@@ -196,6 +226,7 @@ class GpuExecutor:
             x = torch.zeros(op.N, dtype=torch.float64, device="cuda")
             op.solver_start(b, x, kind="refined" if req.precision == "mixed" else "cg", rtol=req.rtol,
                             inner_rtol=self.inner_rtol)
+        self.measured.append((max(0, free0 - torch.cuda.mem_get_info()[0]), device_bytes(req)))
         return {"op": op, "stream": stream, "b": b, "x": x}
 
     def advance(self, h, iters: int):

@@ -102,3 +102,6 @@ def test_server_results_same_alone_and_in_the_mix():
         assert rel(o.result, xo) <= 1e-8
     rep = srv.report()
     assert rep["completed"] == len(reqs) and rep["p99_latency_s"] >= rep["p50_latency_s"] > 0
+    # the admission estimate bounds the device memory each request actually took
+    chk = rep["device_bytes_check"]
+    assert chk["requests"] == len(reqs) and chk["max_measured_over_estimate"] <= 1.0, chk

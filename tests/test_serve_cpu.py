@@ -89,3 +89,25 @@ def test_serve_request_generator():
     n = np.array([(x["p"] * x["n"][0] + 1) ** 3 for x in r])
     assert n.min() >= 8 and n.max() < 1.5e7
     assert 0.35 < np.mean([x["precision"] == "mixed" for x in r]) < 0.65
+
+
+def test_sjf_admits_the_least_work_first():
+    # one slot, everything waiting at once: with "sjf" the requests start in order of
+    # estimated work (the arrival order under "fifo")
+    from paper_2402_15940_b300.serve import estimated_work
+    rs = reqs([("diffusion", 4, 12, 0.0), ("diffusion", 4, 12, 0.0), ("mass", 1, 2, 0.0), ("diffusion", 2, 5, 0.0)])
+    for policy, order in (("sjf", sorted(rs, key=lambda r: (estimated_work(r), r.arrival, r.rid))), ("fifo", rs)):
+        ex = FakeExecutor(lambda r: 10)
+        srv = Server(ex, hbm_budget=1e12, tick_iters=4, max_active=1, clock=FakeClock(), policy=policy)
+        srv.run(rs)
+        assert [rid for kind, rid in ex.log if kind == "start"] == [r.rid for r in order]
+    with pytest.raises(ValueError):
+        Server(FakeExecutor(lambda r: 1), policy="lifo")
+
+
+def test_estimated_work_orders_by_size_order_and_precision():
+    from paper_2402_15940_b300.serve import estimated_work
+    a = Request(0, "diffusion", 2, (8, 8, 8), 0)
+    b = Request(1, "diffusion", 4, (8, 8, 8), 0)
+    c = Request(2, "diffusion", 4, (8, 8, 8), 0, precision="mixed")
+    assert estimated_work(a) < estimated_work(b) and estimated_work(c) < estimated_work(b)
