@@ -828,8 +828,8 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
             reqs = [Request(rid=i, form=s["form"], p=s["p"], n=s["n"], mesh_seed=s["mesh_seed"],
                             precision=s["precision"]) for i, s in enumerate(spec)]
             poisson_arrivals(reqs, rate=rate, seed=k)
-            srv = Server(GpuExecutor(vf, priorities=args.serve_priorities), hbm_budget=args.hbm_budget,
-                         tick_iters=args.tick_iters, policy=args.serve_policy)
+            srv = Server(GpuExecutor(vf, priorities=args.serve_priorities, async_start=args.serve_async),
+                         hbm_budget=args.hbm_budget, tick_iters=args.tick_iters, policy=args.serve_policy)
             srv.run(reqs)
             rep = srv.report()
             rep["rate"] = rate
@@ -844,7 +844,7 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
                                        "p~U{1..8}, DOFs log-uniform 1e3..5e6, FP64 or mixed+refine (1/2 each) "
                                        "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
                            "tick_iters": args.tick_iters, "policy": args.serve_policy,
-                           "stream_priorities": args.serve_priorities},
+                           "stream_priorities": args.serve_priorities, "async_start": args.serve_async},
                 "per_rate": per_rate, "gpu_launches": launch_count() - l0, "clocks": clk.summary()}
         if quiet:
             return line
@@ -900,6 +900,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrival rate of the default line's serve run")
     ap.add_argument("--serve-policy", choices=["fifo", "sjf"], default="fifo",
                     help="admission order of waiting requests (arrival order, or least estimated work first)")
+    ap.add_argument("--serve-sync-start", dest="serve_async", action="store_false",
+                    help="build each request's op on the scheduler thread (default: on a worker thread)")
     ap.add_argument("--no-serve-priorities", dest="serve_priorities", action="store_false",
                     help="every request on a normal-priority stream (default: short requests on high-priority ones)")
     args = ap.parse_args()

@@ -45,19 +45,32 @@ class Request:
         return nx * ny * nz
 
 
+def _torch_block(nbytes: int) -> int:
+    """Device memory torch's caching allocator may take for one tensor: a 2 MB segment below
+    1 MB, a 20 MB segment below 10 MB, else the size rounded up to 2 MB."""
+    mb = 1 << 20
+    if nbytes <= mb:
+        return 2 * mb
+    if nbytes <= 10 * mb:
+        return 20 * mb
+    return (nbytes + 2 * mb - 1) // (2 * mb) * (2 * mb)
+
+
 def device_bytes(req: Request) -> int:
     """Upper estimate of the device memory a resident request holds: vertices, element
     map, FP64 D and its (hi, lo) float copy for the double-float action, FP32 D (mixed),
-    the CG work vectors, right-hand side and solution."""
+    the CG work vectors; the right-hand side and solution as torch allocates them; and a
+    fixed 16 MB for the small arrays, graphs and allocation granularity of an op (measured:
+    within it for every request of the served mix once the library is loaded)."""
     n, q, E, N = req.p + 1, req.p + 2, req.nelems, req.ndofs
     ncomp = 6 if req.form == "diffusion" else 1
     nv = (req.n[0] + 1) * (req.n[1] + 1) * (req.n[2] + 1)
     by = 24 * nv + 4 * n ** 3 * E + 2 * 8 * ncomp * q ** 3 * E
-    by += 8 * N * 8                                   # b, x, r, d, h, 1/diag, copies
+    by += 8 * N * 6                                   # r, d, h, 1/diag, copies
     if req.precision == "mixed":
         by += 4 * ncomp * (((q ** 3) + 3) & ~3) * E   # padded FP32 D
         by += 4 * N * 6 + 8 * N                       # FP32 loop vectors, FP64 residual
-    return int(by * 1.05) + (1 << 20)
+    return int(by * 1.1) + 2 * _torch_block(8 * N) + (16 << 20)
 
 
 def estimated_work(req: Request) -> float:
@@ -198,10 +211,14 @@ class GpuExecutor:
     """Runs each request as a resident library op on its own CUDA stream.  With priorities, a
     request whose estimated work is below short_work runs on a high-priority stream, so the GPU
     dispatches its small kernels ahead of the long requests' (shorter latency for short requests;
-    the long ones take the rest of the machine).  Each start measures the device memory the
-    request took (free memory before and after) against device_bytes' estimate."""
+    the long ones take the rest of the machine).  With async_start, a request's op is built (mesh,
+    D, diagonal, solver state: 1-40 ms each on the host, up to ~0.5 s for a new size class) by a
+    worker thread while the scheduler keeps advancing the requests already running; until it is
+    ready the request takes no steps and polls as busy.  Without it, each start also measures the
+    device memory the request took (free memory before and after) against device_bytes."""
 
-    def __init__(self, vertices_fn, inner_rtol: float = 1e-4, priorities: bool = True, short_work: float = 5e9):
+    def __init__(self, vertices_fn, inner_rtol: float = 1e-4, priorities: bool = True, short_work: float = 5e9,
+                 async_start: bool = False, workers: int = 1):
         import torch
         self.torch = torch
         self.vertices_fn = vertices_fn      # (n, seed) -> vertex array
@@ -209,10 +226,32 @@ class GpuExecutor:
         self.priorities = priorities
         self.short_work = short_work
         self.measured = []                  # (device bytes taken, device_bytes estimate) per request
+        self.device = torch.cuda.current_device()
+        self.pool = None
+        if async_start:
+            from concurrent.futures import ThreadPoolExecutor
+            self.pool = ThreadPoolExecutor(max_workers=workers)
 
     def start(self, req: Request):
+        if self.pool is None:
+            return self._create(req)
+        return {"future": self.pool.submit(self._create, req)}
+
+    def _ready(self, h):
+        f = h.get("future")
+        if f is None:
+            return True
+        if not f.done():
+            return False
+        h.update(f.result())    # (re-raises a failed creation)
+        del h["future"]
+        return True
+
+    def _create(self, req: Request):
         from .fepa import Operator
         torch = self.torch
+        if self.pool is not None:
+            torch.cuda.set_device(self.device)   # (the current device is per thread)
         high = self.priorities and estimated_work(req) < self.short_work
         stream = torch.cuda.Stream(priority=-1 if high else 0)
         free0 = torch.cuda.mem_get_info()[0]   # (allocations are synchronous: no device sync needed)
@@ -226,14 +265,19 @@ class GpuExecutor:
             x = torch.zeros(op.N, dtype=torch.float64, device="cuda")
             op.solver_start(b, x, kind="refined" if req.precision == "mixed" else "cg", rtol=req.rtol,
                             inner_rtol=self.inner_rtol)
-        self.measured.append((max(0, free0 - torch.cuda.mem_get_info()[0]), device_bytes(req)))
+        if self.pool is None:   # (other threads' allocations would blur the difference)
+            self.measured.append((max(0, free0 - torch.cuda.mem_get_info()[0]), device_bytes(req)))
         return {"op": op, "stream": stream, "b": b, "x": x}
 
     def advance(self, h, iters: int):
+        if not self._ready(h):
+            return
         with self.torch.cuda.stream(h["stream"]):
             h["op"].solver_advance(iters)
 
     def poll(self, h):
+        if not self._ready(h):
+            return None
         with self.torch.cuda.stream(h["stream"]):
             return h["op"].solver_poll(blocking=False)
 
@@ -242,6 +286,8 @@ class GpuExecutor:
             return h["x"].cpu().numpy()
 
     def release(self, h):
+        if "future" in h:
+            h.update(h.pop("future").result())
         h["stream"].synchronize()
         h["op"].close()
         h.clear()
