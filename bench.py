@@ -829,7 +829,8 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
                             precision=s["precision"]) for i, s in enumerate(spec)]
             poisson_arrivals(reqs, rate=rate, seed=k)
             srv = Server(GpuExecutor(vf, priorities=args.serve_priorities, async_start=args.serve_async),
-                         hbm_budget=args.hbm_budget, tick_iters=args.tick_iters, policy=args.serve_policy)
+                         hbm_budget=args.hbm_budget, tick_iters=args.tick_iters, policy=args.serve_policy,
+                         tick_seconds=args.tick_seconds if args.tick_seconds > 0 else None)
             srv.run(reqs)
             rep = srv.report()
             rep["rate"] = rate
@@ -844,7 +845,8 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
                                        "p~U{1..8}, DOFs log-uniform 1e3..5e6, FP64 or mixed+refine (1/2 each) "
                                        "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
                            "tick_iters": args.tick_iters, "policy": args.serve_policy,
-                           "stream_priorities": args.serve_priorities, "async_start": args.serve_async},
+                           "stream_priorities": args.serve_priorities, "async_start": args.serve_async,
+                           "tick_seconds": args.tick_seconds},
                 "per_rate": per_rate, "gpu_launches": launch_count() - l0, "clocks": clk.summary()}
         if quiet:
             return line
@@ -884,6 +886,8 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--hbm-budget", type=float, default=150e9)
     ap.add_argument("--tick-iters", type=int, default=32)
+    ap.add_argument("--tick-seconds", type=float, default=2e-3,
+                    help="serve: estimated GPU time per advance of a request (0: always --tick-iters)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--target-err", type=float, default=1e-10,

@@ -104,10 +104,14 @@ class Server:
     """Continuous-batching scheduler over an executor (GpuExecutor or FakeExecutor)."""
 
     def __init__(self, executor, hbm_budget: float = 150e9, tick_iters: int = 32, max_active: int = 256,
-                 keep_results: bool = False, clock: Callable[[], float] = time.perf_counter, policy: str = "fifo"):
+                 keep_results: bool = False, clock: Callable[[], float] = time.perf_counter, policy: str = "fifo",
+                 tick_seconds: Optional[float] = None):
         """policy: "fifo" admits waiting requests in arrival order; "sjf" admits the waiting request
         with the least estimated work first (shorter waits for short requests when slots or memory
-        are scarce; a request that can never fit is rejected either way)."""
+        are scarce; a request that can never fit is rejected either way).  tick_seconds: if set, a
+        request advances by enough iterations per tick for about this much estimated GPU time (at
+        least tick_iters, at most 4096); else by tick_iters."""
+        self.tick_seconds = tick_seconds
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
         self.policy = policy
@@ -125,6 +129,7 @@ class Server:
         self.rejected: list = []
         self.ticks = 0
         self.max_concurrent = 0
+        self.inflight: dict = {}     # rid -> an advance of the request may still be running
 
     def _admit(self, now: float):
         if self.policy == "sjf" and len(self.pending) > 1:
@@ -145,13 +150,27 @@ class Server:
             self.active[req.rid] = (req, handle, need, now)
         self.max_concurrent = max(self.max_concurrent, len(self.active))
 
+    def tick_size(self, req: Request) -> int:
+        """Iterations per advance: tick_iters, or with tick_seconds enough for about that much GPU
+        time (estimated from the DOFs), so the host's per-tick round trip stays small next to it."""
+        if self.tick_seconds is None:
+            return self.tick_iters
+        per_it = req.ndofs / (25e9 if req.precision == "mixed" else 6e9)
+        return int(min(4096, max(self.tick_iters, self.tick_seconds / max(per_it, 1e-12))))
+
     def _tick(self):
+        advanced = 0
         for rid, (req, h, need, adm) in self.active.items():
-            self.ex.advance(h, self.tick_iters)
+            if not self.inflight.get(rid):   # one advance in flight per request: no queue flooding
+                self.ex.advance(h, self.tick_size(req))
+                self.inflight[rid] = True
+                advanced += 1
         self.ticks += 1
         finished = []
         for rid, (req, h, need, adm) in self.active.items():
             st = self.ex.poll(h)
+            if st is not None:
+                self.inflight[rid] = False
             if st is not None and st["done"]:
                 finished.append(rid)
                 res = self.ex.result(h) if self.keep_results else None
@@ -160,8 +179,11 @@ class Server:
                                          req.ndofs, res))
         for rid in finished:
             req, h, need, adm = self.active.pop(rid)
+            self.inflight.pop(rid, None)
             self.ex.release(h)
             self.in_use -= need
+        if not advanced and not finished:
+            time.sleep(50e-6)   # everything is busy on the device: let other threads run
 
     def run(self, requests):
         """Serve `requests` (arrival times relative to the start); returns the outcomes."""

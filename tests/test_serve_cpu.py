@@ -111,3 +111,40 @@ def test_estimated_work_orders_by_size_order_and_precision():
     b = Request(1, "diffusion", 4, (8, 8, 8), 0)
     c = Request(2, "diffusion", 4, (8, 8, 8), 0, precision="mixed")
     assert estimated_work(a) < estimated_work(b) and estimated_work(c) < estimated_work(b)
+
+
+def test_one_advance_in_flight_per_request():
+    # while a request's last advance is still running (poll returns None) the scheduler does not
+    # queue another one; it resumes once the poll reports a state
+    class BusyFake(FakeExecutor):
+        def __init__(self):
+            super().__init__(lambda r: 40)
+            self.busy_left = {}
+            self.advances = 0
+
+        def advance(self, h, iters):
+            assert self.busy_left.get(h["req"].rid, 0) == 0, "advanced while busy"
+            self.advances += 1
+            self.busy_left[h["req"].rid] = 3
+            super().advance(h, iters)
+
+        def poll(self, h):
+            rid = h["req"].rid
+            if self.busy_left.get(rid, 0) > 0:
+                self.busy_left[rid] -= 1
+                return None
+            return super().poll(h)
+
+    ex = BusyFake()
+    srv = Server(ex, hbm_budget=1e12, tick_iters=8, clock=FakeClock())
+    out = srv.run(reqs([("diffusion", 2, 4, 0.0), ("mass", 3, 3, 0.0)]))
+    assert len(out) == 2 and all(o.iterations == 40 for o in out)
+    assert ex.advances == 2 * 5          # 40 iterations in advances of 8, nothing extra queued
+
+
+def test_tick_size_scales_with_the_request():
+    srv = Server(FakeExecutor(lambda r: 1), tick_iters=16, tick_seconds=2e-3)
+    small = Request(0, "mass", 2, (4, 4, 4), 0)
+    big = Request(1, "diffusion", 4, (48, 48, 48), 0)
+    assert srv.tick_size(small) == 4096 and 16 <= srv.tick_size(big) < 4096
+    assert Server(FakeExecutor(lambda r: 1), tick_iters=16).tick_size(big) == 16
