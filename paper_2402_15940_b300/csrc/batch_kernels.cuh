@@ -1,10 +1,12 @@
 // Batched Jacobi-PCG over many independent problems at once (one concatenated vector,
-// per-problem scalars).  Every reduction block covers a chunk of exactly one problem
-// (the chunk table below); the last block to finish sums each problem's block partials
-// in a fixed order and updates that problem's scalars, so a problem's iterates do not
-// depend on which other problems share the batch (up to the atomic order of G^T).
-// Converged problems are skipped by every kernel; the loop runs inside one CUDA graph
-// while-node until the last problem stops.
+// per-problem scalars).  The DOFs are cut into chunks of one problem each (the chunk table
+// below); every reduction writes one partial per chunk and the last block to finish sums each
+// problem's chunk partials in a fixed order and updates that problem's scalars, so a problem's
+// iterates do not depend on which other problems share the batch (up to the atomic order of
+// G^T).  The kernels are persistent: a fixed grid walks its chunks (or, inside the iteration
+// loop, only the chunks of problems still running, from a work list), so finished problems
+// cost no block launches; the loop runs inside one CUDA graph while-node until the last
+// problem stops.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,15 +28,59 @@ struct BGlobal {  // whole batch
 };
 
 struct ChunkTable {
-  const int* blk_prob;     // [nblocks] problem of each reduction block
-  const int64_t* blk_lo;   // [nblocks] first DOF (concatenated numbering)
-  const int64_t* blk_hi;   // [nblocks] one past the last DOF
-  const int* pb_first;     // [nprob] first block of each problem
-  const int* pb_count;     // [nprob] blocks of each problem
+  const int* blk_prob;     // [nchunks] problem of each chunk
+  const int64_t* blk_lo;   // [nchunks] first DOF (concatenated numbering)
+  const int64_t* blk_hi;   // [nchunks] one past the last DOF
+  const int* pb_first;     // [nprob] first chunk of each problem
+  const int* pb_count;     // [nprob] chunks of each problem
   int nprob;
+  int nchunks;
+  const int* act;          // the chunks of running problems (work list; null: every chunk)
+  const int* nact;         // its length
 };
 
-// Sum, per problem, the NV block partials of its blocks (called by the last block);
+// Work lists of the iteration loop, rebuilt whenever the set of running problems changes: the
+// chunks of running problems, and per group the element tiles (of one problem each) of running
+// problems, for the persistent operator kernels
+struct WorkLists {
+  int* act_chunks;          // [nchunks]
+  int* n_act_chunks;        // [1]
+  int ngroups;
+  const int* prob_group;    // [nprob] group of each problem
+  const int* tile_first;    // [nprob] first tile of the problem in its group's tile table
+  const int* tile_count;    // [nprob] its tiles
+  const int* tile_off;      // [ngroups] start of group g's list in act_tiles
+  int* act_tiles;           // per group: tile ids of running problems
+  int* n_act_tiles;         // [ngroups]
+};
+
+__device__ __forceinline__ int chunk_count(const ChunkTable& t) { return t.act ? *t.nact : t.nchunks; }
+__device__ __forceinline__ int chunk_at(const ChunkTable& t, int i) { return t.act ? t.act[i] : i; }
+
+// Block-reduce this block's NV values over one chunk and store them as the chunk's partials
+template <int NV>
+__device__ __forceinline__ void store_chunk(double (&v)[NV], double* partials, int nchunks, int chunk) {
+  double blk[NV];
+  block_sum<NV>(v, blk);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * nchunks + chunk] = blk[k];
+  }
+  __syncthreads();  // (block_sum's shared slots are reused by the next chunk)
+}
+
+// True (in every thread) in the last block to finish; every chunk partial is then visible to it
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return last;
+}
+
+// Sum, per problem, the NV chunk partials of its chunks (called by the last block);
 // f(j, sums) receives problem j's totals.  Returns the number of problems f reports
 // as active, summed over the block (valid in every thread after the call).
 template <int NV, typename F>
@@ -48,7 +94,7 @@ __device__ __forceinline__ int per_problem(const ChunkTable& t, const double* pa
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       s[k] = 0.0;
-      for (int b = t.pb_first[j]; b < t.pb_first[j] + t.pb_count[j]; ++b) s[k] += __ldcg(partials + k * gridDim.x + b);
+      for (int b = t.pb_first[j]; b < t.pb_first[j] + t.pb_count[j]; ++b) s[k] += __ldcg(partials + k * t.nchunks + b);
     }
     mine += f(j, s) ? 1 : 0;
   }
@@ -57,26 +103,46 @@ __device__ __forceinline__ int per_problem(const ChunkTable& t, const double* pa
   return active;
 }
 
+// Rebuild the work lists from pdone (called by one whole block; w.act_chunks null: no lists)
+__device__ __forceinline__ void rebuild_lists(const ChunkTable& t, const WorkLists& w, const int* pdone) {
+  if (!w.act_chunks) return;
+  if (threadIdx.x == 0) *w.n_act_chunks = 0;
+  for (int g = threadIdx.x; g < w.ngroups; g += blockDim.x) w.n_act_tiles[g] = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < t.nprob; j += blockDim.x) {
+    if (__ldcg(pdone + j)) continue;
+    const int nc = t.pb_count[j];
+    const int cb = atomicAdd(w.n_act_chunks, nc);
+    for (int c = 0; c < nc; ++c) w.act_chunks[cb + c] = t.pb_first[j] + c;
+    const int g = w.prob_group[j], nt = w.tile_count[j];
+    int* dst = w.act_tiles + w.tile_off[g] + atomicAdd(w.n_act_tiles + g, nt);
+    for (int k = 0; k < nt; ++k) dst[k] = w.tile_first[j] + k;
+  }
+  __threadfence();
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
-bcg_init(ChunkTable t, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ d,
+bcg_init(ChunkTable t, WorkLists w, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ d,
          double* __restrict__ h, const double* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
          double rtol2, int maxit, double* partials) {
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const double bi = b[i];
-    const double ri = bi - h[i];
-    const double zi = inv_diag ? ri * inv_diag[i] : ri;
-    r[i] = ri;
-    d[i] = zi;
-    h[i] = 0.0;
-    v[0] += zi * ri;
-    v[1] += ri * ri;
-    v[2] += bi * bi;
+  for (int ic = blockIdx.x; ic < t.nchunks; ic += gridDim.x) {
+    const int64_t lo = t.blk_lo[ic], hi = t.blk_hi[ic];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double bi = b[i];
+      const double ri = bi - h[i];
+      const double zi = inv_diag ? ri * inv_diag[i] : ri;
+      r[i] = ri;
+      d[i] = zi;
+      h[i] = 0.0;
+      v[0] += zi * ri;
+      v[1] += ri * ri;
+      v[2] += bi * bi;
+    }
+    store_chunk<3>(v, partials, t.nchunks, ic);
   }
-  double blk[3];
-  block_sum<3>(v, blk);
-  if (publish_partials<3>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     const int active = per_problem<3>(t, partials, [&](int j, const double* s) {
       BState& q = ps[j];
       q.rho = s[0];
@@ -90,6 +156,7 @@ bcg_init(ChunkTable t, const double* __restrict__ b, double* __restrict__ r, dou
       pdone[j] = q.converged || !isfinite(s[1]) || !isfinite(s[2]);  // NaN/inf: stop at once
       return !pdone[j];
     });
+    rebuild_lists(t, w, pdone);
     if (threadIdx.x == 0) {
       gs->active = active;
       gs->done = active == 0;
@@ -102,15 +169,17 @@ __global__ void __launch_bounds__(RED_THREADS)
 bcg_dot_dh(ChunkTable t, const double* __restrict__ d, const double* __restrict__ h, BState* ps,
            const int* __restrict__ pdone, BGlobal* gs, double* partials) {
   if (gs->done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  double v[1] = {0.0};
-  if (!pdone[prob]) {
-    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v[0] += d[i] * h[i];
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    double v[1] = {0.0};
+    if (!pdone[t.blk_prob[c]]) {
+      const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v[0] += d[i] * h[i];
+    }
+    store_chunk<1>(v, partials, t.nchunks, c);
   }
-  double blk[1];
-  block_sum<1>(v, blk);
-  if (publish_partials<1>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     per_problem<1>(t, partials, [&](int j, const double* s) {
       if (!pdone[j]) ps[j].alpha = ps[j].rho / s[0];
       return false;
@@ -120,27 +189,33 @@ bcg_dot_dh(ChunkTable t, const double* __restrict__ d, const double* __restrict_
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
-bcg_update(ChunkTable t, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
+bcg_update(ChunkTable t, WorkLists w, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
            const double* __restrict__ h, const double* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
            double* partials) {
   if (gs->done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  double v[2] = {0.0, 0.0};
-  if (!pdone[prob]) {
-    const double alpha = ps[prob].alpha;
-    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      x[i] += alpha * d[i];
-      const double ri = r[i] - alpha * h[i];
-      r[i] = ri;
-      const double zi = inv_diag ? ri * inv_diag[i] : ri;
-      v[0] += zi * ri;
-      v[1] += ri * ri;
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    const int prob = t.blk_prob[c];
+    double v[2] = {0.0, 0.0};
+    if (!pdone[prob]) {
+      const double alpha = ps[prob].alpha;
+      const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        x[i] += alpha * d[i];
+        const double ri = r[i] - alpha * h[i];
+        r[i] = ri;
+        const double zi = inv_diag ? ri * inv_diag[i] : ri;
+        v[0] += zi * ri;
+        v[1] += ri * ri;
+      }
     }
+    store_chunk<2>(v, partials, t.nchunks, c);
   }
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
+    __shared__ int stopped;
+    if (threadIdx.x == 0) stopped = 0;
+    __syncthreads();
     const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
       if (pdone[j]) return false;
       BState& q = ps[j];
@@ -156,8 +231,10 @@ bcg_update(ChunkTable t, double* __restrict__ x, double* __restrict__ r, const d
       q.beta = s[0] / q.rho;
       q.rho = s[0];
       pdone[j] = stop;
+      if (stop) stopped = 1;
       return !stop;
     });
+    if (stopped) rebuild_lists(t, w, pdone);  // (block-uniform after per_problem's barrier)
     if (threadIdx.x == 0) {
       gs->active = active;
       gs->done = active == 0;
@@ -174,14 +251,18 @@ bcg_direction(ChunkTable t, const double* __restrict__ r, double* __restrict__ d
   const int done = gs->done;
   if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
   if (done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  if (pdone[prob]) return;
-  const double beta = ps[prob].beta;
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const double zi = inv_diag ? r[i] * inv_diag[i] : r[i];
-    d[i] = zi + beta * d[i];
-    h[i] = 0.0;
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    const int prob = t.blk_prob[c];
+    if (pdone[prob]) continue;
+    const double beta = ps[prob].beta;
+    const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+      d[i] = zi + beta * d[i];
+      h[i] = 0.0;
+    }
   }
 }
 
@@ -196,18 +277,19 @@ bcg_direction(ChunkTable t, const double* __restrict__ r, double* __restrict__ d
 __global__ void __launch_bounds__(RED_THREADS)
 bref_residual(ChunkTable t, const double* __restrict__ b, const double* __restrict__ h, float* __restrict__ r32,
               BState* pr, int* pdone, BGlobal* gs, double rtol2, double* partials) {
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  double v[2] = {0.0, 0.0};
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const double bi = b[i];
-    const double ri = bi - h[i];
-    r32[i] = (float)ri;
-    v[0] += ri * ri;
-    v[1] += bi * bi;
+  for (int ic = blockIdx.x; ic < t.nchunks; ic += gridDim.x) {
+    const int64_t lo = t.blk_lo[ic], hi = t.blk_hi[ic];
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double bi = b[i];
+      const double ri = bi - h[i];
+      r32[i] = (float)ri;
+      v[0] += ri * ri;
+      v[1] += bi * bi;
+    }
+    store_chunk<2>(v, partials, t.nchunks, ic);
   }
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
       BState& q = pr[j];
       q.rr = s[0];
@@ -229,24 +311,25 @@ bref_residual(ChunkTable t, const double* __restrict__ b, const double* __restri
 // tol = inner_tol(inner_rtol, rtol, its outer residual) -- or, for the reliable-update solve
 // (delta2 > 0), the first segment's stop at rr <= max(delta2 ||r||^2, rtol^2 ||b||^2 / 4).
 __global__ void __launch_bounds__(RED_THREADS)
-bcg32_init(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, float* __restrict__ d,
+bcg32_init(ChunkTable t, WorkLists w, const float* __restrict__ r, float* __restrict__ e, float* __restrict__ d,
            float* __restrict__ h, const float* __restrict__ inv_diag, BState* ps, const BState* __restrict__ pr,
            int* pdone, BGlobal* gs, double inner_rtol, double rtol, int maxit, double delta2, double* partials) {
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float ri = r[i];
-    const float zi = inv_diag ? ri * inv_diag[i] : ri;
-    e[i] = 0.f;
-    d[i] = zi;
-    h[i] = 0.f;
-    f2_add_prod(zr_h, zr_l, zi, ri);
-    f2_add_prod(rr_h, rr_l, ri, ri);
+  for (int ic = blockIdx.x; ic < t.nchunks; ic += gridDim.x) {
+    const int64_t lo = t.blk_lo[ic], hi = t.blk_hi[ic];
+    float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const float ri = r[i];
+      const float zi = inv_diag ? ri * inv_diag[i] : ri;
+      e[i] = 0.f;
+      d[i] = zi;
+      h[i] = 0.f;
+      f2_add_prod(zr_h, zr_l, zi, ri);
+      f2_add_prod(rr_h, rr_l, ri, ri);
+    }
+    double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+    store_chunk<2>(v, partials, t.nchunks, ic);
   }
-  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
       BState& q = ps[j];
       q.iter = 0;
@@ -272,6 +355,7 @@ bcg32_init(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, flo
       pdone[j] = q.converged;
       return !q.converged;
     });
+    rebuild_lists(t, w, pdone);
     if (threadIdx.x == 0) {
       gs->active = active;
       gs->done = active == 0;
@@ -284,16 +368,18 @@ __global__ void __launch_bounds__(RED_THREADS)
 bcg32_dot_dh(ChunkTable t, const float* __restrict__ d, const float* __restrict__ h, BState* ps,
              const int* __restrict__ pdone, BGlobal* gs, double* partials) {
   if (gs->done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  float s_h = 0.f, s_l = 0.f;
-  if (!pdone[prob]) {
-    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) f2_add_prod(s_h, s_l, d[i], h[i]);
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    float s_h = 0.f, s_l = 0.f;
+    if (!pdone[t.blk_prob[c]]) {
+      const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) f2_add_prod(s_h, s_l, d[i], h[i]);
+    }
+    double v[1] = {f2_value(s_h, s_l)};
+    store_chunk<1>(v, partials, t.nchunks, c);
   }
-  double v[1] = {f2_value(s_h, s_l)};
-  double blk[1];
-  block_sum<1>(v, blk);
-  if (publish_partials<1>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     per_problem<1>(t, partials, [&](int j, const double* s) {
       if (!pdone[j]) ps[j].alpha = ps[j].rho / s[0];
       return false;
@@ -303,28 +389,34 @@ bcg32_dot_dh(ChunkTable t, const float* __restrict__ d, const float* __restrict_
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
-bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const float* __restrict__ d,
+bcg32_update(ChunkTable t, WorkLists w, float* __restrict__ e, float* __restrict__ r, const float* __restrict__ d,
              const float* __restrict__ h, const float* __restrict__ inv_diag, BState* ps, int* pdone, BGlobal* gs,
              double* partials) {
   if (gs->done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
-  if (!pdone[prob]) {
-    const float alpha = (float)ps[prob].alpha;
-    const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      e[i] = fmaf(alpha, d[i], e[i]);
-      const float ri = fmaf(-alpha, h[i], r[i]);
-      r[i] = ri;
-      const float zi = inv_diag ? ri * inv_diag[i] : ri;
-      f2_add_prod(zr_h, zr_l, zi, ri);
-      f2_add_prod(rr_h, rr_l, ri, ri);
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    const int prob = t.blk_prob[c];
+    float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+    if (!pdone[prob]) {
+      const float alpha = (float)ps[prob].alpha;
+      const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        e[i] = fmaf(alpha, d[i], e[i]);
+        const float ri = fmaf(-alpha, h[i], r[i]);
+        r[i] = ri;
+        const float zi = inv_diag ? ri * inv_diag[i] : ri;
+        f2_add_prod(zr_h, zr_l, zi, ri);
+        f2_add_prod(rr_h, rr_l, ri, ri);
+      }
     }
+    double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+    store_chunk<2>(v, partials, t.nchunks, c);
   }
-  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
+    __shared__ int stopped;
+    if (threadIdx.x == 0) stopped = 0;
+    __syncthreads();
     const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
       if (pdone[j]) return false;
       BState& q = ps[j];
@@ -340,8 +432,10 @@ bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const f
       q.beta = s[0] / q.rho;
       q.rho = s[0];
       pdone[j] = stop;
+      if (stop) stopped = 1;
       return !stop;
     });
+    if (stopped) rebuild_lists(t, w, pdone);  // (block-uniform after per_problem's barrier)
     if (threadIdx.x == 0) {
       gs->active = active;
       gs->done = active == 0;
@@ -356,22 +450,23 @@ bcg32_update(ChunkTable t, float* __restrict__ e, float* __restrict__ r, const f
 // rescaled so that the next direction continues its recurrence (d = z + rho / rho_prev d),
 // and its next stop at rr <= max(delta2 rr, rtol^2 ||b||^2 / 4); the others stop.
 __global__ void __launch_bounds__(RED_THREADS)
-bcg32_replace(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, const float* __restrict__ inv_diag,
-              BState* ps, const BState* __restrict__ pr, int* pdone, BGlobal* gs, double delta2, double rtol,
-              double* partials) {
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float ri = r[i];
-    const float zi = inv_diag ? ri * inv_diag[i] : ri;
-    e[i] = 0.f;
-    f2_add_prod(zr_h, zr_l, zi, ri);
-    f2_add_prod(rr_h, rr_l, ri, ri);
+bcg32_replace(ChunkTable t, WorkLists w, const float* __restrict__ r, float* __restrict__ e,
+              const float* __restrict__ inv_diag, BState* ps, const BState* __restrict__ pr, int* pdone, BGlobal* gs,
+              double delta2, double rtol, double* partials) {
+  for (int ic = blockIdx.x; ic < t.nchunks; ic += gridDim.x) {
+    const int64_t lo = t.blk_lo[ic], hi = t.blk_hi[ic];
+    float zr_h = 0.f, zr_l = 0.f, rr_h = 0.f, rr_l = 0.f;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const float ri = r[i];
+      const float zi = inv_diag ? ri * inv_diag[i] : ri;
+      e[i] = 0.f;
+      f2_add_prod(zr_h, zr_l, zi, ri);
+      f2_add_prod(rr_h, rr_l, ri, ri);
+    }
+    double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
+    store_chunk<2>(v, partials, t.nchunks, ic);
   }
-  double v[2] = {f2_value(zr_h, zr_l), f2_value(rr_h, rr_l)};
-  double blk[2];
-  block_sum<2>(v, blk);
-  if (publish_partials<2>(blk, partials, &gs->ticket)) {
+  if (last_block(&gs->ticket)) {
     const int active = per_problem<2>(t, partials, [&](int j, const double* s) {
       BState& q = ps[j];
       if (pdone[j] || q.iter >= q.maxit) {
@@ -386,6 +481,7 @@ bcg32_replace(ChunkTable t, const float* __restrict__ r, float* __restrict__ e, 
       q.converged = 0;
       return true;
     });
+    rebuild_lists(t, w, pdone);
     if (threadIdx.x == 0) {
       gs->active = active;
       gs->done = active == 0;
@@ -402,14 +498,18 @@ bcg32_direction(ChunkTable t, const float* __restrict__ r, float* __restrict__ d
   const int done = gs->done;
   if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
   if (done) return;
-  const int prob = t.blk_prob[blockIdx.x];
-  if (pdone[prob]) return;
-  const float beta = (float)ps[prob].beta;
-  const int64_t lo = t.blk_lo[blockIdx.x], hi = t.blk_hi[blockIdx.x];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
-    d[i] = fmaf(beta, d[i], zi);
-    h[i] = 0.f;
+  const int nc = chunk_count(t);
+  for (int ic = blockIdx.x; ic < nc; ic += gridDim.x) {
+    const int c = chunk_at(t, ic);
+    const int prob = t.blk_prob[c];
+    if (pdone[prob]) continue;
+    const float beta = (float)ps[prob].beta;
+    const int64_t lo = t.blk_lo[c], hi = t.blk_hi[c];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const float zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+      d[i] = fmaf(beta, d[i], zi);
+      h[i] = 0.f;
+    }
   }
 }
 

@@ -211,11 +211,13 @@ struct DfTune {
   static constexpr bool EO3 = DIFF ? (P == 3 || P == 4 || P == 8) : (P >= 2);
 };
 
-template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
-__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
-pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
-            double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
-            const int* __restrict__ prob_done, int dexp) {
+// The block's work on one tile of ne <= NE consecutive elements starting at e0 (called once per
+// block by pa_apply_df, or per tile of a work list by pa_apply_df_tiles)
+template <int P, int Q, bool DIFF, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
+__device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restrict__ gmap,
+                                        const float2* __restrict__ qd, const double* __restrict__ x,
+                                        double* __restrict__ y, const int* __restrict__ elem_prob,
+                                        const int* __restrict__ prob_done, int dexp) {
   using S = DfShape<P, Q, DIFF>;
   using L = typename S::L;
   using T = TabDf<P, Q>;
@@ -229,13 +231,10 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
   using EBT = TabEo<P, 2>;
   using EGT = TabEo<P, 3>;
   static_assert(DQ1 * n * n <= L::S1C, "S1 component size");
-  if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_df[];
   dfl* sXall = reinterpret_cast<dfl*>(smem_df);
   dfl* sWall = sXall + NE * L::XSZ;
   const int tid = threadIdx.x, el = threadIdx.y;
-  const int64_t e0 = (int64_t)blockIdx.x * NE;
-  const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
   // L2 prefetch of the group's D and map (batched problems: not when the problems of the
   // group's first and last elements have converged)
   if (PF > 0 && tid == 0 && el == 0 &&
@@ -713,6 +712,32 @@ pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, 
         atomicAdd(y + (~gi), x[~gi]);
       }
     }
+  }
+}
+
+template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
+pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
+            double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
+            const int* __restrict__ prob_done, int dexp) {
+  constexpr int NE = DfShape<P, Q, DIFF>::NE;
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  df_tile<P, Q, DIFF, KU, PF>(e0, (int)((E - e0) < NE ? (E - e0) : NE), gmap, qd, x, y, elem_prob, prob_done, dexp);
+}
+
+// Persistent form over a work list (the batch's iteration loop), as pa_apply_f32_tiles
+template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
+pa_apply_df_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, const int* __restrict__ nact,
+                  const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
+                  double* __restrict__ y, const int* __restrict__ skip, int dexp) {
+  if (skip && *skip) return;
+  const int count = *nact;
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int2 tl = tiles[act[i]];
+    df_tile<P, Q, DIFF>(tl.x, tl.y, gmap, qd, x, y, nullptr, nullptr, dexp);
+    __syncthreads();  // (the next tile reuses the shared buffers)
   }
 }
 

@@ -150,14 +150,15 @@ struct PaShape {
 // transposed y and x stages follow through shared memory, and the result is
 // scatter-added to y (G^T).  R is the arithmetic type: double for the FP64 operator,
 // float for the FP32 operator of the mixed-precision solve (D, tables, x, y all in R).
+// The block's work on a tile of ne <= NE consecutive elements from e0 (called once per block by
+// pa_apply, or per tile of a work list by pa_apply_tiles)
 template <typename R, int P, int Q, bool DIFF>
-__global__ void __launch_bounds__(PaShape<R, P, Q, DIFF>::TPE * PaShape<R, P, Q, DIFF>::NE)
-pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R* __restrict__ Btab,
-         const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip,
-         const int* __restrict__ elem_prob, const int* __restrict__ prob_done) {
+__device__ __forceinline__ void pa_tile(int64_t e0, int ne, const int* __restrict__ gmap, const R* __restrict__ qd,
+                                        const R* __restrict__ Btab, const R* __restrict__ Gtab,
+                                        const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ elem_prob,
+                                        const int* __restrict__ prob_done) {
   using S = PaShape<R, P, Q, DIFF>;
   constexpr int n = S::N, T = S::TPE;
-  if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* smem = reinterpret_cast<R*>(smem_raw);
   R* sB = smem;
@@ -166,9 +167,9 @@ pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R*
   R* S1 = sX + n * n * n;
   R* S2 = S1 + S::NC1 * n * n * Q;
   const int tid = threadIdx.x;
-  const int64_t e = (int64_t)blockIdx.x * S::NE + threadIdx.y;
+  const int64_t e = e0 + threadIdx.y;
   // batched operators: elements of problems that have converged do nothing
-  const bool live = e < E && !(elem_prob && prob_done[elem_prob[e]]);
+  const bool live = (int)threadIdx.y < ne && !(elem_prob && prob_done[elem_prob[e]]);
   const int* g = gmap + e * (n * n * n);
 
   for (int i = threadIdx.y * T + tid; i < Q * n; i += T * S::NE) {
@@ -321,6 +322,32 @@ pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R*
         atomicAdd(y + (~gi), x[~gi]);
       }
     }
+}
+
+template <typename R, int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(PaShape<R, P, Q, DIFF>::TPE * PaShape<R, P, Q, DIFF>::NE)
+pa_apply(int E, const int* __restrict__ gmap, const R* __restrict__ qd, const R* __restrict__ Btab,
+         const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip,
+         const int* __restrict__ elem_prob, const int* __restrict__ prob_done) {
+  constexpr int NE = PaShape<R, P, Q, DIFF>::NE;
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  pa_tile<R, P, Q, DIFF>(e0, (int)((E - e0) < NE ? (E - e0) : NE), gmap, qd, Btab, Gtab, x, y, elem_prob, prob_done);
+}
+
+// Persistent form over a work list (the batch's iteration loop), as pa_apply_f32_tiles
+template <typename R, int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(PaShape<R, P, Q, DIFF>::TPE * PaShape<R, P, Q, DIFF>::NE)
+pa_apply_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, const int* __restrict__ nact,
+               const int* __restrict__ gmap, const R* __restrict__ qd, const R* __restrict__ Btab,
+               const R* __restrict__ Gtab, const R* __restrict__ x, R* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int count = *nact;
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int2 tl = tiles[act[i]];
+    pa_tile<R, P, Q, DIFF>(tl.x, tl.y, gmap, qd, Btab, Gtab, x, y, nullptr, nullptr);
+    __syncthreads();  // (the next tile reuses the shared buffers)
+  }
 }
 
 // ---------------------------------------------------------------------------

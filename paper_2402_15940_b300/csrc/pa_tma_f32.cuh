@@ -528,16 +528,18 @@ __device__ __forceinline__ void dot_publish(float acc, int nthreads, int flat, d
 // p <= 3 and 3-17 % slower from p = 4 (the 6 q registers it holds cost occupancy there).
 // BSKIP: the batched build, which reads elem_prob / prob_done (a separate instantiation, so
 // the single-operator kernels carry none of its checks: they cost those 5 % when tested).
+// The block's work on one tile of ne <= NE consecutive elements starting at e0 (called once per
+// block by pa_apply_f32_tma, or per tile of a work list by pa_apply_f32_tiles)
 template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3),
           bool BSKIP = false, bool DOT = false>
-__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
-pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
-                 float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
-                 const int* __restrict__ prob_done, int* __restrict__ err, double* __restrict__ dot) {
+__device__ __forceinline__ void f32_tile(int64_t e0, int ne, const int* __restrict__ gmap,
+                                         const float* __restrict__ qd32, const float* __restrict__ x,
+                                         float* __restrict__ y, const int* __restrict__ elem_prob,
+                                         const int* __restrict__ prob_done, int* __restrict__ err,
+                                         double* __restrict__ dot) {
   using S = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
   static_assert(!DOT || (P >= 3 && !BSKIP), "the fused (x, A x) needs the shared-memory scatter");
-  if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_tma[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma);
   float* sD = reinterpret_cast<float*>(smem_tma + 16);
@@ -545,8 +547,6 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
   float* sS1 = sXall + NE * S::XE;                     // [NE][W1]
   float* sS2 = sS1 + NE * S::W1;                       // [NE][W2]
   const int tid = threadIdx.x, el = threadIdx.y;
-  const int64_t e0 = (int64_t)blockIdx.x * NE;
-  const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
   // batched problems (BSKIP): the elements of a converged problem do no work, and a block
   // whose elements all belong to converged problems leaves at once
   auto alive = [&](int e) { return e < ne && !(BSKIP && prob_done[elem_prob[e0 + e]]); };
@@ -742,6 +742,36 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
     }
   }
   if constexpr (DOT) dot_publish(acc, TPE * NE, el * TPE + tid, dot);
+}
+
+template <int P, int Q, bool DIFF, bool STAGE_D, int NE_DIV, int PF = 2, bool FLAT = (P <= 4), bool DEARLY = (P <= 3),
+          bool BSKIP = false, bool DOT = false>
+__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::TPE * TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE)
+pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
+                 float* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
+                 const int* __restrict__ prob_done, int* __restrict__ err, double* __restrict__ dot) {
+  constexpr int NE = TmaShape<P, Q, DIFF, STAGE_D, NE_DIV>::NE;
+  if (skip && *skip) return;
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  f32_tile<P, Q, DIFF, STAGE_D, NE_DIV, PF, FLAT, DEARLY, BSKIP, DOT>(e0, (int)((E - e0) < NE ? (E - e0) : NE), gmap,
+                                                                     qd32, x, y, elem_prob, prob_done, err, dot);
+}
+
+// Persistent form over a work list (the batch's iteration loop): a fixed grid walks the tiles
+// act[0 .. *nact) of the table tiles (element offset, count <= NE) -- the tiles of problems still
+// running -- so finished problems launch no blocks.  Direct D (variant 2's shape).
+template <int P, int Q, bool DIFF>
+__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, false, 2>::TPE * TmaShape<P, Q, DIFF, false, 2>::NE)
+pa_apply_f32_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, const int* __restrict__ nact,
+                   const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
+                   float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
+  if (skip && *skip) return;
+  const int count = *nact;
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const int2 tl = tiles[act[i]];
+    f32_tile<P, Q, DIFF, false, 2>(tl.x, tl.y, gmap, qd32, x, y, nullptr, nullptr, err, nullptr);
+    __syncthreads();  // (the next tile reuses the shared buffers)
+  }
 }
 
 // ---------------------------------------------------------------------------
