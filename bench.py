@@ -604,8 +604,8 @@ def run_batch(args, rank, world, dist, steps=None, warmup=None, quiet=False):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    steps = steps if steps is None else steps
-    warmup = warmup if warmup is None else warmup
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     mix = FI.problem_mix(args.batch_count, seed=rank)
     probs = [{"n": m["n"], "p": m["p"], "form": m["form"],
               "vertices": FI.perturbed_cube_vertices(*m["n"], seed=m["mesh_seed"])} for m in mix]

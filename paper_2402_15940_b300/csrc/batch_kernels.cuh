@@ -37,6 +37,8 @@ struct ChunkTable {
   int nchunks;
   const int* act;          // the chunks of running problems (work list; null: every chunk)
   const int* nact;         // its length
+  const int* aprob;        // the running problems (work list; null: every problem)
+  const int* naprob;       // its length
 };
 
 // Work lists of the iteration loop, rebuilt whenever the set of running problems changes: the
@@ -45,6 +47,8 @@ struct ChunkTable {
 struct WorkLists {
   int* act_chunks;          // [nchunks]
   int* n_act_chunks;        // [1]
+  int* act_probs;           // [nprob]
+  int* n_act_probs;         // [1]
   int ngroups;
   const int* prob_group;    // [nprob] group of each problem
   const int* tile_first;    // [nprob] first tile of the problem in its group's tile table
@@ -80,23 +84,31 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
   return last;
 }
 
-// Sum, per problem, the NV chunk partials of its chunks (called by the last block);
-// f(j, sums) receives problem j's totals.  Returns the number of problems f reports
-// as active, summed over the block (valid in every thread after the call).
+// Sum, per problem, the NV chunk partials of its chunks (called by the last block): one warp
+// per problem, its lanes striding over the chunks and a fixed shuffle tree combining them (the
+// order depends only on the problem's own chunk count); over every problem, or over the work
+// list of running problems where the table carries one.  f(j, sums) -- called by one lane --
+// receives problem j's totals.  Returns the number of problems f reports as active, summed over
+// the block (valid in every thread after the call).
 template <int NV, typename F>
 __device__ __forceinline__ int per_problem(const ChunkTable& t, const double* partials, F f) {
   __shared__ int active;
   if (threadIdx.x == 0) active = 0;
   __syncthreads();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int np = t.aprob ? *t.naprob : t.nprob;
   int mine = 0;
-  for (int j = threadIdx.x; j < t.nprob; j += blockDim.x) {
+  for (int jj = threadIdx.x >> 5; jj < np; jj += nw) {
+    const int j = t.aprob ? t.aprob[jj] : jj;
+    const int b0 = t.pb_first[j], b1 = b0 + t.pb_count[j];
     double s[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       s[k] = 0.0;
-      for (int b = t.pb_first[j]; b < t.pb_first[j] + t.pb_count[j]; ++b) s[k] += __ldcg(partials + k * t.nchunks + b);
+      for (int b = b0 + lane; b < b1; b += 32) s[k] += __ldcg(partials + k * t.nchunks + b);
+      s[k] = warp_sum(s[k]);
     }
-    mine += f(j, s) ? 1 : 0;
+    if (lane == 0) mine += f(j, s) ? 1 : 0;
   }
   atomicAdd(&active, mine);
   __syncthreads();
@@ -106,11 +118,15 @@ __device__ __forceinline__ int per_problem(const ChunkTable& t, const double* pa
 // Rebuild the work lists from pdone (called by one whole block; w.act_chunks null: no lists)
 __device__ __forceinline__ void rebuild_lists(const ChunkTable& t, const WorkLists& w, const int* pdone) {
   if (!w.act_chunks) return;
-  if (threadIdx.x == 0) *w.n_act_chunks = 0;
+  if (threadIdx.x == 0) {
+    *w.n_act_chunks = 0;
+    *w.n_act_probs = 0;
+  }
   for (int g = threadIdx.x; g < w.ngroups; g += blockDim.x) w.n_act_tiles[g] = 0;
   __syncthreads();
   for (int j = threadIdx.x; j < t.nprob; j += blockDim.x) {
     if (__ldcg(pdone + j)) continue;
+    w.act_probs[atomicAdd(w.n_act_probs, 1)] = j;
     const int nc = t.pb_count[j];
     const int cb = atomicAdd(w.n_act_chunks, nc);
     for (int c = 0; c < nc; ++c) w.act_chunks[cb + c] = t.pb_first[j] + c;
