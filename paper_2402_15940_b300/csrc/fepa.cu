@@ -112,14 +112,13 @@ struct KernelSet {
   void (*rhs_df)(int64_t, int, int, const int*, const float2*, const int*, const double*, double, double, double*);
   int rhs_df_smem, rhs_df_ne;
   Apply32Variant v32[N32_VARIANTS];
-  Apply32Variant v32_batch;  // variant 2 built to skip the elements of converged batch problems
   // persistent forms over a work list of element tiles (the batch's iteration loops)
   void (*apply_tiles)(const int2*, const int*, const int*, const int*, const double*, const double*, const double*,
                       const double*, double*, const int*);
   void (*apply_df_tiles)(const int2*, const int*, const int*, const int*, const float2*, const double*, double*,
                          const int*, int);
-  void (*apply32_tiles)(const int2*, const int*, const int*, const int*, const float*, const float*, float*,
-                        const int*, int*);
+  void (*apply32_tiles[2])(const int2*, const int*, const int*, const int*, const float*, const float*, float*,
+                           const int*, int*);  // shapes of variants 1 and 2
   Apply32Fn v32dot[3] = {};  // variants 0-2 built to add (x, A x) into DOT_SLOTS doubles (p >= 3)
   void (*diag)(int, const int*, const double*, const double*, const double*, double*);
   int apply_smem, apply_tpe, apply_ne;
@@ -146,14 +145,12 @@ KernelSet make_set() {
               TmaShape<P, Q, DIFF, false, 1>::NE, TmaShape<P, Q, DIFF, false, 1>::NE, false};
   k.v32[2] = {pa_apply_f32_tma<P, Q, DIFF, false, 2>, TmaShape<P, Q, DIFF, false, 2>::SMEM,
               TmaShape<P, Q, DIFF, false, 2>::NE, TmaShape<P, Q, DIFF, false, 2>::NE, false};
-  k.v32_batch = {pa_apply_f32_tma<P, Q, DIFF, false, 2, 2, (P <= 4), (P <= 3), true>,
-                 TmaShape<P, Q, DIFF, false, 2>::SMEM, TmaShape<P, Q, DIFF, false, 2>::NE,
-                 TmaShape<P, Q, DIFF, false, 2>::NE, false};
   k.v32[3] = {pa_apply_f32_pipe<P, Q, DIFF>, PipeShape<P, Q, DIFF>::SMEM, PipeShape<P, Q, DIFF>::NE,
               PipeShape<P, Q, DIFF>::NE, true};
   k.apply_tiles = pa_apply_tiles<double, P, Q, DIFF>;
   k.apply_df_tiles = pa_apply_df_tiles<P, Q, DIFF>;
-  k.apply32_tiles = pa_apply_f32_tiles<P, Q, DIFF>;  // (variant 2's shape: as v32_batch)
+  k.apply32_tiles[0] = pa_apply_f32_tiles<P, Q, DIFF, 1>;
+  k.apply32_tiles[1] = pa_apply_f32_tiles<P, Q, DIFF, 2>;
   if constexpr (P >= 3) {
     k.v32dot[0] = pa_apply_f32_tma<P, Q, DIFF, true, 1, 2, (P <= 4), (P <= 3), false, true>;
     k.v32dot[1] = pa_apply_f32_tma<P, Q, DIFF, false, 1, 2, (P <= 4), (P <= 3), false, true>;

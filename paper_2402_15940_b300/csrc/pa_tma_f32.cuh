@@ -759,9 +759,10 @@ pa_apply_f32_tma(int E, const int* __restrict__ gmap, const float* __restrict__ 
 
 // Persistent form over a work list (the batch's iteration loop): a fixed grid walks the tiles
 // act[0 .. *nact) of the table tiles (element offset, count <= NE) -- the tiles of problems still
-// running -- so finished problems launch no blocks.  Direct D (variant 2's shape).
-template <int P, int Q, bool DIFF>
-__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, false, 2>::TPE * TmaShape<P, Q, DIFF, false, 2>::NE)
+// running -- so finished problems launch no blocks.  Direct D, in the shape of variant 1
+// (NE_DIV 1) or 2 (NE_DIV 2), chosen per batch group by timing.
+template <int P, int Q, bool DIFF, int NE_DIV>
+__global__ void __launch_bounds__(TmaShape<P, Q, DIFF, false, NE_DIV>::TPE * TmaShape<P, Q, DIFF, false, NE_DIV>::NE)
 pa_apply_f32_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, const int* __restrict__ nact,
                    const int* __restrict__ gmap, const float* __restrict__ qd32, const float* __restrict__ x,
                    float* __restrict__ y, const int* __restrict__ skip, int* __restrict__ err) {
@@ -769,7 +770,7 @@ pa_apply_f32_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, 
   const int count = *nact;
   for (int i = blockIdx.x; i < count; i += gridDim.x) {
     const int2 tl = tiles[act[i]];
-    f32_tile<P, Q, DIFF, false, 2>(tl.x, tl.y, gmap, qd32, x, y, nullptr, nullptr, err, nullptr);
+    f32_tile<P, Q, DIFF, false, NE_DIV>(tl.x, tl.y, gmap, qd32, x, y, nullptr, nullptr, err, nullptr);
     __syncthreads();  // (the next tile reuses the shared buffers)
   }
 }
