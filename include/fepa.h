@@ -267,9 +267,11 @@ int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax);
  * with half as many elements per block, 3 = persistent blocks pipelined over element
  * groups (TMA copy of the next group's D and cp.async gather of its x overlap the
  * current group's arithmetic).  By default (variant -1) the first FP32 use
- * times every variant on this op's mesh and keeps the fastest; the choice is cached per
+ * times every variant on this op's mesh, in the form the FP32 CG loop launches it (with
+ * (x, A x) fused where the variant has that build and fused products are enabled, else
+ * with the separate dot-product pass), and keeps the fastest; the choice is cached per
  * device, (p, q, form) and mesh size class (E < 1e3, 1e4, 1e5, larger) for the process.
- * All variants compute the same result.
+ * All variants compute the same result (up to the order of the atomic additions).
  */
 int fepa_op_set_f32_variant(fepa_op* op, int32_t variant);
 int32_t fepa_op_f32_variant(const fepa_op* op);          /* -1 until chosen */

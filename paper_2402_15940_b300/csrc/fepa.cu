@@ -166,6 +166,8 @@ KernelSet make_set() {
   return k;
 }
 
+static_assert(FEPA_MAX_ORDER == 8, "the FP32 pair tables (tab32_offset) are laid out for p = 1..8");
+
 template <int P>
 void fill_order(KernelSet (&t)[FEPA_MAX_ORDER + 1][2][2]) {
   t[P][0][0] = make_set<P, P + 1, false>();
@@ -422,6 +424,9 @@ int launch_apply(fepa_op* op, const double* x, double* y, const int* skip, cudaS
   return FEPA_OK;
 }
 
+// whether FP32 variant v has a build that also adds (x, A x) into DOT_SLOTS doubles
+bool has_dot_build(const fepa_op* op, int v) { return v >= 0 && v < 3 && op->ks.v32dot[v]; }
+
 // y += A x in FP32 with variant v (launch only; not counted).  dot: also add (x, A x) into
 // these DOT_SLOTS doubles (only where fused_dot_ok).
 int launch_apply32_variant(fepa_op* op, int v, const float* x, float* y, const int* skip, cudaStream_t s,
@@ -553,8 +558,25 @@ void init_tuned() {
 int time_variants32(fepa_op* op, int* best) {
   cudaStream_t s = op->stream;
   float *x = nullptr, *y = nullptr;
+  double* slots = nullptr;
   TRY(dalloc(&x, op->N));
   int rc = dalloc(&y, op->N);
+  if (rc == FEPA_OK) rc = dalloc(&slots, DOT_SLOTS);
+  if (rc == FEPA_OK && cudaMemsetAsync(slots, 0, DOT_SLOTS * sizeof(double), s) != cudaSuccess)
+    rc = fail(FEPA_ERR_CUDA, "memset failed");
+  // each variant in the form the FP32 CG loop launches it: its build with (x, A x) fused where
+  // it has one (and the op allows it), else the plain action plus the separate dot pass
+  auto run = [&](int v) -> int {
+    if (op->fuse_dot && has_dot_build(op, v)) {
+      g_launches.fetch_add(1);
+      return launch_apply32_variant(op, v, x, y, nullptr, s, slots);
+    }
+    TRY(launch_apply32_variant(op, v, x, y, nullptr, s));
+    dot32_slots<<<grid_for(op->N, RED_THREADS, 148 * 8), RED_THREADS, 0, s>>>(op->N, x, y, slots);
+    CUDA_TRY(cudaGetLastError());
+    g_launches.fetch_add(2);
+    return FEPA_OK;
+  };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float best_ms = 1e30f;
   *best = 0;
@@ -564,10 +586,10 @@ int time_variants32(fepa_op* op, int* best) {
     rc = fail(FEPA_ERR_CUDA, "memset failed");
   for (int v = 0; rc == FEPA_OK && v < N32_VARIANTS; ++v) {
     if (op->v32_grid[v] <= 0) continue;
-    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply32_variant(op, v, x, y, nullptr, s);
+    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = run(v);
     if (rc != FEPA_OK) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = launch_apply32_variant(op, v, x, y, nullptr, s);
+    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = run(v);
     cudaEventRecord(e1, s);
     if (rc != FEPA_OK) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -576,7 +598,6 @@ int time_variants32(fepa_op* op, int* best) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    g_launches.fetch_add(7);
     if (ms < best_ms) {
       best_ms = ms;
       *best = v;
@@ -586,6 +607,7 @@ int time_variants32(fepa_op* op, int* best) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(x);
   if (y) cudaFree(y);
+  if (slots) cudaFree(slots);
   return rc;
 }
 
@@ -708,11 +730,7 @@ int ensure_f32(fepa_op* op) {
   const int64_t count = op->E * ncomp * (int64_t)op->ks.d32_stride;
   if (!op->qd32) {
     TRY(dalloc(&op->qd32, count));
-    const size_t slot = (size_t)((op->p - 1) * 2 + (op->q - op->p - 1)) * TAB_SLOT;
-    CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->B32h.data(), op->B32h.size() * sizeof(float), slot * sizeof(float),
-                                     cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyToSymbolAsync(c_tab32, op->G32h.data(), op->G32h.size() * sizeof(float),
-                                     (slot + 100) * sizeof(float), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(upload_tab32(op->p, op->q, op->B32h, op->G32h, s));
     for (int v = 0; v < N32_VARIANTS; ++v) TRY(allow_smem((const void*)op->ks.v32[v].fn, op->ks.v32[v].smem));
     for (int v = 0; v < 3; ++v)
       if (op->ks.v32dot[v]) TRY(allow_smem((const void*)op->ks.v32dot[v], op->ks.v32[v].smem));
@@ -816,7 +834,7 @@ int body64(fepa_op* op, CgLoop& L, const double* invd, cudaStream_t s, cudaGraph
 
 // FP32 loop: (d, h) comes out of the action kernel itself (no separate pass over d and h)
 // when the chosen variant has that build and the op allows it
-bool fused_dot_ok(const fepa_op* op) { return op->fuse_dot && op->v32 >= 0 && op->v32 < 3 && op->ks.v32dot[op->v32]; }
+bool fused_dot_ok(const fepa_op* op) { return op->fuse_dot && has_dot_build(op, op->v32); }
 
 int body32(fepa_op* op, CgLoop& L, const float* invd, cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond) {
   const int rb = L.red_blocks;
@@ -1473,7 +1491,7 @@ int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax) {
     CUDA_TRY(cudaMemsetAsync(op->dot_slots, 0, DOT_SLOTS * sizeof(double), s));
   }
   CUDA_TRY(cudaMemsetAsync(y, 0, op->N * sizeof(float), s));
-  if (op->v32 < 3 && op->ks.v32dot[op->v32]) {
+  if (has_dot_build(op, op->v32)) {
     TRY(launch_apply32_variant(op, op->v32, x, y, nullptr, s, op->dot_slots));
     g_launches.fetch_add(1);
   } else {

@@ -2,7 +2,8 @@
 // y = G^T B^T D B G x of Fig. fig_feod, arXiv 2402.15940), built for an HBM-bound
 // kernel on sm_103a.  Common to all variants:
 //   * the 1D tables live in __constant__ memory at compile-time offsets, so with the
-//     loops unrolled they are free FMA operands;
+//     loops unrolled they are free FMA operands -- as pairs of entries, so that one packed
+//     FMA (two FP32 FMAs in one instruction) produces two outputs of a line;
 //   * every stage is register-blocked: a thread loads one line of its element once
 //     and produces all outputs of that line; stage 3, the pointwise D and the
 //     transposed stage 3 stay in registers per (i,j) column;
@@ -22,22 +23,93 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "cg_kernels.cuh"
 #include "pa_kernels.cuh"
 
 namespace fepa {
 
-// tables of every compiled (P, Q): slot ((P-1)*2 + (Q-P-1)) holds B then G, 100 floats each
+// slot layout of the double-float tables (pa_df64.cuh): B then G, 100 entries each
 constexpr int TAB_SLOT = 200;
 constexpr int TAB_SLOTS = 16;
-__constant__ float c_tab32[TAB_SLOT * TAB_SLOTS];
+
+// FP32 1D tables of every compiled (P, Q) as float2 pairs, for the packed FMA (__ffma2_rn:
+// two FMAs in one instruction, each component rounded as fmaf), with a table pair as one
+// constant-bank operand and the other operand a pair or a broadcast scalar:
+//   rows     R[kp][a] = (T(2kp, a), T(2kp+1, a)),  kp < ceil(Q/2)  (.y = 0 past row Q-1)
+//   columns  C[k][ap] = (T(k, 2ap), T(k, 2ap+1)),  ap < ceil(n/2)  (.y = 0 past column n-1)
+// for T = B, G (Q x n, T(i, a) = basis a or its derivative at point i); slots packed in the
+// order (1, 2), (1, 3), (2, 3), (2, 4), ... (8, 10).
+constexpr int tab32_slot_pairs(int P, int Q) { return 2 * (((Q + 1) / 2) * (P + 1) + Q * ((P + 2) / 2)); }
+constexpr int tab32_offset(int P, int Q) {
+  int off = 0;
+  for (int p = 1; p <= 8; ++p)
+    for (int q = p + 1; q <= p + 2; ++q) {
+      if (p == P && q == Q) return off;
+      off += tab32_slot_pairs(p, q);
+    }
+  return off;  // past the last slot: the total
+}
+constexpr int TAB32_PAIRS = tab32_offset(9, 0);
+__constant__ float2 c_tab32[TAB32_PAIRS];
 
 template <int P, int Q>
 struct Tab32 {
   static_assert(Q == P + 1 || Q == P + 2, "compiled q");
-  static constexpr int OFF = ((P - 1) * 2 + (Q - P - 1)) * TAB_SLOT;
-  static __device__ __forceinline__ float B(int i, int a) { return c_tab32[OFF + i * (P + 1) + a]; }
-  static __device__ __forceinline__ float G(int i, int a) { return c_tab32[OFF + 100 + i * (P + 1) + a]; }
+  static constexpr int N = P + 1, QH = (Q + 1) / 2, NH = (N + 1) / 2;
+  static constexpr int BR = tab32_offset(P, Q), GR = BR + QH * N, BC = GR + QH * N, GC = BC + Q * NH;
+  static __device__ __forceinline__ float2 Br(int kp, int a) { return c_tab32[BR + kp * N + a]; }
+  static __device__ __forceinline__ float2 Gr(int kp, int a) { return c_tab32[GR + kp * N + a]; }
+  static __device__ __forceinline__ float2 Bc(int k, int ap) { return c_tab32[BC + k * NH + ap]; }
+  static __device__ __forceinline__ float2 Gc(int k, int ap) { return c_tab32[GC + k * NH + ap]; }
+  static __device__ __forceinline__ float B(int i, int a) { return (i & 1) ? Br(i >> 1, a).y : Br(i >> 1, a).x; }
+  static __device__ __forceinline__ float G(int i, int a) { return (i & 1) ? Gr(i >> 1, a).y : Gr(i >> 1, a).x; }
+};
+
+// the pair tables of (p, q) from the row-major q x n tables B, G (host)
+inline std::vector<float2> tab32_pairs(int p, int q, const std::vector<float>& B, const std::vector<float>& G) {
+  const int n = p + 1, qh = (q + 1) / 2, nh = (n + 1) / 2;
+  std::vector<float2> out;
+  out.reserve(tab32_slot_pairs(p, q));
+  for (const std::vector<float>* T : {&B, &G})
+    for (int kp = 0; kp < qh; ++kp)
+      for (int a = 0; a < n; ++a)
+        out.push_back(make_float2((*T)[2 * kp * n + a], 2 * kp + 1 < q ? (*T)[(2 * kp + 1) * n + a] : 0.f));
+  for (const std::vector<float>* T : {&B, &G})
+    for (int k = 0; k < q; ++k)
+      for (int ap = 0; ap < nh; ++ap)
+        out.push_back(make_float2((*T)[k * n + 2 * ap], 2 * ap + 1 < n ? (*T)[k * n + 2 * ap + 1] : 0.f));
+  return out;
+}
+
+// upload the FP32 pair tables of (p, q) into their constant-memory slot
+inline cudaError_t upload_tab32(int p, int q, const std::vector<float>& B, const std::vector<float>& G,
+                                cudaStream_t s) {
+  const std::vector<float2> t = tab32_pairs(p, q, B, G);
+  return cudaMemcpyToSymbolAsync(c_tab32, t.data(), t.size() * sizeof(float2), tab32_offset(p, q) * sizeof(float2),
+                                 cudaMemcpyHostToDevice, s);
+}
+
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+// Which stages of the FP32 action use the packed FMA, per (P, Q, form): bit 0 stage 1,
+// bit 1 stage 2, bit 2 stage 3 (points paired; else one point at a time, in scalar FMAs),
+// bit 3 stage 3's transposed contraction (with bit 2 clear), bit 4 stage 2^T, bit 5 stage 1^T.
+// Measured on B300 (variants 1 and 2 against the all-scalar build, stand-alone launches):
+// all stages packed is 5-29 % faster from p = 5 and for mass at p = 4, 8; where pairing the
+// points of stage 3 costs registers (and resident blocks) it stays scalar or pairs only its
+// transposed contraction: diffusion p = 4, q = 6 2 % faster (all packed: 48 registers, 5 %
+// slower), p = 8 23 %, p = 1-3 within 1 %.
+constexpr int pack32_mask(int P, int Q, bool DIFF) {
+  return DIFF ? ((Q == P + 2 && P == 4) ? 51 : (Q == P + 2 && (P <= 3 || P == 8)) ? 59 : 63)
+              : (P == 7 ? 51 : 63);
+}
+template <int P, int Q, bool DIFF>
+struct Pack32 {
+  static constexpr int MASK = pack32_mask(P, Q, DIFF);
+  static constexpr bool S1 = MASK & 1, S2 = MASK & 2, S3F = MASK & 4, S3T = (MASK & 4) || (MASK & 8),
+                        S2T = MASK & 16, S1T = MASK & 32;
 };
 
 // S1 strides and element padding per (P, Q) of the double-float kernel's layout (the FP32
@@ -272,16 +344,35 @@ __device__ __forceinline__ void f32_stage1(int tid, bool live, const float* sX, 
 #pragma unroll
   for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
   float* o = S1 + (L::CS == n * L::Q1 ? tid * L::Q1 : (tid % n) * L::Q1 + (tid / n) * L::CS);
+  if constexpr (!Pack32<P, Q, DIFF>::S1) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    float sb = 0.f, sg = 0.f;
+    for (int i = 0; i < Q; ++i) {
+      float sb = 0.f, sg = 0.f;
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        sb = fmaf(T::B(i, a), xv[a], sb);
+        if (DIFF) sg = fmaf(T::G(i, a), xv[a], sg);
+      }
+      o[i] = sb;
+      if (DIFF) o[L::S1C + i] = sg;
+    }
+    return;
+  }
+  // outputs i, i+1 in one packed FMA per input (each output's sum in the order of a)
+#pragma unroll
+  for (int ip = 0; ip < T::QH; ++ip) {
+    float2 sb = make_float2(0.f, 0.f), sg = make_float2(0.f, 0.f);
 #pragma unroll
     for (int a = 0; a < n; ++a) {
-      sb = fmaf(T::B(i, a), xv[a], sb);
-      if (DIFF) sg = fmaf(T::G(i, a), xv[a], sg);
+      sb = __ffma2_rn(T::Br(ip, a), bcast2(xv[a]), sb);
+      if (DIFF) sg = __ffma2_rn(T::Gr(ip, a), bcast2(xv[a]), sg);
     }
-    o[i] = sb;
-    if (DIFF) o[L::S1C + i] = sg;
+    o[2 * ip] = sb.x;
+    if (DIFF) o[L::S1C + 2 * ip] = sg.x;
+    if (2 * ip + 1 < Q) {
+      o[2 * ip + 1] = sb.y;
+      if (DIFF) o[L::S1C + 2 * ip + 1] = sg.y;
+    }
   }
 }
 
@@ -300,33 +391,61 @@ __device__ __forceinline__ void f32_stage2(int tid, bool live, const float* S1, 
     vb[b] = S1[b * L::Q1 + c * L::CS + i];
     if (DIFF) vg[b] = S1[L::S1C + b * L::Q1 + c * L::CS + i];
   }
+  if constexpr (!Pack32<P, Q, DIFF>::S2) {
 #pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    float bb = 0.f, bg = 0.f, gb = 0.f;
+    for (int j = 0; j < Q; ++j) {
+      float bb = 0.f, bg = 0.f, gb = 0.f;
 #pragma unroll
-    for (int b = 0; b < n; ++b) {
-      bb = fmaf(T::B(j, b), vb[b], bb);
+      for (int b = 0; b < n; ++b) {
+        bb = fmaf(T::B(j, b), vb[b], bb);
+        if (DIFF) {
+          bg = fmaf(T::G(j, b), vb[b], bg);
+          gb = fmaf(T::B(j, b), vg[b], gb);
+        }
+      }
+      const int o = c * L::P2 + j * Q + i;
       if (DIFF) {
-        bg = fmaf(T::G(j, b), vb[b], bg);
-        gb = fmaf(T::B(j, b), vg[b], gb);
+        S2[o] = gb;
+        S2[L::S2C + o] = bg;
+        S2[2 * L::S2C + o] = bb;
+      } else {
+        S2[o] = bb;
       }
     }
-    const int o = c * L::P2 + j * Q + i;
-    if (DIFF) {
-      S2[o] = gb;
-      S2[L::S2C + o] = bg;
-      S2[2 * L::S2C + o] = bb;
-    } else {
-      S2[o] = bb;
+    return;
+  }
+#pragma unroll
+  for (int jp = 0; jp < T::QH; ++jp) {
+    float2 bb = make_float2(0.f, 0.f), bg = bb, gb = bb;
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      bb = __ffma2_rn(T::Br(jp, b), bcast2(vb[b]), bb);
+      if (DIFF) {
+        bg = __ffma2_rn(T::Gr(jp, b), bcast2(vb[b]), bg);
+        gb = __ffma2_rn(T::Br(jp, b), bcast2(vg[b]), gb);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * jp + h;
+      if (j >= Q) break;
+      const int o = c * L::P2 + j * Q + i;
+      if (DIFF) {
+        S2[o] = h ? gb.y : gb.x;
+        S2[L::S2C + o] = h ? bg.y : bg.x;
+        S2[2 * L::S2C + o] = h ? bb.y : bb.x;
+      } else {
+        S2[o] = h ? bb.y : bb.x;
+      }
     }
   }
 }
 
-// stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers; D at dE
-// (shared or global), component stride DSTRIDE, point k at dE[k*Q*Q]
-// PRE: the column's D was loaded into dpre[k * NCD + m] before the preceding barrier
+// stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers, in scalar FMAs
+// (one point at a time); D at dE (shared or global), component stride DSTRIDE, point k at
+// dE[k*Q*Q].  PRE: the column's D was loaded into dpre[k * NCD + m] before the preceding barrier
 template <int P, int Q, bool DIFF, bool PRE = false>
-__device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE, const float* dpre = nullptr) {
+__device__ __forceinline__ void f32_stage3_scalar(int tid, bool live, float* S2, const float* dE, const float* dpre = nullptr) {
   using L = F32Smem<P, Q, DIFF>;
   using T = Tab32<P, Q>;
   constexpr int n = L::N;
@@ -402,6 +521,143 @@ __device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const 
   }
 }
 
+// stage 3 (z) + D + stage 3^T, one (i,j) column per thread, in registers, by the policy of
+// Pack32: points paired in packed FMAs, or only the transposed contraction's columns paired
+// (bits 2, 3), else the scalar form above; arguments as there
+template <int P, int Q, bool DIFF, bool PRE = false>
+__device__ __forceinline__ void f32_stage3(int tid, bool live, float* S2, const float* dE, const float* dpre = nullptr) {
+  using L = F32Smem<P, Q, DIFF>;
+  using T = Tab32<P, Q>;
+  constexpr int n = L::N;
+  if constexpr (!Pack32<P, Q, DIFF>::S3T) {
+    f32_stage3_scalar<P, Q, DIFF, PRE>(tid, live, S2, dE, dpre);
+    return;
+  }
+  if (!live) return;
+  float c0[n], c1[n], c2[n];
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    c0[c] = S2[c * L::P2 + tid];
+    if (DIFF) {
+      c1[c] = S2[L::S2C + c * L::P2 + tid];
+      c2[c] = S2[2 * L::S2C + c * L::P2 + tid];
+    }
+  }
+  // transposed-stage accumulators: columns (2cp, 2cp+1) as pairs, column n-1 alone when n is odd
+  constexpr int NP = n / 2;
+  constexpr bool ODDN = (n & 1) != 0;
+  float2 A0[NP], A1[NP], A2[NP];
+  float z0 = 0.f, z1 = 0.f, z2 = 0.f;
+#pragma unroll
+  for (int cp = 0; cp < NP; ++cp) {
+    A0[cp] = make_float2(0.f, 0.f);
+    if (DIFF) A1[cp] = A2[cp] = A0[cp];
+  }
+  // D of point k+1 is loaded while point k is computed (one step of software pipelining)
+  constexpr int NCD = DIFF ? 6 : 1;
+  float dn[NCD];
+  if (!PRE) {
+#pragma unroll
+    for (int m = 0; m < NCD; ++m) dn[m] = dE[m * L::DSTRIDE];
+  }
+  constexpr bool PF = Pack32<P, Q, DIFF>::S3F, PT = Pack32<P, Q, DIFF>::S3T;
+#pragma unroll
+  for (int kp = 0; kp < T::QH; ++kp) {
+    // points 2kp, 2kp+1 of the column in packed FMAs
+    float2 U0 = make_float2(0.f, 0.f), U1 = U0, U2 = U0;
+    if (PF) {
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+      U0 = __ffma2_rn(T::Br(kp, c), bcast2(c0[c]), U0);
+      if (DIFF) {
+        U1 = __ffma2_rn(T::Br(kp, c), bcast2(c1[c]), U1);
+        U2 = __ffma2_rn(T::Gr(kp, c), bcast2(c2[c]), U2);
+      }
+    }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * kp + h;
+      if (k >= Q) break;
+      if (!PF) {
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          u0 = fmaf(T::B(k, c), c0[c], u0);
+          if (DIFF) {
+            u1 = fmaf(T::B(k, c), c1[c], u1);
+            u2 = fmaf(T::G(k, c), c2[c], u2);
+          }
+        }
+        if (h) { U0.y = u0; U1.y = u1; U2.y = u2; } else { U0.x = u0; U1.x = u1; U2.x = u2; }
+      }
+      float dc[NCD];
+      if (PRE) {
+#pragma unroll
+        for (int m = 0; m < NCD; ++m) dc[m] = dpre[k * NCD + m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < NCD; ++m) dc[m] = dn[m];
+        if (k + 1 < Q) {
+#pragma unroll
+          for (int m = 0; m < NCD; ++m) dn[m] = dE[(k + 1) * Q * Q + m * L::DSTRIDE];
+        }
+      }
+      if (DIFF) {
+        const float u0 = h ? U0.y : U0.x, u1 = h ? U1.y : U1.x, u2 = h ? U2.y : U2.x;
+        const float d00 = dc[0], d01 = dc[1 % NCD], d02 = dc[2 % NCD], d11 = dc[3 % NCD], d12 = dc[4 % NCD],
+                    d22 = dc[5 % NCD];
+        const float v0 = fmaf(d00, u0, fmaf(d01, u1, d02 * u2));
+        const float v1 = fmaf(d01, u0, fmaf(d11, u1, d12 * u2));
+        const float v2 = fmaf(d02, u0, fmaf(d12, u1, d22 * u2));
+#pragma unroll
+        for (int cp = 0; cp < NP; ++cp) {
+          if (PT) {
+            A0[cp] = __ffma2_rn(T::Bc(k, cp), bcast2(v0), A0[cp]);
+            A1[cp] = __ffma2_rn(T::Bc(k, cp), bcast2(v1), A1[cp]);
+            A2[cp] = __ffma2_rn(T::Gc(k, cp), bcast2(v2), A2[cp]);
+          } else {
+            A0[cp].x = fmaf(T::Bc(k, cp).x, v0, A0[cp].x);
+            A0[cp].y = fmaf(T::Bc(k, cp).y, v0, A0[cp].y);
+            A1[cp].x = fmaf(T::Bc(k, cp).x, v1, A1[cp].x);
+            A1[cp].y = fmaf(T::Bc(k, cp).y, v1, A1[cp].y);
+            A2[cp].x = fmaf(T::Gc(k, cp).x, v2, A2[cp].x);
+            A2[cp].y = fmaf(T::Gc(k, cp).y, v2, A2[cp].y);
+          }
+        }
+        if (ODDN) {
+          z0 = fmaf(T::Bc(k, NP).x, v0, z0);
+          z1 = fmaf(T::Bc(k, NP).x, v1, z1);
+          z2 = fmaf(T::Gc(k, NP).x, v2, z2);
+        }
+      } else {
+        const float v = dc[0] * (h ? U0.y : U0.x);
+#pragma unroll
+        for (int cp = 0; cp < NP; ++cp) {
+          if (PT) {
+            A0[cp] = __ffma2_rn(T::Bc(k, cp), bcast2(v), A0[cp]);
+          } else {
+            A0[cp].x = fmaf(T::Bc(k, cp).x, v, A0[cp].x);
+            A0[cp].y = fmaf(T::Bc(k, cp).y, v, A0[cp].y);
+          }
+        }
+        if (ODDN) z0 = fmaf(T::Bc(k, NP).x, v, z0);
+      }
+    }
+  }
+  // each thread overwrites only its own column
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    const bool last = ODDN && c == n - 1;
+    const int cp = last ? 0 : c / 2;
+    S2[c * L::P2 + tid] = last ? z0 : ((c & 1) ? A0[cp].y : A0[cp].x);
+    if (DIFF) {
+      S2[L::S2C + c * L::P2 + tid] = last ? z1 : ((c & 1) ? A1[cp].y : A1[cp].x);
+      S2[2 * L::S2C + c * L::P2 + tid] = last ? z2 : ((c & 1) ? A2[cp].y : A2[cp].x);
+    }
+  }
+}
+
 // stage 2^T (y): line (i,c) -> S1[0][c][b][i] = sum_j B[j][b] A0,
 //                             S1[1][c][b][i] = sum_j G[j][b] A1 + B[j][b] A2
 template <int P, int Q, bool DIFF>
@@ -420,16 +676,71 @@ __device__ __forceinline__ void f32_stage2t(int tid, bool live, const float* S2,
       v2[j] = S2[2 * L::S2C + c * L::P2 + j * Q + i];
     }
   }
+  if constexpr (!Pack32<P, Q, DIFF>::S2T) {
 #pragma unroll
-  for (int b = 0; b < n; ++b) {
-    float t0 = 0.f, t1 = 0.f;
+    for (int b = 0; b < n; ++b) {
+      float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        t0 = fmaf(T::B(j, b), v0[j], t0);
+        if (DIFF) t1 = fmaf(T::G(j, b), v1[j], fmaf(T::B(j, b), v2[j], t1));
+      }
+      S1[b * L::Q1 + c * L::CS + i] = t0;
+      if (DIFF) S1[L::S1C + b * L::Q1 + c * L::CS + i] = t1;
+    }
+    return;
+  }
+  // outputs b, b+1 in one packed FMA per input (each output's sum in the order of j)
+#pragma unroll
+  for (int bp = 0; bp < T::NH; ++bp) {
+    float2 t0 = make_float2(0.f, 0.f), t1 = t0;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-      t0 = fmaf(T::B(j, b), v0[j], t0);
-      if (DIFF) t1 = fmaf(T::G(j, b), v1[j], fmaf(T::B(j, b), v2[j], t1));
+      t0 = __ffma2_rn(T::Bc(j, bp), bcast2(v0[j]), t0);
+      if (DIFF) t1 = __ffma2_rn(T::Gc(j, bp), bcast2(v1[j]), __ffma2_rn(T::Bc(j, bp), bcast2(v2[j]), t1));
     }
-    S1[b * L::Q1 + c * L::CS + i] = t0;
-    if (DIFF) S1[L::S1C + b * L::Q1 + c * L::CS + i] = t1;
+    S1[2 * bp * L::Q1 + c * L::CS + i] = t0.x;
+    if (DIFF) S1[L::S1C + 2 * bp * L::Q1 + c * L::CS + i] = t1.x;
+    if (2 * bp + 1 < n) {
+      S1[(2 * bp + 1) * L::Q1 + c * L::CS + i] = t0.y;
+      if (DIFF) S1[L::S1C + (2 * bp + 1) * L::Q1 + c * L::CS + i] = t1.y;
+    }
+  }
+}
+
+// stage 1^T arithmetic of one line: s[a] = sum_i G[i][a] t0[i] + B[i][a] t1[i] (diffusion) or
+// sum_i B[i][a] t0[i] (mass), outputs a, a+1 in one packed FMA per input
+template <int P, int Q, bool DIFF>
+__device__ __forceinline__ void f32_line1t(const float (&t0)[Q], const float (&t1)[Q], float (&s)[P + 1]) {
+  using T = Tab32<P, Q>;
+  constexpr int n = P + 1;
+  if constexpr (!Pack32<P, Q, DIFF>::S1T) {
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      float v = 0.f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (DIFF)
+          v = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], v));
+        else
+          v = fmaf(T::B(i, a), t0[i], v);
+      }
+      s[a] = v;
+    }
+    return;
+  }
+#pragma unroll
+  for (int ap = 0; ap < T::NH; ++ap) {
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (DIFF)
+        v = __ffma2_rn(T::Gc(i, ap), bcast2(t0[i]), __ffma2_rn(T::Bc(i, ap), bcast2(t1[i]), v));
+      else
+        v = __ffma2_rn(T::Bc(i, ap), bcast2(t0[i]), v);
+    }
+    s[2 * ap] = v.x;
+    if (2 * ap + 1 < n) s[2 * ap + 1] = v.y;
   }
 }
 
@@ -449,16 +760,11 @@ __device__ __forceinline__ void f32_stage1t(int tid, bool live, const float* S1,
     t0[i] = in[i];
     if (DIFF) t1[i] = in[L::S1C + i];
   }
+  float sv[n];
+  f32_line1t<P, Q, DIFF>(t0, t1, sv);
 #pragma unroll
   for (int a = 0; a < n; ++a) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (DIFF)
-        s = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], s));
-      else
-        s = fmaf(T::B(i, a), t0[i], s);
-    }
+    const float s = sv[a];
     const int gi = gl[a + n * tid];
     if (gi >= 0) {
       atomicAdd(y + gi, s);
@@ -488,18 +794,12 @@ __device__ __forceinline__ void f32_stage1t_smem(int tid, bool live, const float
     t0[i] = in[i];
     if (DIFF) t1[i] = in[L::S1C + i];
   }
+  float sv[n];
+  f32_line1t<P, Q, DIFF>(t0, t1, sv);
 #pragma unroll
   for (int a = 0; a < n; ++a) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (DIFF)
-        s = fmaf(T::G(i, a), t0[i], fmaf(T::B(i, a), t1[i], s));
-      else
-        s = fmaf(T::B(i, a), t0[i], s);
-    }
-    if (DOT) acc = fmaf(Y[tid * L::XL + a], s, acc);
-    Y[tid * L::XL + a] = s;
+    if (DOT) acc = fmaf(Y[tid * L::XL + a], sv[a], acc);
+    Y[tid * L::XL + a] = sv[a];
   }
 }
 
