@@ -148,9 +148,9 @@ def reduce_max_sum(t, work, dist=None, device="cpu"):
 FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of the
 # current apply kernels on the default workload: captured at 40^3 elements (412.9 / 413.0 MB FP32
-# variants 1 / 2, 413.0 MB variant 1 with (d, A d) fused, 794.5 MB double-float with its exponent-
-# range test: the algorithmic bytes, y read once for the atomics) and scaled to 64^3 by elements
-# (D, map) and DOFs (x, y).
+# variants 1 / 2, 413.0 MB variant 1 with (d, A d) fused -- re-taken with the packed-FMA build, same
+# bytes --, 794.5 MB double-float with its exponent-range test: the algorithmic bytes, y read once
+# for the atomics) and scaled to 64^3 by elements (D, map) and DOFs (x, y).
 # Only reported when that kernel is timed.
 NCU_TRAFFIC_P4_N64 = {"f32_v1": 1.6910e9, "f32_v2": 1.6916e9, "f32dot_v1": 1.6914e9, "df": 3.2555e9}
 # ceiling of the double-float FP64 action: 12 FP32-pipe instructions per FP64-accurate
