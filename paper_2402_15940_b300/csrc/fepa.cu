@@ -212,11 +212,14 @@ int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vec
                                    cudaMemcpyHostToDevice, s));
   if (q != p + 2) return FEPA_OK;
   // even/odd tables of B, G (q x n) and B^T, G^T (n x q) for the double-float action
-  std::vector<float> teo(4 * EO_MAT * 2, 0.f);
-  auto put = [&](int mat, int k, double v) {
-    const float h = (float)v;
-    teo[2 * (mat * EO_MAT + k)] = h;
-    teo[2 * (mat * EO_MAT + k) + 1] = (float)(v - (double)h);
+  // entry k of matrix mat: a hi pair then a lo pair; half 0 (x) or 1 (y) of the pair
+  std::vector<float2> teo(4 * EO_MAT * 2, make_float2(0.f, 0.f));
+  auto put = [&](int mat, int k, int half, double v) {
+    const float h = (float)v, l = (float)(v - (double)h);
+    float2& ph = teo[2 * (mat * EO_MAT + k)];
+    float2& pl = teo[2 * (mat * EO_MAT + k) + 1];
+    (half ? ph.y : ph.x) = h;
+    (half ? pl.y : pl.x) = l;
   };
   for (int mat = 0; mat < 4; ++mat) {
     const std::vector<double>& M = (mat % 2 == 0) ? Bh : Gh;
@@ -232,16 +235,16 @@ int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vec
           return fail(FEPA_ERR_CUDA, "1D tables of p=%d q=%d are not symmetric", p, q);
     for (int o = 0; o < HO; ++o)
       for (int i = 0; i < HI; ++i) {
-        put(mat, o * HI + i, 0.5 * (m(o, i) + m(o, NI - 1 - i)));
-        put(mat, HO * HI + o * HI + i, 0.5 * (m(o, i) - m(o, NI - 1 - i)));
+        put(mat, o * HI + i, 0, 0.5 * (m(o, i) + m(o, NI - 1 - i)));
+        put(mat, o * HI + i, 1, 0.5 * (m(o, i) - m(o, NI - 1 - i)));
       }
     if (NI % 2)
-      for (int o = 0; o < HO; ++o) put(mat, 2 * HO * HI + o, m(o, HI));
+      for (int o = 0; o < HO; ++o) put(mat, HO * HI + o, 0, m(o, HI));
     if (NO % 2)
-      for (int i = 0; i <= HI && i < NI; ++i) put(mat, 2 * HO * HI + HO + i, m(HO, i));
+      for (int i = 0; i <= HI && i < NI; ++i) put(mat, HO * HI + HO + i, 0, m(HO, i));
   }
-  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabeo, teo.data(), teo.size() * sizeof(float),
-                                   (size_t)(p - 1) * 4 * EO_MAT * 2 * sizeof(float), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabeo, teo.data(), teo.size() * sizeof(float2),
+                                   (size_t)(p - 1) * 4 * EO_MAT * 2 * sizeof(float2), cudaMemcpyHostToDevice, s));
   return FEPA_OK;
 }
 

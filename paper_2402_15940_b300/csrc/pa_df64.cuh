@@ -103,6 +103,58 @@ __device__ __forceinline__ dfl df_recip(dfl b) {
   return df_norm(dfl{r0, __fmul_rn(r0, df_norm(e).h)});
 }
 
+// ---------------------------------------------------------------------------
+// two double-float values in packed form: (h.x, l.x) and (h.y, l.y).  Each operation below
+// is the scalar one of the same name applied to both halves with packed FP32 instructions
+// (__fadd2_rn, __fmul2_rn, __ffma2_rn: per component the rounding of the scalar
+// instruction), so the results are bit-identical to two scalar calls in half the
+// instructions.
+// ---------------------------------------------------------------------------
+struct __align__(16) df2 {
+  float2 h, l;
+};
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+__device__ __forceinline__ df2 df2_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ df2 df2_pack(dfl a, dfl b) { return {make_float2(a.h, b.h), make_float2(a.l, b.l)}; }
+__device__ __forceinline__ dfl df2_x(df2 a) { return {a.h.x, a.l.x}; }
+__device__ __forceinline__ dfl df2_y(df2 a) { return {a.h.y, a.l.y}; }
+
+// acc += t * x (df_fma on both halves)
+__device__ __forceinline__ void df2_fma(df2& acc, float2 th, float2 tl, float2 xh, float2 xl) {
+  const float2 p = __fmul2_rn(th, xh);
+  float2 e = __ffma2_rn(th, xh, f2neg(p));
+  e = __ffma2_rn(th, xl, e);
+  e = __ffma2_rn(tl, xh, e);
+  const float2 s = __fadd2_rn(acc.h, p);
+  const float2 bv = f2sub(s, acc.h);
+  const float2 err = __fadd2_rn(f2sub(acc.h, f2sub(s, bv)), f2sub(p, bv));
+  acc.h = s;
+  acc.l = __fadd2_rn(acc.l, __fadd2_rn(err, e));
+}
+
+// a + b (df_add on both halves)
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+  const float2 s = __fadd2_rn(a.h, b.h);
+  const float2 bv = f2sub(s, a.h);
+  const float2 e = __fadd2_rn(f2sub(a.h, f2sub(s, bv)), f2sub(b.h, bv));
+  const float2 t = __fadd2_rn(e, __fadd2_rn(a.l, b.l));
+  const float2 r = __fadd2_rn(s, t);
+  return {r, f2sub(t, f2sub(r, s))};
+}
+
+// renormalise (df_norm on both halves)
+__device__ __forceinline__ df2 df2_norm(df2 a) {
+  const float2 s = __fadd2_rn(a.h, a.l);
+  return {s, f2sub(a.l, f2sub(s, a.h))};
+}
+
+// (a + b, a - b) of two scalars' double-float values in one packed addition
+__device__ __forceinline__ df2 df2_sumdiff(dfl a, dfl b) {
+  return df2_add(df2_pack(a, a), df2{make_float2(b.h, -b.h), make_float2(b.l, -b.l)});
+}
+
 // tables of every compiled (P, Q) as (hi, lo) pairs: slot as in c_tab32
 __constant__ float c_tabdf[TAB_SLOT * TAB_SLOTS * 2];
 
@@ -116,55 +168,58 @@ __constant__ float c_tabdf[TAB_SLOT * TAB_SLOTS * 2];
 //   y_o = E_o + O_o,  y_{NO-1-o} = S (E_o - O_o)   (o < NO/2),
 // and for odd NO the middle output is sum_i M(mid, i) x(+ or -)_i (+ M(mid, mid) x_mid
 // when S = +1): half the multiply-adds of the direct form for n + Q extra additions.
-// Tables per q = p + 2 slot (p - 1): matrices 0 B, 1 G (Q x n), 2 B^T, 3 G^T (n x Q), each
-// EO_MAT (hi, lo) pairs: e (NO/2 x NI/2), d, M(o, mid) (o < NO/2), M(mid, i) (i <= NI/2).
-constexpr int EO_MAT = 52;
-__constant__ float c_tabeo[FEPA_MAX_ORDER * 4 * EO_MAT * 2];
+// E_o and O_o are accumulated side by side as one packed pair (df2 below), so their tables are
+// stored as pairs too.  Tables per q = p + 2 slot (p - 1): matrices 0 B, 1 G (Q x n), 2 B^T,
+// 3 G^T (n x Q), each EO_MAT entries of a hi pair and a lo pair (float2 each):
+// (e(o,i), d(o,i)) for o < NO/2, i < NI/2, then (M(o, mid), 0) for o < NO/2, then
+// (M(mid, i), 0) for i <= NI/2.
+constexpr int EO_MAT = 30;
+__constant__ float2 c_tabeo[FEPA_MAX_ORDER * 4 * EO_MAT * 2];
 
 template <int P, int MAT>
 struct TabEo {
   static constexpr int NO = MAT < 2 ? P + 2 : P + 1, NI = MAT < 2 ? P + 1 : P + 2;
   static constexpr int HO = NO / 2, HI = NI / 2;
-  static_assert(2 * HO * HI + HO + HI + 1 <= EO_MAT, "even/odd table size");
+  static_assert(HO * HI + HO + HI + 1 <= EO_MAT, "even/odd table size");
   static constexpr int OFF = ((P - 1) * 4 + MAT) * EO_MAT * 2;
-  static __device__ __forceinline__ dfl at(int k) { return {c_tabeo[OFF + 2 * k], c_tabeo[OFF + 2 * k + 1]}; }
-  static __device__ __forceinline__ dfl E(int o, int i) { return at(o * HI + i); }
-  static __device__ __forceinline__ dfl D(int o, int i) { return at(HO * HI + o * HI + i); }
-  static __device__ __forceinline__ dfl MC(int o) { return at(2 * HO * HI + o); }
-  static __device__ __forceinline__ dfl MR(int i) { return at(2 * HO * HI + HO + i); }
+  static __device__ __forceinline__ float2 hp(int k) { return c_tabeo[OFF + 2 * k]; }
+  static __device__ __forceinline__ float2 lp(int k) { return c_tabeo[OFF + 2 * k + 1]; }
+  // (e(o,i), d(o,i)) as hi and lo pairs
+  static __device__ __forceinline__ float2 EDh(int o, int i) { return hp(o * HI + i); }
+  static __device__ __forceinline__ float2 EDl(int o, int i) { return lp(o * HI + i); }
+  static __device__ __forceinline__ dfl E(int o, int i) { return {EDh(o, i).x, EDl(o, i).x}; }
+  static __device__ __forceinline__ dfl D(int o, int i) { return {EDh(o, i).y, EDl(o, i).y}; }
+  static __device__ __forceinline__ dfl MC(int o) { return {hp(HO * HI + o).x, lp(HO * HI + o).x}; }
+  static __device__ __forceinline__ dfl MR(int i) { return {hp(HO * HI + HO + i).x, lp(HO * HI + HO + i).x}; }
 };
 
-// x+ and x- of the mirrored input pairs
+// the mirrored input pairs packed as (x+_i, x-_i)
 template <int NI>
-__device__ __forceinline__ void eo_split(const dfl (&x)[NI], dfl (&xp)[NI / 2], dfl (&xm)[NI / 2]) {
+__device__ __forceinline__ void eo_split2(const dfl (&x)[NI], df2 (&xpm)[NI / 2]) {
 #pragma unroll
-  for (int i = 0; i < NI / 2; ++i) {
-    xp[i] = df_add(x[i], x[NI - 1 - i]);
-    xm[i] = df_sub(x[i], x[NI - 1 - i]);
-  }
+  for (int i = 0; i < NI / 2; ++i) xpm[i] = df2_sumdiff(x[i], x[NI - 1 - i]);
 }
 
-// y = M x from the split input (outputs normalised)
+// y = M x from the packed split input: E_o and O_o accumulate as one pair; the mirrored
+// outputs E_o + O_o and E_o - O_o come from one packed addition
 template <class TE, int S>
-__device__ __forceinline__ void eo_apply(const dfl (&xp)[TE::HI], const dfl (&xm)[TE::HI], dfl xmid,
-                                         dfl (&y)[TE::NO]) {
+__device__ __forceinline__ void eo_apply2(const df2 (&xpm)[TE::HI], dfl xmid, dfl (&y)[TE::NO]) {
   constexpr int HO = TE::HO, HI = TE::HI, NO = TE::NO, NI = TE::NI;
 #pragma unroll
   for (int o = 0; o < HO; ++o) {
-    dfl e = df_zero(), d = df_zero();
+    df2 ed = df2_zero();
 #pragma unroll
-    for (int i = 0; i < HI; ++i) {
-      df_fma(e, TE::E(o, i), xp[i]);
-      df_fma(d, TE::D(o, i), xm[i]);
-    }
+    for (int i = 0; i < HI; ++i) df2_fma(ed, TE::EDh(o, i), TE::EDl(o, i), xpm[i].h, xpm[i].l);
+    dfl e = df2_x(ed);
     if (NI % 2) df_fma(e, TE::MC(o), xmid);
-    y[o] = df_add(e, d);
-    y[NO - 1 - o] = S > 0 ? df_sub(e, d) : df_sub(d, e);
+    const df2 r = df2_sumdiff(e, df2_y(ed));  // (e + d, e - d)
+    y[o] = df2_x(r);
+    y[NO - 1 - o] = S > 0 ? df2_y(r) : df_neg(df2_y(r));
   }
   if (NO % 2) {
     dfl m = df_zero();
 #pragma unroll
-    for (int i = 0; i < HI; ++i) df_fma(m, TE::MR(i), S > 0 ? xp[i] : xm[i]);
+    for (int i = 0; i < HI; ++i) df_fma(m, TE::MR(i), S > 0 ? df2_x(xpm[i]) : df2_y(xpm[i]));
     if (S > 0 && NI % 2) df_fma(m, TE::MR(HI), xmid);
     y[HO] = df_norm(m);
   }
@@ -312,10 +367,11 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
 #pragma unroll
     for (int a = 0; a < n; ++a) xv[a] = sX[tid * L::XL + a];
     if constexpr (EO) {
-      dfl xp[n / 2], xm[n / 2], yb[Q], yg[Q];
-      eo_split<n>(xv, xp, xm);
-      eo_apply<EB, 1>(xp, xm, xv[n / 2], yb);
-      if (DIFF) eo_apply<EG, -1>(xp, xm, xv[n / 2], yg);
+      df2 xpm[n / 2];
+      dfl yb[Q], yg[Q];
+      eo_split2<n>(xv, xpm);
+      eo_apply2<EB, 1>(xpm, xv[n / 2], yb);
+      if (DIFF) eo_apply2<EG, -1>(xpm, xv[n / 2], yg);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         S1[tid * DQ1 + i] = yb[i];
@@ -347,19 +403,20 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
       if (DIFF) vg[b] = S1[L::S1C + (b + n * c) * DQ1 + i];
     }
     if constexpr (EO) {
-      dfl bp[n / 2], bm[n / 2], yb[Q];
-      eo_split<n>(vb, bp, bm);
-      eo_apply<EB, 1>(bp, bm, vb[n / 2], yb);
+      df2 bpm[n / 2];
+      dfl yb[Q];
+      eo_split2<n>(vb, bpm);
+      eo_apply2<EB, 1>(bpm, vb[n / 2], yb);
 #pragma unroll
       for (int j = 0; j < Q; ++j) S2[(DIFF ? 2 * L::S2C : 0) + c * L::P2 + j * Q + i] = yb[j];
       if (DIFF) {
         dfl yg[Q];
-        eo_apply<EG, -1>(bp, bm, vb[n / 2], yg);
+        eo_apply2<EG, -1>(bpm, vb[n / 2], yg);
 #pragma unroll
         for (int j = 0; j < Q; ++j) S2[L::S2C + c * L::P2 + j * Q + i] = yg[j];
-        dfl gp[n / 2], gm[n / 2];
-        eo_split<n>(vg, gp, gm);
-        eo_apply<EB, 1>(gp, gm, vg[n / 2], yg);
+        df2 gpm[n / 2];
+        eo_split2<n>(vg, gpm);
+        eo_apply2<EB, 1>(gpm, vg[n / 2], yg);
 #pragma unroll
         for (int j = 0; j < Q; ++j) S2[c * L::P2 + j * Q + i] = yg[j];
       }
@@ -410,20 +467,51 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
       // accumulate into the even (E) and odd (O) halves of a (mirrored outputs recombined
       // at the end)
       constexpr int HN = n / 2, HQ = Q / 2;
-      dfl c0p[HN], c0m[HN], c1p[HN], c1m[HN], c2p[HN], c2m[HN];
-      dfl ae0[HN], ao0[HN], ae1[HN], ao1[HN], ae2[HN], ao2[HN];
+      // packed pairs: (c+, c-) of the column, (E, O) of the z contraction, (p, q) of v at the
+      // point pair, (a_E, a_O) of the transposed contraction; D of both points as pairs
+      df2 cpm0[HN], cpm1[HN], cpm2[HN], aeo0[HN], aeo1[HN], aeo2[HN];
       dfl am0 = df_zero(), am1 = df_zero(), am2 = df_zero();
-      eo_split<n>(c0, c0p, c0m);
+      eo_split2<n>(c0, cpm0);
       if (DIFF) {
-        eo_split<n>(c1, c1p, c1m);
-        eo_split<n>(c2, c2p, c2m);
+        eo_split2<n>(c1, cpm1);
+        eo_split2<n>(c2, cpm2);
       }
 #pragma unroll
       for (int c = 0; c < HN; ++c) {
-        ae0[c] = ao0[c] = df_zero();
-        if (DIFF) ae1[c] = ao1[c] = ae2[c] = ao2[c] = df_zero();
+        aeo0[c] = df2_zero();
+        if (DIFF) aeo1[c] = aeo2[c] = df2_zero();
       }
-      // v = D u at point k (diffusion: symmetric 3 x 3; mass: scalar)
+      // v = D u at points ka (.x) and kb (.y) (diffusion: symmetric 3 x 3; mass: scalar)
+      auto dpoint2 = [&](int ka, int kb, df2 u0, df2 u1, df2 u2, df2& v0, df2& v1, df2& v2) {
+        float2 dh[L::NC], dl[L::NC];
+#pragma unroll
+        for (int m = 0; m < L::NC; ++m) {
+          const float2 da = __ldg(dE + ka * Q * Q + m * L::Q3), db = __ldg(dE + kb * Q * Q + m * L::Q3);
+          dh[m] = make_float2(da.x, db.x);
+          dl[m] = make_float2(da.y, db.y);
+        }
+        if (DIFF) {
+          const int i1 = 1 % L::NC, i2 = 2 % L::NC, i3 = 3 % L::NC, i4 = 4 % L::NC, i5 = 5 % L::NC;
+          v0 = df2_zero(); v1 = df2_zero(); v2 = df2_zero();
+          df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
+          df2_fma(v0, dh[i1], dl[i1], u1.h, u1.l);
+          df2_fma(v0, dh[i2], dl[i2], u2.h, u2.l);
+          df2_fma(v1, dh[i1], dl[i1], u0.h, u0.l);
+          df2_fma(v1, dh[i3], dl[i3], u1.h, u1.l);
+          df2_fma(v1, dh[i4], dl[i4], u2.h, u2.l);
+          df2_fma(v2, dh[i2], dl[i2], u0.h, u0.l);
+          df2_fma(v2, dh[i4], dl[i4], u1.h, u1.l);
+          df2_fma(v2, dh[i5], dl[i5], u2.h, u2.l);
+          v0 = df2_norm(v0);
+          v1 = df2_norm(v1);
+          v2 = df2_norm(v2);
+        } else {
+          v0 = df2_zero();
+          df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
+          v0 = df2_norm(v0);
+        }
+      };
+      // v = D u at one point k (the middle point of an odd Q), scalar
       auto dpoint = [&](int k, dfl u0, dfl u1, dfl u2, dfl& v0, dfl& v1, dfl& v2) {
         float2 dc[L::NC];
 #pragma unroll
@@ -454,18 +542,16 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
 #pragma unroll KU
       for (int kk = 0; kk < HQ; ++kk) {
         const int k2 = Q - 1 - kk;
-        dfl e0 = df_zero(), o0 = df_zero(), e1 = df_zero(), o1 = df_zero(), e2 = df_zero(), o2 = df_zero();
+        df2 eo0 = df2_zero(), eo1 = df2_zero(), eo2 = df2_zero();  // (E, O)
 #pragma unroll
         for (int i = 0; i < HN; ++i) {
-          df_fma(e0, EB::E(kk, i), c0p[i]);
-          df_fma(o0, EB::D(kk, i), c0m[i]);
+          df2_fma(eo0, EB::EDh(kk, i), EB::EDl(kk, i), cpm0[i].h, cpm0[i].l);
           if (DIFF) {
-            df_fma(e1, EB::E(kk, i), c1p[i]);
-            df_fma(o1, EB::D(kk, i), c1m[i]);
-            df_fma(e2, EG::E(kk, i), c2p[i]);
-            df_fma(o2, EG::D(kk, i), c2m[i]);
+            df2_fma(eo1, EB::EDh(kk, i), EB::EDl(kk, i), cpm1[i].h, cpm1[i].l);
+            df2_fma(eo2, EG::EDh(kk, i), EG::EDl(kk, i), cpm2[i].h, cpm2[i].l);
           }
         }
+        dfl e0 = df2_x(eo0), e1 = df2_x(eo1), e2 = df2_x(eo2);
         if (n % 2) {
           df_fma(e0, EB::MC(kk), c0[HN]);
           if (DIFF) {
@@ -473,38 +559,37 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
             df_fma(e2, EG::MC(kk), c2[HN]);
           }
         }
-        dfl va0, va1, va2, vb0, vb1, vb2;  // v at kk and at k2
+        // u at (kk, k2): (E + O, E - O); the G component's mirror is O - E
+        const df2 u0 = df2_sumdiff(e0, df2_y(eo0));
+        df2 u1 = u0, u2 = u0;
         if (DIFF) {
-          dpoint(kk, df_add(e0, o0), df_add(e1, o1), df_add(e2, o2), va0, va1, va2);
-          dpoint(k2, df_sub(e0, o0), df_sub(e1, o1), df_sub(o2, e2), vb0, vb1, vb2);
-        } else {
-          dpoint(kk, df_add(e0, o0), e1, e2, va0, va1, va2);
-          dpoint(k2, df_sub(e0, o0), e1, e2, vb0, vb1, vb2);
+          u1 = df2_sumdiff(e1, df2_y(eo1));
+          u2 = df2_sumdiff(e2, df2_y(eo2));
+          u2.h.y = -u2.h.y;
+          u2.l.y = -u2.l.y;
         }
-        const dfl p0 = df_add(va0, vb0), q0 = df_sub(va0, vb0);
-        dfl p1, q1, p2, q2;
+        df2 v0, v1, v2;
+        dpoint2(kk, k2, u0, u1, u2, v0, v1, v2);
+        // (p, q) = (v(kk) + v(k2), v(kk) - v(k2))
+        const df2 pq0 = df2_sumdiff(df2_x(v0), df2_y(v0));
+        df2 pq1 = pq0, pq2 = pq0;
         if (DIFF) {
-          p1 = df_add(va1, vb1);
-          q1 = df_sub(va1, vb1);
-          p2 = df_add(va2, vb2);
-          q2 = df_sub(va2, vb2);
+          pq1 = df2_sumdiff(df2_x(v1), df2_y(v1));
+          pq2 = df2_sumdiff(df2_x(v2), df2_y(v2));
         }
 #pragma unroll
         for (int c = 0; c < HN; ++c) {
-          df_fma(ae0[c], EBT::E(c, kk), p0);
-          df_fma(ao0[c], EBT::D(c, kk), q0);
+          df2_fma(aeo0[c], EBT::EDh(c, kk), EBT::EDl(c, kk), pq0.h, pq0.l);
           if (DIFF) {
-            df_fma(ae1[c], EBT::E(c, kk), p1);
-            df_fma(ao1[c], EBT::D(c, kk), q1);
-            df_fma(ae2[c], EGT::E(c, kk), p2);
-            df_fma(ao2[c], EGT::D(c, kk), q2);
+            df2_fma(aeo1[c], EBT::EDh(c, kk), EBT::EDl(c, kk), pq1.h, pq1.l);
+            df2_fma(aeo2[c], EGT::EDh(c, kk), EGT::EDl(c, kk), pq2.h, pq2.l);
           }
         }
         if (n % 2) {
-          df_fma(am0, EBT::MR(kk), p0);
+          df_fma(am0, EBT::MR(kk), df2_x(pq0));
           if (DIFF) {
-            df_fma(am1, EBT::MR(kk), p1);
-            df_fma(am2, EGT::MR(kk), q2);
+            df_fma(am1, EBT::MR(kk), df2_x(pq1));
+            df_fma(am2, EGT::MR(kk), df2_y(pq2));
           }
         }
       }
@@ -512,10 +597,10 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
         dfl u0 = df_zero(), u1 = df_zero(), u2 = df_zero();
 #pragma unroll
         for (int i = 0; i < HN; ++i) {
-          df_fma(u0, EB::MR(i), c0p[i]);
+          df_fma(u0, EB::MR(i), df2_x(cpm0[i]));
           if (DIFF) {
-            df_fma(u1, EB::MR(i), c1p[i]);
-            df_fma(u2, EG::MR(i), c2m[i]);
+            df_fma(u1, EB::MR(i), df2_x(cpm1[i]));
+            df_fma(u2, EG::MR(i), df2_y(cpm2[i]));
           }
         }
         if (n % 2) {
@@ -526,10 +611,18 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
         dpoint(HQ, df_norm(u0), df_norm(u1), df_norm(u2), v0, v1, v2);
 #pragma unroll
         for (int c = 0; c < HN; ++c) {
-          df_fma(ae0[c], EBT::MC(c), v0);
+          dfl t0 = df2_x(aeo0[c]);
+          df_fma(t0, EBT::MC(c), v0);
+          aeo0[c].h.x = t0.h;
+          aeo0[c].l.x = t0.l;
           if (DIFF) {
-            df_fma(ae1[c], EBT::MC(c), v1);
-            df_fma(ae2[c], EGT::MC(c), v2);
+            dfl t1 = df2_x(aeo1[c]), t2 = df2_x(aeo2[c]);
+            df_fma(t1, EBT::MC(c), v1);
+            df_fma(t2, EGT::MC(c), v2);
+            aeo1[c].h.x = t1.h;
+            aeo1[c].l.x = t1.l;
+            aeo2[c].h.x = t2.h;
+            aeo2[c].l.x = t2.l;
           }
         }
         if (n % 2) {
@@ -539,13 +632,16 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
       }
 #pragma unroll
       for (int c = 0; c < HN; ++c) {
-        a0[c] = df_add(ae0[c], ao0[c]);
-        a0[n - 1 - c] = df_sub(ae0[c], ao0[c]);
+        const df2 r0 = df2_sumdiff(df2_x(aeo0[c]), df2_y(aeo0[c]));
+        a0[c] = df2_x(r0);
+        a0[n - 1 - c] = df2_y(r0);
         if (DIFF) {
-          a1[c] = df_add(ae1[c], ao1[c]);
-          a1[n - 1 - c] = df_sub(ae1[c], ao1[c]);
-          a2[c] = df_add(ae2[c], ao2[c]);
-          a2[n - 1 - c] = df_sub(ao2[c], ae2[c]);
+          const df2 r1 = df2_sumdiff(df2_x(aeo1[c]), df2_y(aeo1[c]));
+          const df2 r2 = df2_sumdiff(df2_x(aeo2[c]), df2_y(aeo2[c]));
+          a1[c] = df2_x(r1);
+          a1[n - 1 - c] = df2_y(r1);
+          a2[c] = df2_x(r2);
+          a2[n - 1 - c] = df_neg(df2_y(r2));
         }
       }
       if (n % 2) {
@@ -631,17 +727,19 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
       }
     }
     if constexpr (EO) {
-      dfl p0[Q / 2], m0[Q / 2], y0[n];
-      eo_split<Q>(v0, p0, m0);
-      eo_apply<EBT, 1>(p0, m0, v0[Q / 2], y0);
+      df2 pm0[Q / 2];
+      dfl y0[n];
+      eo_split2<Q>(v0, pm0);
+      eo_apply2<EBT, 1>(pm0, v0[Q / 2], y0);
 #pragma unroll
       for (int b = 0; b < n; ++b) S1[(b + n * c) * DQ1 + i] = y0[b];
       if (DIFF) {
-        dfl p1[Q / 2], m1[Q / 2], y1[n];
-        eo_split<Q>(v1, p1, m1);
-        eo_apply<EGT, -1>(p1, m1, v1[Q / 2], y1);
-        eo_split<Q>(v2, p0, m0);
-        eo_apply<EBT, 1>(p0, m0, v2[Q / 2], y0);
+        df2 pm1[Q / 2];
+        dfl y1[n];
+        eo_split2<Q>(v1, pm1);
+        eo_apply2<EGT, -1>(pm1, v1[Q / 2], y1);
+        eo_split2<Q>(v2, pm0);
+        eo_apply2<EBT, 1>(pm0, v2[Q / 2], y0);
 #pragma unroll
         for (int b = 0; b < n; ++b) S1[L::S1C + (b + n * c) * DQ1 + i] = df_add(y1[b], y0[b]);
       }
@@ -674,17 +772,18 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
     }
     dfl ys[n];
     if constexpr (EO) {
-      dfl pp[Q / 2], mm[Q / 2], yb[n];
+      df2 ppm[Q / 2];
+      dfl yb[n];
       if (DIFF) {
-        eo_split<Q>(t0, pp, mm);
-        eo_apply<EGT, -1>(pp, mm, t0[Q / 2], ys);
-        eo_split<Q>(t1, pp, mm);
-        eo_apply<EBT, 1>(pp, mm, t1[Q / 2], yb);
+        eo_split2<Q>(t0, ppm);
+        eo_apply2<EGT, -1>(ppm, t0[Q / 2], ys);
+        eo_split2<Q>(t1, ppm);
+        eo_apply2<EBT, 1>(ppm, t1[Q / 2], yb);
 #pragma unroll
         for (int a = 0; a < n; ++a) ys[a] = df_add(ys[a], yb[a]);
       } else {
-        eo_split<Q>(t0, pp, mm);
-        eo_apply<EBT, 1>(pp, mm, t0[Q / 2], ys);
+        eo_split2<Q>(t0, ppm);
+        eo_apply2<EBT, 1>(ppm, t0[Q / 2], ys);
       }
     } else {
 #pragma unroll
