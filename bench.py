@@ -149,10 +149,10 @@ FP64_PEAK_GFLOPS = 1250.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of the
 # current apply kernels on the default workload: captured at 40^3 elements (412.9 / 413.0 MB FP32
 # variants 1 / 2, 413.0 MB variant 1 with (d, A d) fused -- re-taken with the packed-FMA build, same
-# bytes --, 794.5 MB double-float with its exponent-range test: the algorithmic bytes, y read once
-# for the atomics) and scaled to 64^3 by elements (D, map) and DOFs (x, y).
+# bytes --, 795.3 MB double-float in packed pairs with its exponent-range test: the algorithmic
+# bytes, y read once for the atomics) and scaled to 64^3 by elements (D, map) and DOFs (x, y).
 # Only reported when that kernel is timed.
-NCU_TRAFFIC_P4_N64 = {"f32_v1": 1.6910e9, "f32_v2": 1.6916e9, "f32dot_v1": 1.6914e9, "df": 3.2555e9}
+NCU_TRAFFIC_P4_N64 = {"f32_v1": 1.6910e9, "f32_v2": 1.6916e9, "f32dot_v1": 1.6914e9, "df": 3.2589e9}
 # ceiling of the double-float FP64 action: 12 FP32-pipe instructions per FP64-accurate
 # multiply-add (exact product by FMA, TwoSum accumulation) on 128 FP32 lanes/SM x 148 SMs
 # at 2.032 GHz, 2 flops per multiply-add

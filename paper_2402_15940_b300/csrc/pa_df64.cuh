@@ -256,14 +256,15 @@ struct DfShape {
 // Lower orders and the mass form are fastest with no constraint (an explicit minimum
 // of 1 lets the allocator take up to 255 registers: 1.1-2x slower); the mass form rolls
 // its (short) stage-3 loop from p = 6 on.
-// EO3: stage 3 (z, D, z^T) also in even/odd form over mirrored point pairs (q = p + 2).
-// Measured against the even/odd line stages alone: mass 1-7 % faster; diffusion p = 3, 4, 8
-// 4-8 % faster, p = 2, 5, 6, 7 2-18 % slower (more live values: spills at p = 6, 7).
+// EO3: stage 3 (z, D, z^T) also in even/odd form over mirrored point pairs (q = p + 2), in
+// packed pairs.  Measured (stand-alone launches against the scalar build): diffusion p = 4
+// 12 %, p = 5 9 %, p = 6 19 %, p = 7 24 %, p = 8 32 % faster; at p = 2 13 % slower than the
+// direct stage 3 (kept there).  (Before the packed form it was slower at p = 5, 6, 7.)
 template <int P, int Q, bool DIFF>
 struct DfTune {
   static constexpr int MINB = (DIFF && P >= 4) ? 2 : 0;
   static constexpr int KU = (P >= (DIFF ? 4 : 6)) ? 1 : Q;
-  static constexpr bool EO3 = DIFF ? (P == 3 || P == 4 || P == 8) : (P >= 2);
+  static constexpr bool EO3 = DIFF ? (P >= 3) : (P >= 2);
 };
 
 // The block's work on one tile of ne <= NE consecutive elements starting at e0 (called once per
