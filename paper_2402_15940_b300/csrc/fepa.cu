@@ -558,6 +558,45 @@ void init_tuned() {
   g_tuned_init = true;
 }
 
+// Time the launch functions run(v) of the enabled variants v < nvar on stream s: two warm-up
+// calls each, then three rounds, each timing 5 calls of every variant in turn; a variant's time
+// is its best round, so that a round slowed by other work on the GPU (another stream of a
+// serving process, say) does not decide the choice, which is cached for the process.
+template <class Run, class Enabled>
+int time_rounds(cudaStream_t s, int nvar, Run run, Enabled enabled, int* best) {
+  constexpr int ROUNDS = 3, REPS = 5;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(FEPA_ERR_CUDA, "event creation failed");
+  }
+  std::vector<float> t(nvar, 1e30f);
+  int rc = FEPA_OK;
+  for (int v = 0; rc == FEPA_OK && v < nvar; ++v)
+    for (int w = 0; w < 2 && rc == FEPA_OK && enabled(v); ++w) rc = run(v);
+  for (int round = 0; rc == FEPA_OK && round < ROUNDS; ++round)
+    for (int v = 0; rc == FEPA_OK && v < nvar; ++v) {
+      if (!enabled(v)) continue;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < REPS && rc == FEPA_OK; ++r) rc = run(v);
+      cudaEventRecord(e1, s);
+      if (rc != FEPA_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(FEPA_ERR_CUDA, "autotune timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t[v] = std::min(t[v], ms);
+    }
+  *best = 0;
+  for (int v = 0; v < nvar; ++v)
+    if (enabled(v) && (!enabled(*best) || t[v] < t[*best])) *best = v;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 int time_variants32(fepa_op* op, int* best) {
   cudaStream_t s = op->stream;
   float *x = nullptr, *y = nullptr;
@@ -580,34 +619,10 @@ int time_variants32(fepa_op* op, int* best) {
     g_launches.fetch_add(2);
     return FEPA_OK;
   };
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  float best_ms = 1e30f;
   *best = 0;
-  if (rc == FEPA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-    rc = fail(FEPA_ERR_CUDA, "event creation failed");
   if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(float), s) != cudaSuccess)
     rc = fail(FEPA_ERR_CUDA, "memset failed");
-  for (int v = 0; rc == FEPA_OK && v < N32_VARIANTS; ++v) {
-    if (op->v32_grid[v] <= 0) continue;
-    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = run(v);
-    if (rc != FEPA_OK) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = run(v);
-    cudaEventRecord(e1, s);
-    if (rc != FEPA_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      rc = fail(FEPA_ERR_CUDA, "autotune timing failed");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      *best = v;
-    }
-  }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
+  if (rc == FEPA_OK) rc = time_rounds(s, N32_VARIANTS, run, [&](int v) { return op->v32_grid[v] > 0; }, best);
   cudaFree(x);
   if (y) cudaFree(y);
   if (slots) cudaFree(slots);
@@ -649,35 +664,15 @@ int time_variants64(fepa_op* op, int* best) {
   double *x = nullptr, *y = nullptr;
   TRY(dalloc(&x, op->N));
   int rc = dalloc(&y, op->N);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  float best_ms = 1e30f;
   *best = 0;
-  if (rc == FEPA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
-    rc = fail(FEPA_ERR_CUDA, "event creation failed");
   if (rc == FEPA_OK && cudaMemsetAsync(x, 0, op->N * sizeof(double), s) != cudaSuccess)
     rc = fail(FEPA_ERR_CUDA, "memset failed");
   if (rc == FEPA_OK) rc = ensure_df(op);
-  for (int v = 0; rc == FEPA_OK && v < N64_VARIANTS; ++v) {
-    for (int w = 0; w < 2 && rc == FEPA_OK; ++w) rc = launch_apply64_variant(op, v, x, y, nullptr, s);
-    if (rc != FEPA_OK) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 5 && rc == FEPA_OK; ++r) rc = launch_apply64_variant(op, v, x, y, nullptr, s);
-    cudaEventRecord(e1, s);
-    if (rc != FEPA_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      rc = fail(FEPA_ERR_CUDA, "autotune timing failed");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    g_launches.fetch_add(7);
-    if (ms < best_ms) {
-      best_ms = ms;
-      *best = v;
-    }
-  }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
+  auto run = [&](int v) -> int {
+    g_launches.fetch_add(1);
+    return launch_apply64_variant(op, v, x, y, nullptr, s);
+  };
+  if (rc == FEPA_OK) rc = time_rounds(s, N64_VARIANTS, run, [](int) { return true; }, best);
   cudaFree(x);
   if (y) cudaFree(y);
   return rc;
