@@ -269,9 +269,11 @@ int fepa_op_apply_f32_dot(fepa_op* op, const float* x, float* y, double* xax);
  * current group's arithmetic).  By default (variant -1) the first FP32 use
  * times every variant on this op's mesh, in the form the FP32 CG loop launches it (with
  * (x, A x) fused where the variant has that build and fused products are enabled, else
- * with the separate dot-product pass), and keeps the fastest; the choice is cached per
- * device, (p, q, form) and mesh size class (E < 1e3, 1e4, 1e5, larger) for the process.
- * All variants compute the same result (up to the order of the atomic additions).
+ * with the separate dot-product pass), in three rounds, each variant's best round
+ * counting, and keeps the fastest; the choice is cached per device, (p, q, form) and mesh
+ * size class (E < 1e3, 1e4, 1e5, larger) for the process.  All variants compute the same
+ * result (up to the order of the atomic additions); their contractions issue two FP32
+ * multiply-adds per packed instruction where that measured faster for the (p, q, form).
  */
 int fepa_op_set_f32_variant(fepa_op* op, int32_t variant);
 int32_t fepa_op_f32_variant(const fepa_op* op);          /* -1 until chosen */
@@ -282,16 +284,17 @@ const char* fepa_f32_variant_name(int32_t variant);
  * Variants: 0 = native FP64 (DFMA), 1 = double-float: x is split into two floats
  * (hi + lo) as it is gathered and D is read as (hi, lo) pairs (a copy of D kept beside
  * the FP64 one, 8 bytes per value), every contraction step is an accurate dot-product
- * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative error),
- * and the element result is recombined in FP64 -- error far inside the FP64 action's
- * tolerance.  Each block checks the exponents of its gathered x against D's largest
+ * step on the FP32 pipe (exact FMA product, TwoSum accumulation, ~2^-48 relative error;
+ * the even/odd halves of output pairs in packed two-wide instructions, bit-identical per
+ * component), and the element result is recombined in FP64 -- error far inside the FP64
+ * action's tolerance.  Each block checks the exponents of its gathered x against D's largest
  * exponent (found by the geometry kernel) and, where the products would leave the
  * float range less the low word's 24 bits, re-gathers x times an exact power of two and
  * scales the results back (a second pass over the block's x, rare).  This library's own
  * design for a GPU whose FP64 rate is a small fraction of its FP32 rate; the paper's
  * FP64 kernels have no counterpart.  By default (-1) the first FP64 use times both on
- * this op's mesh and keeps the faster; cached per device, (p, q, form) and mesh size
- * class.  The allocation-free solve never times: it uses the chosen or forced variant
+ * this op's mesh (three rounds, best round each) and keeps the faster; cached per device,
+ * (p, q, form) and mesh size class.  The allocation-free solve never times: it uses the chosen or forced variant
  * (the double-float one only if its copy of D is current), else 0.
  */
 int fepa_op_set_f64_variant(fepa_op* op, int32_t variant);
