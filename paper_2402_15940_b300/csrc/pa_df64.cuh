@@ -249,13 +249,15 @@ struct DfShape {
 
 // PF: L2 prefetch of the group's D and map at block start (as in pa_tma_f32.cuh; 4-9 %).
 // MINB: resident blocks per SM the register allocation must allow (0: no constraint);
-// KU: unroll of the stage-3 quadrature loop (Q = fully unrolled).  Measured on B300:
-// for diffusion from p = 4 on, a fully unrolled stage 3 holds 100-255 registers and one
-// or two blocks per SM; with the loop rolled (tables read per k from constant memory)
-// and two blocks per SM guaranteed, p = 4 runs 1.08x, p = 6 2.7x and p = 8 2.2x faster.
-// Lower orders and the mass form are fastest with no constraint (an explicit minimum
-// of 1 lets the allocator take up to 255 registers: 1.1-2x slower); the mass form rolls
-// its (short) stage-3 loop from p = 6 on.
+// KU: unroll of the stage-3 quadrature loop (Q = fully unrolled).  Measured on B300 with
+// the scalar arithmetic: for diffusion from p = 4 on, a fully unrolled stage 3 held 100-255
+// registers and one or two blocks per SM; with the loop rolled (tables read per k from
+// constant memory) and two blocks per SM guaranteed, p = 4 ran 1.08x, p = 6 2.7x and p = 8
+// 2.2x faster.  Lower orders and the mass form are fastest with no constraint (an explicit
+// minimum of 1 lets the allocator take up to 255 registers: 1.1-2x slower).  With the
+// packed pairs (two blocks per SM kept), a fully unrolled stage 3 is faster again for
+// diffusion p = 4, 5, 6 (4 %, 9 %, 2 %) and mass p = 6, 8 (15 %, 13 %); p = 7 equal, p = 8
+// 16 % slower (rolled there).
 // EO3: stage 3 (z, D, z^T) also in even/odd form over mirrored point pairs (q = p + 2), in
 // packed pairs.  Measured (stand-alone launches against the scalar build): diffusion p = 4
 // 12 %, p = 5 9 %, p = 6 19 %, p = 7 24 %, p = 8 32 % faster; at p = 2 13 % slower than the
@@ -263,7 +265,7 @@ struct DfShape {
 template <int P, int Q, bool DIFF>
 struct DfTune {
   static constexpr int MINB = (DIFF && P >= 4) ? 2 : 0;
-  static constexpr int KU = (P >= (DIFF ? 4 : 6)) ? 1 : Q;
+  static constexpr int KU = (DIFF && P >= 7) ? 1 : Q;
   static constexpr bool EO3 = DIFF ? (P >= 3) : (P >= 2);
 };
 
