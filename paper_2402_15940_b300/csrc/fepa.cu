@@ -198,18 +198,23 @@ const KernelTable& kernels() {
 // (hi, lo) float pairs of the FP64 1D tables for the double-float action, into the
 // constant-memory slot of (p, q)
 int upload_df_tables(int p, int q, const std::vector<double>& Bh, const std::vector<double>& Gh, cudaStream_t s) {
-  const int n = p + 1;
-  std::vector<float> tdf(2 * TAB_SLOT, 0.f);
-  for (int k = 0; k < q * n; ++k) {
-    const float bh = (float)Bh[k], gh = (float)Gh[k];
-    tdf[2 * k] = bh;
-    tdf[2 * k + 1] = (float)(Bh[k] - (double)bh);
-    tdf[2 * (100 + k)] = gh;
-    tdf[2 * (100 + k) + 1] = (float)(Gh[k] - (double)gh);
-  }
-  const size_t slot = (size_t)((p - 1) * 2 + (q - p - 1)) * TAB_SLOT * 2;
-  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float), slot * sizeof(float),
-                                   cudaMemcpyHostToDevice, s));
+  const int n = p + 1, qh = (q + 1) / 2, nh = (n + 1) / 2;
+  // the pair layout of TabDf: (hi pair, lo pair) per entry; rows then columns, B then G
+  std::vector<float2> tdf;
+  tdf.reserve(2 * tab32_slot_pairs(p, q));
+  auto put_pair = [&](double a, double b) {
+    const float ah = (float)a, bh = (float)b;
+    tdf.push_back(make_float2(ah, bh));
+    tdf.push_back(make_float2((float)(a - (double)ah), (float)(b - (double)bh)));
+  };
+  for (const std::vector<double>* T : {&Bh, &Gh})
+    for (int kp = 0; kp < qh; ++kp)
+      for (int a = 0; a < n; ++a) put_pair((*T)[2 * kp * n + a], 2 * kp + 1 < q ? (*T)[(2 * kp + 1) * n + a] : 0.0);
+  for (const std::vector<double>* T : {&Bh, &Gh})
+    for (int k = 0; k < q; ++k)
+      for (int ap = 0; ap < nh; ++ap) put_pair((*T)[k * n + 2 * ap], 2 * ap + 1 < n ? (*T)[k * n + 2 * ap + 1] : 0.0);
+  CUDA_TRY(cudaMemcpyToSymbolAsync(c_tabdf, tdf.data(), tdf.size() * sizeof(float2),
+                                   2 * (size_t)tab32_offset(p, q) * sizeof(float2), cudaMemcpyHostToDevice, s));
   if (q != p + 2) return FEPA_OK;
   // even/odd tables of B, G (q x n) and B^T, G^T (n x q) for the double-float action
   // entry k of matrix mat: a hi pair then a lo pair; half 0 (x) or 1 (y) of the pair

@@ -155,8 +155,11 @@ __device__ __forceinline__ df2 df2_sumdiff(dfl a, dfl b) {
   return df2_add(df2_pack(a, a), df2{make_float2(b.h, -b.h), make_float2(b.l, -b.l)});
 }
 
-// tables of every compiled (P, Q) as (hi, lo) pairs: slot as in c_tab32
-__constant__ float c_tabdf[TAB_SLOT * TAB_SLOTS * 2];
+// FP64 1D tables of every compiled (P, Q) as double-float values in the pair layout of the FP32
+// tables (tab32_offset, pa_tma_f32.cuh), each pair as a hi pair then a lo pair: rows
+// R[kp][a] = (T(2kp, a), T(2kp+1, a)) and columns C[k][ap] = (T(k, 2ap), T(k, 2ap+1)) for
+// T = B, G, so that the packed direct contractions take a table pair as one operand
+__constant__ float2 c_tabdf[2 * TAB32_PAIRS];
 
 // Even/odd form of the 1D contractions (q = p + 2).  The GLL nodes and the Gauss points are
 // symmetric about 1/2, so B(Q-1-q, n-1-a) = B(q, a) and G(Q-1-q, n-1-a) = -G(q, a).  For a
@@ -225,16 +228,60 @@ __device__ __forceinline__ void eo_apply2(const df2 (&xpm)[TE::HI], dfl xmid, df
   }
 }
 
+// v = D u at two quadrature points ka (.x) and kb (.y) of a stage-3 column, packed: D at dE as
+// (hi, lo) pairs, point stride PS, component stride DS; diffusion the symmetric 3 x 3 D of each
+// point times (u0, u1, u2), mass D u0 (per component the scalar steps of the single-point form)
+template <bool DIFF, int NC, int PS, int DS>
+__device__ __forceinline__ void df2_dpoint(const float2* __restrict__ dE, int ka, int kb, df2 u0, df2 u1, df2 u2,
+                                           df2& v0, df2& v1, df2& v2) {
+  float2 dh[NC], dl[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    const float2 da = __ldg(dE + ka * PS + m * DS), db = __ldg(dE + kb * PS + m * DS);
+    dh[m] = make_float2(da.x, db.x);
+    dl[m] = make_float2(da.y, db.y);
+  }
+  v0 = df2_zero();
+  if (DIFF) {
+    const int i1 = 1 % NC, i2 = 2 % NC, i3 = 3 % NC, i4 = 4 % NC, i5 = 5 % NC;
+    v1 = df2_zero();
+    v2 = df2_zero();
+    df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
+    df2_fma(v0, dh[i1], dl[i1], u1.h, u1.l);
+    df2_fma(v0, dh[i2], dl[i2], u2.h, u2.l);
+    df2_fma(v1, dh[i1], dl[i1], u0.h, u0.l);
+    df2_fma(v1, dh[i3], dl[i3], u1.h, u1.l);
+    df2_fma(v1, dh[i4], dl[i4], u2.h, u2.l);
+    df2_fma(v2, dh[i2], dl[i2], u0.h, u0.l);
+    df2_fma(v2, dh[i4], dl[i4], u1.h, u1.l);
+    df2_fma(v2, dh[i5], dl[i5], u2.h, u2.l);
+    v1 = df2_norm(v1);
+    v2 = df2_norm(v2);
+  } else {
+    df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
+  }
+  v0 = df2_norm(v0);
+}
+
 template <int P, int Q>
 struct TabDf {
-  static constexpr int OFF = ((P - 1) * 2 + (Q - P - 1)) * TAB_SLOT * 2;
+  static constexpr int N = P + 1, QH = (Q + 1) / 2, NH = (N + 1) / 2;
+  static constexpr int BR = 2 * tab32_offset(P, Q), GR = BR + 2 * QH * N, BC = GR + 2 * QH * N, GC = BC + 2 * Q * NH;
+  // packed: hi and lo pairs of rows (2kp, 2kp+1) at column a, of columns (2ap, 2ap+1) at row k
+  static __device__ __forceinline__ float2 Brh(int kp, int a) { return c_tabdf[BR + 2 * (kp * N + a)]; }
+  static __device__ __forceinline__ float2 Brl(int kp, int a) { return c_tabdf[BR + 2 * (kp * N + a) + 1]; }
+  static __device__ __forceinline__ float2 Grh(int kp, int a) { return c_tabdf[GR + 2 * (kp * N + a)]; }
+  static __device__ __forceinline__ float2 Grl(int kp, int a) { return c_tabdf[GR + 2 * (kp * N + a) + 1]; }
+  static __device__ __forceinline__ float2 Bch(int k, int ap) { return c_tabdf[BC + 2 * (k * NH + ap)]; }
+  static __device__ __forceinline__ float2 Bcl(int k, int ap) { return c_tabdf[BC + 2 * (k * NH + ap) + 1]; }
+  static __device__ __forceinline__ float2 Gch(int k, int ap) { return c_tabdf[GC + 2 * (k * NH + ap)]; }
+  static __device__ __forceinline__ float2 Gcl(int k, int ap) { return c_tabdf[GC + 2 * (k * NH + ap) + 1]; }
+  // scalar entries
   static __device__ __forceinline__ dfl B(int i, int a) {
-    const int k = OFF + 2 * (i * (P + 1) + a);
-    return {c_tabdf[k], c_tabdf[k + 1]};
+    return (i & 1) ? dfl{Brh(i >> 1, a).y, Brl(i >> 1, a).y} : dfl{Brh(i >> 1, a).x, Brl(i >> 1, a).x};
   }
   static __device__ __forceinline__ dfl G(int i, int a) {
-    const int k = OFF + 2 * (100 + i * (P + 1) + a);
-    return {c_tabdf[k], c_tabdf[k + 1]};
+    return (i & 1) ? dfl{Grh(i >> 1, a).y, Grl(i >> 1, a).y} : dfl{Grh(i >> 1, a).x, Grl(i >> 1, a).x};
   }
 };
 
@@ -267,6 +314,10 @@ struct DfTune {
   static constexpr int MINB = (DIFF && P >= 4) ? 2 : 0;
   static constexpr int KU = (DIFF && P >= 7) ? 1 : Q;
   static constexpr bool EO3 = DIFF ? (P >= 3) : (P >= 2);
+  // PK3: the direct stage 3 (where EO3 is not used) in packed pairs over point pairs.
+  // Measured: diffusion q = p + 2, p = 2 6 % and p = 1 1 % faster; mass p = 1 5 % and
+  // q = p + 1 3 % slower (more registers: 76-84 instead of 48-64), scalar there.
+  static constexpr bool PK3 = DIFF && Q == P + 2 && P <= 2;
 };
 
 // The block's work on one tile of ne <= NE consecutive elements starting at e0 (called once per
@@ -484,36 +535,6 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
         aeo0[c] = df2_zero();
         if (DIFF) aeo1[c] = aeo2[c] = df2_zero();
       }
-      // v = D u at points ka (.x) and kb (.y) (diffusion: symmetric 3 x 3; mass: scalar)
-      auto dpoint2 = [&](int ka, int kb, df2 u0, df2 u1, df2 u2, df2& v0, df2& v1, df2& v2) {
-        float2 dh[L::NC], dl[L::NC];
-#pragma unroll
-        for (int m = 0; m < L::NC; ++m) {
-          const float2 da = __ldg(dE + ka * Q * Q + m * L::Q3), db = __ldg(dE + kb * Q * Q + m * L::Q3);
-          dh[m] = make_float2(da.x, db.x);
-          dl[m] = make_float2(da.y, db.y);
-        }
-        if (DIFF) {
-          const int i1 = 1 % L::NC, i2 = 2 % L::NC, i3 = 3 % L::NC, i4 = 4 % L::NC, i5 = 5 % L::NC;
-          v0 = df2_zero(); v1 = df2_zero(); v2 = df2_zero();
-          df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
-          df2_fma(v0, dh[i1], dl[i1], u1.h, u1.l);
-          df2_fma(v0, dh[i2], dl[i2], u2.h, u2.l);
-          df2_fma(v1, dh[i1], dl[i1], u0.h, u0.l);
-          df2_fma(v1, dh[i3], dl[i3], u1.h, u1.l);
-          df2_fma(v1, dh[i4], dl[i4], u2.h, u2.l);
-          df2_fma(v2, dh[i2], dl[i2], u0.h, u0.l);
-          df2_fma(v2, dh[i4], dl[i4], u1.h, u1.l);
-          df2_fma(v2, dh[i5], dl[i5], u2.h, u2.l);
-          v0 = df2_norm(v0);
-          v1 = df2_norm(v1);
-          v2 = df2_norm(v2);
-        } else {
-          v0 = df2_zero();
-          df2_fma(v0, dh[0], dl[0], u0.h, u0.l);
-          v0 = df2_norm(v0);
-        }
-      };
       // v = D u at one point k (the middle point of an odd Q), scalar
       auto dpoint = [&](int k, dfl u0, dfl u1, dfl u2, dfl& v0, dfl& v1, dfl& v2) {
         float2 dc[L::NC];
@@ -572,7 +593,7 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
           u2.l.y = -u2.l.y;
         }
         df2 v0, v1, v2;
-        dpoint2(kk, k2, u0, u1, u2, v0, v1, v2);
+        df2_dpoint<DIFF, L::NC, Q * Q, L::Q3>(dE, kk, k2, u0, u1, u2, v0, v1, v2);
         // (p, q) = (v(kk) + v(k2), v(kk) - v(k2))
         const df2 pq0 = df2_sumdiff(df2_x(v0), df2_y(v0));
         df2 pq1 = pq0, pq2 = pq0;
@@ -654,7 +675,7 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
           a2[HN] = am2;
         }
       }
-    } else {
+    } else if constexpr (!DfTune<P, Q, DIFF>::PK3) {
 #pragma unroll KU
     for (int k = 0; k < Q; ++k) {
       float2 dc[L::NC];
@@ -705,6 +726,72 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
         for (int c = 0; c < n; ++c) df_fma(a0[c], T::B(k, c), v);
       }
     }
+    } else {
+      // direct form in packed pairs: the quadrature points (2kp, 2kp+1) of the forward
+      // contractions (row pairs of the tables, input broadcast), D at both points, and the
+      // transposed contraction over column pairs (c, c+1) (output broadcast); per output the
+      // scalar steps, in the same order
+      constexpr int QH = (Q + 1) / 2, NP = n / 2;
+      constexpr bool ODDN = (n % 2) != 0;
+      df2 A0[NP], A1[NP], A2[NP];
+      dfl z0 = df_zero(), z1 = df_zero(), z2 = df_zero();  // column n - 1 of an odd n
+#pragma unroll
+      for (int cp = 0; cp < NP; ++cp) {
+        A0[cp] = df2_zero();
+        if (DIFF) A1[cp] = A2[cp] = df2_zero();
+      }
+#pragma unroll KU
+      for (int kp = 0; kp < QH; ++kp) {
+        const int ka = 2 * kp, kb = (2 * kp + 1 < Q) ? 2 * kp + 1 : 2 * kp;  // (an odd Q's last pair repeats its point)
+        df2 U0 = df2_zero(), U1 = df2_zero(), U2 = df2_zero();
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          df2_fma(U0, T::Brh(kp, c), T::Brl(kp, c), bcast2(c0[c].h), bcast2(c0[c].l));
+          if (DIFF) {
+            df2_fma(U1, T::Brh(kp, c), T::Brl(kp, c), bcast2(c1[c].h), bcast2(c1[c].l));
+            df2_fma(U2, T::Grh(kp, c), T::Grl(kp, c), bcast2(c2[c].h), bcast2(c2[c].l));
+          }
+        }
+        U0 = df2_norm(U0);
+        if (DIFF) {
+          U1 = df2_norm(U1);
+          U2 = df2_norm(U2);
+        }
+        df2 V0, V1, V2;
+        df2_dpoint<DIFF, L::NC, Q * Q, L::Q3>(dE, ka, kb, U0, U1, U2, V0, V1, V2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 2 * kp + h;
+          if (k >= Q) break;
+          const dfl v0 = h ? df2_y(V0) : df2_x(V0);
+#pragma unroll
+          for (int cp = 0; cp < NP; ++cp) {
+            df2_fma(A0[cp], T::Bch(k, cp), T::Bcl(k, cp), bcast2(v0.h), bcast2(v0.l));
+            if (DIFF) {
+              const dfl v1 = h ? df2_y(V1) : df2_x(V1), v2 = h ? df2_y(V2) : df2_x(V2);
+              df2_fma(A1[cp], T::Bch(k, cp), T::Bcl(k, cp), bcast2(v1.h), bcast2(v1.l));
+              df2_fma(A2[cp], T::Gch(k, cp), T::Gcl(k, cp), bcast2(v2.h), bcast2(v2.l));
+            }
+          }
+          if (ODDN) {
+            df_fma(z0, dfl{T::Bch(k, NP).x, T::Bcl(k, NP).x}, v0);
+            if (DIFF) {
+              df_fma(z1, dfl{T::Bch(k, NP).x, T::Bcl(k, NP).x}, h ? df2_y(V1) : df2_x(V1));
+              df_fma(z2, dfl{T::Gch(k, NP).x, T::Gcl(k, NP).x}, h ? df2_y(V2) : df2_x(V2));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        const bool last = ODDN && c == n - 1;
+        const int cp = last ? 0 : c / 2;
+        a0[c] = last ? z0 : ((c & 1) ? df2_y(A0[cp]) : df2_x(A0[cp]));
+        if (DIFF) {
+          a1[c] = last ? z1 : ((c & 1) ? df2_y(A1[cp]) : df2_x(A1[cp]));
+          a2[c] = last ? z2 : ((c & 1) ? df2_y(A2[cp]) : df2_x(A2[cp]));
+        }
+      }
     }
 #pragma unroll
     for (int c = 0; c < n; ++c) {

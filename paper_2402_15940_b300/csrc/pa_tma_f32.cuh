@@ -30,10 +30,6 @@
 
 namespace fepa {
 
-// slot layout of the double-float tables (pa_df64.cuh): B then G, 100 entries each
-constexpr int TAB_SLOT = 200;
-constexpr int TAB_SLOTS = 16;
-
 // FP32 1D tables of every compiled (P, Q) as float2 pairs, for the packed FMA (__ffma2_rn:
 // two FMAs in one instruction, each component rounded as fmaf), with a table pair as one
 // constant-bank operand and the other operand a pair or a broadcast scalar:
