@@ -292,8 +292,10 @@ const char* fepa_f32_variant_name(int32_t variant);
  * float range less the low word's 24 bits, re-gathers x times an exact power of two and
  * scales the results back (a second pass over the block's x, rare).  This library's own
  * design for a GPU whose FP64 rate is a small fraction of its FP32 rate; the paper's
- * FP64 kernels have no counterpart.  By default (-1) the first FP64 use times both on
- * this op's mesh (three rounds, best round each) and keeps the faster; cached per device,
+ * FP64 kernels have no counterpart.  2 = the double-float kernel in blocks of half as many
+ * elements (the same arithmetic per element; only the order of the atomic additions of the
+ * scatter differs; more and smaller blocks, which can fill the GPU better on small meshes).  By default (-1) the first FP64 use times the three
+ * on this op's mesh (three rounds, best round each) and keeps the fastest; cached per device,
  * (p, q, form) and mesh size class.  The allocation-free solve never times: it uses the chosen or forced variant
  * (the double-float one only if its copy of D is current), else 0.
  */
@@ -471,8 +473,9 @@ int32_t fepa_batch_groups(const fepa_batch* batch);                  /* distinct
 int fepa_batch_set_stream(fepa_batch* batch, void* stream);
 
 /* FP64 action variant of every group (as fepa_op_set_f64_variant: 0 DFMA, 1 double-float,
- * -1 = the process-wide choice for the group's (p, q, form, size class) if one was
- * measured, else the faster of the two timed on the group at the next apply or solve). */
+ * 2 double-float in half-size tiles -- the elements per block of the group's persistent
+ * kernel; -1 = the process-wide choice for the group's (p, q, form, size class) if one was
+ * measured, else the fastest of the three timed on the group at the next apply or solve). */
 int fepa_batch_set_f64_variant(fepa_batch* batch, int32_t variant);
 
 /* y = A x for every problem at once (x, y: device, total DOFs). */

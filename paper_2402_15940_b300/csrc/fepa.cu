@@ -93,7 +93,9 @@ using Apply32Fn = void (*)(int, const int*, const float*, const float*, float*, 
                            int*, double*);
 
 constexpr int N32_VARIANTS = 4;  // (staged D, NE), (direct D, NE), (direct D, NE/2), persistent pipeline
-constexpr int N64_VARIANTS = 2;  // FP64 pipe (DFMA), double-float on the FP32 pipe
+// FP64 pipe (DFMA), double-float on the FP32 pipe, double-float in half-size blocks
+constexpr int N64_VARIANTS = 3;
+constexpr bool df_variant(int v) { return v == 1 || v == 2; }
 using ApplyDfFn = void (*)(int, const int*, const float2*, const double*, double*, const int*, const int*,
                           const int*, int);
 
@@ -105,8 +107,8 @@ struct Apply32Variant {
 
 struct KernelSet {
   ApplyFn<double> apply;
-  ApplyDfFn apply_df;
-  int df_smem, df_ne;
+  ApplyDfFn apply_df[2];  // double-float action, full- and half-size blocks (FP64 variants 1, 2)
+  int df_smem[2], df_ne[2];
   void (*diag_df)(int, const int*, const float2*, double*);
   int diag_df_smem, diag_df_ne;
   void (*rhs_df)(int64_t, int, int, const int*, const float2*, const int*, const double*, double, double, double*);
@@ -115,8 +117,8 @@ struct KernelSet {
   // persistent forms over a work list of element tiles (the batch's iteration loops)
   void (*apply_tiles)(const int2*, const int*, const int*, const int*, const double*, const double*, const double*,
                       const double*, double*, const int*);
-  void (*apply_df_tiles)(const int2*, const int*, const int*, const int*, const float2*, const double*, double*,
-                         const int*, int);
+  void (*apply_df_tiles[2])(const int2*, const int*, const int*, const int*, const float2*, const double*, double*,
+                            const int*, int);
   void (*apply32_tiles[2])(const int2*, const int*, const int*, const int*, const float*, const float*, float*,
                            const int*, int*);  // shapes of variants 1 and 2
   Apply32Fn v32dot[3] = {};  // variants 0-2 built to add (x, A x) into DOT_SLOTS doubles (p >= 3)
@@ -130,9 +132,12 @@ template <int P, int Q, bool DIFF>
 KernelSet make_set() {
   KernelSet k;
   k.apply = pa_apply<double, P, Q, DIFF>;
-  k.apply_df = pa_apply_df<P, Q, DIFF>;
-  k.df_smem = DfShape<P, Q, DIFF>::SMEM;
-  k.df_ne = DfShape<P, Q, DIFF>::NE;
+  k.apply_df[0] = pa_apply_df<P, Q, DIFF, 1>;
+  k.apply_df[1] = pa_apply_df<P, Q, DIFF, 2>;
+  k.df_smem[0] = DfShape<P, Q, DIFF, 1>::SMEM;
+  k.df_smem[1] = DfShape<P, Q, DIFF, 2>::SMEM;
+  k.df_ne[0] = DfShape<P, Q, DIFF, 1>::NE;
+  k.df_ne[1] = DfShape<P, Q, DIFF, 2>::NE;
   k.diag_df = pa_diag_df<P, Q, DIFF>;
   k.diag_df_smem = DiagDfShape<P, Q, DIFF>::SMEM;
   k.diag_df_ne = DiagDfShape<P, Q, DIFF>::NE;
@@ -148,7 +153,8 @@ KernelSet make_set() {
   k.v32[3] = {pa_apply_f32_pipe<P, Q, DIFF>, PipeShape<P, Q, DIFF>::SMEM, PipeShape<P, Q, DIFF>::NE,
               PipeShape<P, Q, DIFF>::NE, true};
   k.apply_tiles = pa_apply_tiles<double, P, Q, DIFF>;
-  k.apply_df_tiles = pa_apply_df_tiles<P, Q, DIFF>;
+  k.apply_df_tiles[0] = pa_apply_df_tiles<P, Q, DIFF, 1>;
+  k.apply_df_tiles[1] = pa_apply_df_tiles<P, Q, DIFF, 2>;
   k.apply32_tiles[0] = pa_apply_f32_tiles<P, Q, DIFF, 1>;
   k.apply32_tiles[1] = pa_apply_f32_tiles<P, Q, DIFF, 2>;
   if constexpr (P >= 3) {
@@ -399,10 +405,11 @@ int dalloc(T** p, size_t count) {
 // y += A x in FP64 with variant v (launch only; not counted)
 int launch_apply64_variant(fepa_op* op, int v, const double* x, double* y, const int* skip, cudaStream_t s) {
   const KernelSet& k = op->ks;
-  if (v == 1) {
-    const int grid = (int)((op->E + k.df_ne - 1) / k.df_ne);
-    k.apply_df<<<grid, dim3(k.apply_tpe, k.df_ne), k.df_smem, s>>>((int)op->E, op->gmap, op->qddf, x, y, skip,
-                                                                   nullptr, nullptr, op->dexp);
+  if (df_variant(v)) {
+    const int sh = v - 1;  // block shape: full or half
+    const int grid = (int)((op->E + k.df_ne[sh] - 1) / k.df_ne[sh]);
+    k.apply_df[sh]<<<grid, dim3(k.apply_tpe, k.df_ne[sh]), k.df_smem[sh], s>>>((int)op->E, op->gmap, op->qddf, x, y,
+                                                                               skip, nullptr, nullptr, op->dexp);
   } else {
     const int grid = (int)((op->E + k.apply_ne - 1) / k.apply_ne);
     k.apply<<<grid, dim3(k.apply_tpe, k.apply_ne), k.apply_smem, s>>>((int)op->E, op->gmap, op->qd, op->B, op->G, x,
@@ -418,7 +425,7 @@ int prepare_f64(fepa_op* op);
 // forced variant, else the DFMA kernel (counted)
 int launch_apply_untuned(fepa_op* op, const double* x, double* y, const int* skip, cudaStream_t s) {
   int v = op->v64 >= 0 ? op->v64 : (op->v64_forced >= 0 ? op->v64_forced : 0);
-  if (v == 1 && !op->qddf_valid) v = 0;  // its D copy would need an allocation
+  if (df_variant(v) && !op->qddf_valid) v = 0;  // its D copy would need an allocation
   TRY(launch_apply64_variant(op, v, x, y, skip, s));
   g_launches.fetch_add(1);
   return FEPA_OK;
@@ -516,7 +523,7 @@ int compute_diagonal(fepa_op* op, double* out, cudaStream_t s, bool prepare = tr
   if (prepare) TRY(prepare_f64(op));
   CUDA_TRY(cudaMemsetAsync(out, 0, op->N * sizeof(double), s));
   const KernelSet& k = op->ks;
-  if (op->v64 == 1 && op->qddf_valid) {
+  if (df_variant(op->v64) && op->qddf_valid) {
     const int grid = (int)((op->E + k.diag_df_ne - 1) / k.diag_df_ne);
     k.diag_df<<<grid, dim3(op->q * op->q, k.diag_df_ne), k.diag_df_smem, s>>>((int)op->E, op->gmap, op->qddf, out);
   } else {
@@ -708,7 +715,7 @@ int ensure_v64(fepa_op* op) {
     slot = best;
   }
   op->v64 = slot;
-  if (op->v64 != 1 && op->qddf) {  // the timing built a D copy the chosen kernel does not read
+  if (!df_variant(op->v64) && op->qddf) {  // the timing built a D copy the chosen kernel does not read
     cudaStreamSynchronize(op->stream);
     cudaFree(op->qddf);
     op->qddf = nullptr;
@@ -720,7 +727,7 @@ int ensure_v64(fepa_op* op) {
 // variant chosen and its data current (call outside graph capture, before launches)
 int prepare_f64(fepa_op* op) {
   TRY(ensure_v64(op));
-  if (op->v64 == 1) TRY(ensure_df(op));
+  if (df_variant(op->v64)) TRY(ensure_df(op));
   return FEPA_OK;
 }
 
@@ -1203,7 +1210,7 @@ int create_common(fepa_op* op, int32_t p, int32_t q1d, int32_t form, void* strea
   if (cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(FEPA_ERR_CUDA, "stream creation failed");
   TRY(allow_smem((const void*)op->ks.apply, op->ks.apply_smem));
-  TRY(allow_smem((const void*)op->ks.apply_df, op->ks.df_smem));
+  for (int sh = 0; sh < 2; ++sh) TRY(allow_smem((const void*)op->ks.apply_df[sh], op->ks.df_smem[sh]));
   TRY(allow_smem((const void*)op->ks.diag_df, op->ks.diag_df_smem));
   TRY(allow_smem((const void*)op->ks.diag, op->ks.diag_smem));
   TRY(allow_smem((const void*)op->ks.rhs_df, op->ks.rhs_df_smem));
@@ -1532,7 +1539,8 @@ int fepa_op_set_f64_variant(fepa_op* op, int32_t variant) {
 int32_t fepa_op_f64_variant(const fepa_op* op) { return op ? op->v64 : -1; }
 
 const char* fepa_f64_variant_name(int32_t variant) {
-  static const char* names[N64_VARIANTS] = {"FP64 pipe (DFMA)", "double-float on the FP32 pipe"};
+  static const char* names[N64_VARIANTS] = {"FP64 pipe (DFMA)", "double-float on the FP32 pipe",
+                                             "double-float on the FP32 pipe, half block"};
   return (variant >= 0 && variant < N64_VARIANTS) ? names[variant] : "unknown";
 }
 

@@ -286,11 +286,14 @@ struct TabDf {
 };
 
 // one element group per block (as many elements as fill ~256 threads), D read directly
-template <int P, int Q, bool DIFF>
+// Launch shape of the double-float action: NE_DIV 1 the block of the FP32 layout's NE0
+// elements, 2 half as many (FP64 variant 2: more, smaller blocks, for small meshes and the
+// batch's groups; chosen by timing per (p, q, form, size class) and per batch group)
+template <int P, int Q, bool DIFF, int NE_DIV = 1>
 struct DfShape {
   using L = F32Layout<P, Q, DIFF>;
   static constexpr int N = P + 1, TPE = Q * Q;
-  static constexpr int NE = L::NE0;
+  static constexpr int NE = (L::NE0 / NE_DIV) > 0 ? (L::NE0 / NE_DIV) : 1;
   static constexpr int SMEM = NE * (L::XSZ + L::WORK) * 8;
 };
 
@@ -322,12 +325,12 @@ struct DfTune {
 
 // The block's work on one tile of ne <= NE consecutive elements starting at e0 (called once per
 // block by pa_apply_df, or per tile of a work list by pa_apply_df_tiles)
-template <int P, int Q, bool DIFF, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
+template <int P, int Q, bool DIFF, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2, int NE_DIV = 1>
 __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restrict__ gmap,
                                         const float2* __restrict__ qd, const double* __restrict__ x,
                                         double* __restrict__ y, const int* __restrict__ elem_prob,
                                         const int* __restrict__ prob_done, int dexp) {
-  using S = DfShape<P, Q, DIFF>;
+  using S = DfShape<P, Q, DIFF, NE_DIV>;
   using L = typename S::L;
   using T = TabDf<P, Q>;
   constexpr int n = S::N, TPE = S::TPE, NE = S::NE;
@@ -904,20 +907,23 @@ __device__ __forceinline__ void df_tile(int64_t e0, int ne, const int* __restric
   }
 }
 
-template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB, int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
-__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
+// (MINB scales with NE_DIV: half-size blocks keep the register cap of the full-size ones)
+template <int P, int Q, bool DIFF, int NE_DIV = 1, int MINB = DfTune<P, Q, DIFF>::MINB * NE_DIV,
+          int KU = DfTune<P, Q, DIFF>::KU, int PF = 2>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF, NE_DIV>::TPE * DfShape<P, Q, DIFF, NE_DIV>::NE, MINB)
 pa_apply_df(int E, const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
             double* __restrict__ y, const int* __restrict__ skip, const int* __restrict__ elem_prob,
             const int* __restrict__ prob_done, int dexp) {
-  constexpr int NE = DfShape<P, Q, DIFF>::NE;
+  constexpr int NE = DfShape<P, Q, DIFF, NE_DIV>::NE;
   if (skip && *skip) return;
   const int64_t e0 = (int64_t)blockIdx.x * NE;
-  df_tile<P, Q, DIFF, KU, PF>(e0, (int)((E - e0) < NE ? (E - e0) : NE), gmap, qd, x, y, elem_prob, prob_done, dexp);
+  df_tile<P, Q, DIFF, KU, PF, NE_DIV>(e0, (int)((E - e0) < NE ? (E - e0) : NE), gmap, qd, x, y, elem_prob, prob_done,
+                                      dexp);
 }
 
 // Persistent form over a work list (the batch's iteration loop), as pa_apply_f32_tiles
-template <int P, int Q, bool DIFF, int MINB = DfTune<P, Q, DIFF>::MINB>
-__global__ void __launch_bounds__(DfShape<P, Q, DIFF>::TPE * DfShape<P, Q, DIFF>::NE, MINB)
+template <int P, int Q, bool DIFF, int NE_DIV = 1, int MINB = DfTune<P, Q, DIFF>::MINB * NE_DIV>
+__global__ void __launch_bounds__(DfShape<P, Q, DIFF, NE_DIV>::TPE * DfShape<P, Q, DIFF, NE_DIV>::NE, MINB)
 pa_apply_df_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, const int* __restrict__ nact,
                   const int* __restrict__ gmap, const float2* __restrict__ qd, const double* __restrict__ x,
                   double* __restrict__ y, const int* __restrict__ skip, int dexp) {
@@ -925,7 +931,7 @@ pa_apply_df_tiles(const int2* __restrict__ tiles, const int* __restrict__ act, c
   const int count = *nact;
   for (int i = blockIdx.x; i < count; i += gridDim.x) {
     const int2 tl = tiles[act[i]];
-    df_tile<P, Q, DIFF>(tl.x, tl.y, gmap, qd, x, y, nullptr, nullptr, dexp);
+    df_tile<P, Q, DIFF, DfTune<P, Q, DIFF>::KU, 2, NE_DIV>(tl.x, tl.y, gmap, qd, x, y, nullptr, nullptr, dexp);
     __syncthreads();  // (the next tile reuses the shared buffers)
   }
 }

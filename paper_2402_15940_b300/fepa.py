@@ -385,7 +385,8 @@ class Operator:
         return v, self._lib.fepa_f32_variant_name(v).decode()
 
     def set_f64_variant(self, variant):
-        """-1: autotune at next FP64 use; 0: FP64 pipe; 1: double-float on the FP32 pipe."""
+        """-1: autotune at next FP64 use; 0: FP64 pipe; 1: double-float on the FP32 pipe;
+        2: double-float in half-size blocks."""
         _check(self._lib.fepa_op_set_f64_variant(self._h, int(variant)))
 
     def f64_variant(self):
@@ -580,7 +581,8 @@ class Batch:
         _check(self._lib.fepa_batch_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
     def set_f64_variant(self, variant):
-        """-1: measured choice per group; 0: FP64 pipe; 1: double-float on the FP32 pipe."""
+        """-1: measured choice per group; 0: FP64 pipe; 1: double-float on the FP32 pipe;
+        2: double-float in half-size tiles."""
         _check(self._lib.fepa_batch_set_f64_variant(self._h, int(variant)))
 
     def apply(self, x, out=None):

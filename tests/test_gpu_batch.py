@@ -60,9 +60,10 @@ def test_batch_layout_and_groups():
     assert bt.groups == len({(pr["p"], pr["form"]) for pr in probs})
 
 
-@pytest.mark.parametrize("variant", [-1, 0, 1])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2])
 def test_batch_apply_matches_oracle(variant):
-    """Both FP64 action kernels (DFMA, double-float) and the measured choice."""
+    """The FP64 action kernels (DFMA, double-float in full- and half-size tiles) and the
+    measured choice."""
     probs = small_mix(seed=1)
     bt = F().Batch(probs)
     bt.set_f64_variant(variant)
@@ -74,7 +75,7 @@ def test_batch_apply_matches_oracle(variant):
         assert rel(y[sl], op.apply(x[sl], constrained=True)) <= 1e-12, i
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_batch_solve_matches_oracle_and_alone(variant):
     probs = small_mix(seed=2, count=12)
     bt = F().Batch(probs)

@@ -201,6 +201,33 @@ def test_apply_f32_dot_matches_oracle(form, p, shape, variant):
     assert abs(float(xax2.item()) - float(xax.item())) <= 1e-6 * abs(xd @ ya)
 
 
+@pytest.mark.parametrize("field", ["sine_solution", "interior_one"])
+def test_apply_f32_dot_on_smooth_low_energy_vectors(field):
+    """(x, A x) from the fused FP32 kernel at BP3 p = 4 on smooth, low-energy x, where the
+    diffusion form's terms cancel most: the discrete solution of the sine problem, and a field
+    that is 1 at every free DOF and 0 on the boundary (A_e x_e is rounding noise on every
+    interior element).  The fused FP32 sum is compared with the exact (x, A x) of the same
+    FP32 x, and with the product formed from the kernel's FP32 y in FP64 (what the separate
+    dot pass computes)."""
+    op, mesh = make((6, 5, 4), 4, "diffusion", seed=52)
+    prob = O.Problem(mesh, 4, None, "diffusion")
+    op.set_essential(prob.ess.astype(np.int32))
+    op.set_f32_variant(1)
+    if field == "sine_solution":
+        xd, _, _ = prob.solve(prob.sine_rhs(), rtol=1e-12)
+    else:
+        xd = np.ones(op.N)
+        xd[prob.ess] = 0.0
+    x32 = torch.from_numpy(xd.astype(np.float32)).cuda()
+    xr = x32.cpu().numpy().astype(np.float64)
+    exact = xr @ prob.apply(xr, constrained=True)
+    y, xax = op.apply_f32_dot(x32)
+    e_fused = abs(float(xax.item()) - exact) / abs(exact)
+    e_sep = abs(xr @ y.cpu().numpy().astype(np.float64) - exact) / abs(exact)
+    print(f"{field}: (x, A x) relative error fused {e_fused:.2e}, from FP32 y {e_sep:.2e}")
+    assert e_fused <= 1e-5 and e_sep <= 1e-5
+
+
 @pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("form,p,shape,variant", FIRST_STEP_CASES)
 def test_first_cg_step_matches_oracle(form, p, shape, variant, fused):
