@@ -519,7 +519,11 @@ def run_ours(args, rank, world, dist):
         # operators' variant choices are not the ones timed while the served stream kept the GPU busy
         extras["sweep"] = run_sweep(args, rank, world, dist, targets=(3e7,), quiet=True)
         extras["batch"] = run_batch(args, rank, world, dist, steps=min(args.steps, 2), warmup=1, quiet=True)
-        extras["serve"] = run_serve(args, rank, world, dist, rates=[float(args.serve_rate)], quiet=True)
+        extras["serve"] = run_serve(args, rank, world, dist, rates=[float(args.serve_rate)], quiet=True,
+                                    solver="jacobi")
+        # the same stream with the p-multigrid preconditioner for the large diffusion requests
+        extras["serve_pmg"] = run_serve(args, rank, world, dist, rates=[float(args.serve_rate)], quiet=True,
+                                        solver="auto")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -814,11 +818,15 @@ def run_sweep(args, rank, world, dist, targets=(1e5, 1e6, 3e7), quiet=False):
     return 0
 
 
-def run_serve(args, rank, world, dist, rates=None, quiet=False):
+def run_serve(args, rank, world, dist, rates=None, quiet=False, solver=None):
     """Served solve stream: for each arrival rate, `--requests` requests (mass or
     diffusion, p uniform in 1..8, DOFs log-uniform in 1e3..5e6, FP64 or mixed with
     refinement to 1e-10, seeded perturbed cubes, sine RHS) arrive as a Poisson process
-    and are served with continuous batching under an HBM budget."""
+    and are served with continuous batching under an HBM budget.  solver "jacobi": every
+    request by Jacobi-PCG (mixed: FP32 Jacobi-PCG in FP64 refinement); "auto": diffusion
+    requests of at least --pmg-min-dofs DOFs by CG with the p-multigrid V-cycle (FP64, or
+    FP32 for the mixed ones)."""
+    solver = args.serve_solver if solver is None else solver
     import torch
 
     from paper_2402_15940_b300 import launch_count
@@ -838,6 +846,7 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
             poisson_arrivals(reqs, rate=rate, seed=k)
             srv = Server(GpuExecutor(vf, priorities=args.serve_priorities, async_start=args.serve_async),
                          hbm_budget=args.hbm_budget, tick_iters=args.tick_iters, policy=args.serve_policy,
+                         solver=solver, pmg_min_dofs=args.pmg_min_dofs,
                          tick_seconds=args.tick_seconds if args.tick_seconds > 0 else None)
             srv.run(reqs)
             rep = srv.report()
@@ -852,6 +861,9 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False):
                 "config": {"workload": f"{args.requests} requests per rate, Poisson arrivals, mass|diffusion, "
                                        "p~U{1..8}, DOFs log-uniform 1e3..5e6, FP64 or mixed+refine (1/2 each) "
                                        "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
+                           "solver": ("Jacobi-PCG (mixed: FP32 Jacobi-PCG in FP64 refinement)" if solver == "jacobi"
+                                      else f"diffusion requests of >= {args.pmg_min_dofs} DOFs: FP64 CG with the "
+                                           "p-multigrid V-cycle (FP32 V-cycle for the mixed ones); others Jacobi-PCG"),
                            "tick_iters": args.tick_iters, "policy": args.serve_policy,
                            "stream_priorities": args.serve_priorities, "async_start": args.serve_async,
                            "tick_seconds": args.tick_seconds},
@@ -910,6 +922,10 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the short batch and serve runs of the default line")
     ap.add_argument("--serve-rate", type=float, default=1000.0, help="arrival rate of the default line's serve run")
+    ap.add_argument("--serve-solver", choices=["jacobi", "auto"], default="jacobi",
+                    help="--workload serve: Jacobi-PCG for every request, or p-multigrid CG for large diffusion ones")
+    ap.add_argument("--pmg-min-dofs", type=int, default=50000,
+                    help="smallest diffusion request solved with the p-multigrid preconditioner (--serve-solver auto)")
     ap.add_argument("--serve-policy", choices=["fifo", "sjf"], default="fifo",
                     help="admission order of waiting requests (arrival order, or least estimated work first)")
     ap.add_argument("--serve-sync-start", dest="serve_async", action="store_false",

@@ -576,6 +576,18 @@ int fepa_mg_vcycle(fepa_mg* mg, const double* b, double* x);
 /* CG on the fine op preconditioned by the V-cycle (flexible Polak-Ribiere beta, equal to
  * the standard one for an exact fixed preconditioner); blocks until done */
 int fepa_mg_solve(fepa_mg* mg, const double* b, double* x, double rtol, int32_t maxit, fepa_cg_stats* stats);
+/* The same solve in resumable form (Sec. 2.1's preconditioned CG, driven by a serving loop as
+ * fepa_solver_start/advance/poll drive the Jacobi forms): start enqueues r = b - A x and the
+ * stopping threshold on the fine op's stream; advance enqueues up to `iterations` iterations
+ * (V-cycle and CG steps; an iteration enqueued after the stopping test has fired changes
+ * nothing but runs its V-cycle on the hierarchy's own vectors); poll returns FEPA_BUSY while
+ * the last enqueued work runs (blocking = 0) or waits for it, then reads the state, and once
+ * done copies the solution into x (device, N doubles, which must stay valid until then).
+ * The iterates equal fepa_mg_solve's.  One solve at a time per hierarchy; state.iterations
+ * counts CG iterations, outer_iterations is 0. */
+int fepa_mg_solver_start(fepa_mg* mg, const double* b, double* x, double rtol, int32_t maxit);
+int fepa_mg_solver_advance(fepa_mg* mg, int32_t iterations);
+int fepa_mg_solver_poll(fepa_mg* mg, int32_t blocking, fepa_solver_state* state);
 
 /*
  * CG solve that allocates nothing.  The paper has no counterpart: this call exists

@@ -432,6 +432,9 @@ pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, doubl
   }
 }
 
+// The iteration kernels below (and cg_dot_dh) return at once when the state says done, so an
+// iteration enqueued after the stopping test (the resumable solve's last advance) changes nothing.
+
 // rho_new = (z, r) and beta in the flexible (Polak-Ribiere) form
 //   beta = (z_new, r_new - r_old) / rho_old = -alpha (z_new, h) / rho_old,  h = A d_old,
 // which equals rho_new / rho_old for a fixed symmetric preconditioner and stays robust
@@ -439,6 +442,7 @@ pcg_start(int64_t N, const double* __restrict__ b, double* __restrict__ r, doubl
 __global__ void __launch_bounds__(RED_THREADS)
 pcg_rho(int64_t N, const double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ h,
         CgState* st, double* partials) {
+  if (st->done) return;
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = z[i];
@@ -460,6 +464,7 @@ pcg_rho(int64_t N, const double* __restrict__ z, const double* __restrict__ r, c
 
 __global__ void pcg_direction(int64_t N, const double* __restrict__ z, double* __restrict__ d, double* __restrict__ h,
                               const CgState* st) {
+  if (st->done) return;
   const double beta = st->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     d[i] = beta == 0.0 ? z[i] : z[i] + beta * d[i];
@@ -471,6 +476,7 @@ __global__ void pcg_direction(int64_t N, const double* __restrict__ z, double* _
 __global__ void __launch_bounds__(RED_THREADS)
 pcg_update(int64_t N, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
            const double* __restrict__ h, CgState* st, double* partials) {
+  if (st->done) return;
   const double alpha = st->alpha;
   double v[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {

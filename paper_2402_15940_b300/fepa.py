@@ -143,6 +143,9 @@ SIGNATURES = [
     ("fepa_mg_smooth", ctypes.c_int, [_P, _I32, _P, _P]),
     ("fepa_mg_vcycle", ctypes.c_int, [_P, _P, _P]),
     ("fepa_mg_solve", ctypes.c_int, [_P, _P, _P, _D, _I32, ctypes.POINTER(CgStats)]),
+    ("fepa_mg_solver_start", ctypes.c_int, [_P, _P, _P, _D, _I32]),
+    ("fepa_mg_solver_advance", ctypes.c_int, [_P, _I32]),
+    ("fepa_mg_solver_poll", ctypes.c_int, [_P, _I32, ctypes.POINTER(SolverState)]),
     ("fepa_cg_solve_noalloc", ctypes.c_int, [_P, _P, _P, _D, _I32, _I32, ctypes.POINTER(CgStats)]),
     ("fepa_test_set_first_wait_limit", ctypes.c_int, [_I32]),
 ]
@@ -735,3 +738,24 @@ class Multigrid:
         _check(self._lib.fepa_mg_solve(self._h, _dev_ptr(b, torch.float64, n, "b"), _dev_ptr(x, torch.float64, n, "x"),
                                        float(rtol), int(maxit), ctypes.byref(st)))
         return x, st.as_dict()
+
+    # -- resumable solve (a serving loop's form of solve)
+    def solver_start(self, b, x, rtol=1e-10, maxit=1000):
+        torch = _torch()
+        n = self.levels[0]["ndofs"]
+        self._sv_keep = (b, x)   # the buffers must outlive the solve
+        self.op._sync_stream()
+        _check(self._lib.fepa_mg_solver_start(self._h, _dev_ptr(b, torch.float64, n, "b"),
+                                              _dev_ptr(x, torch.float64, n, "x"), float(rtol), int(maxit)))
+
+    def solver_advance(self, iterations):
+        _check(self._lib.fepa_mg_solver_advance(self._h, int(iterations)))
+
+    def solver_poll(self, blocking=False):
+        """None while work is in flight (non-blocking), else the state dict."""
+        st = SolverState()
+        rc = self._lib.fepa_mg_solver_poll(self._h, 1 if blocking else 0, ctypes.byref(st))
+        if rc == BUSY:
+            return None
+        _check(rc)
+        return st.as_dict()

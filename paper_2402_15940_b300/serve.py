@@ -6,7 +6,12 @@ library op on a stream of its own), admits waiting requests in arrival order whe
 the HBM budget allows, and on every tick advances each active request by a bounded
 number of CG iterations (fepa_solver_advance), so requests that arrive while others
 are running join at the next tick and their work overlaps on the device.  Finished
-requests leave at tick boundaries and release their memory.
+requests leave at tick boundaries and release their memory.  With solver="auto",
+diffusion requests of at least pmg_min_dofs DOFs are solved by CG preconditioned with
+the p-multigrid V-cycle (Sec. 2.1; FP64 V-cycle for FP64 requests, FP32 V-cycle inside
+the FP64 CG for mixed ones) instead of Jacobi-PCG, advanced by the resumable
+fepa_mg_solver_* calls; the others keep Jacobi (mass matrices are well conditioned, and
+below the threshold the V-cycle's set-up and launches cost more than they save).
 
 The scheduler is plain host logic; all device work goes through the C ABI of
 libfepa.so (GpuExecutor).  A FakeExecutor with the same interface drives the host
@@ -33,6 +38,7 @@ class Request:
     precision: str = "fp64"   # "fp64" | "mixed"
     arrival: float = 0.0      # seconds after the start of the run
     rtol: float = 1e-10
+    solver: str = "jacobi"    # "jacobi" | "pmg" (set by the server's solver policy)
 
     @property
     def ndofs(self) -> int:
@@ -70,7 +76,18 @@ def device_bytes(req: Request) -> int:
     if req.precision == "mixed":
         by += 4 * ncomp * (((q ** 3) + 3) & ~3) * E   # padded FP32 D
         by += 4 * N * 6 + 8 * N                       # FP32 loop vectors, FP64 residual
-    return int(by * 1.1) + 2 * _torch_block(8 * N) + (16 << 20)
+    levels = 0
+    if req.solver == "pmg":
+        # coarser levels (orders p/2, p/4, ..., 1): each at most the fine level's D (FP64, its
+        # (hi, lo) and FP32 copies) and map scaled by its point and node counts, plus the V-cycle
+        # and outer PCG vectors of every level and a fixed 16 MB per level op
+        pc, frac = req.p, 0.0
+        while pc > 1:
+            pc = max(1, pc // 2)
+            frac += ((pc + 2) / q) ** 3 + ((pc + 1) / n) ** 3
+            levels += 1
+        by += int(frac * (20 * ncomp * q ** 3 * E + 4 * n ** 3 * E)) + 8 * N * 20
+    return int(by * 1.1) + 2 * _torch_block(8 * N) + (16 << 20) * (1 + levels)
 
 
 def estimated_work(req: Request) -> float:
@@ -78,6 +95,8 @@ def estimated_work(req: Request) -> float:
     iteration count, which grows like p times the elements per side, with an FP32 iteration of
     the mixed solve counted at a quarter of an FP64 one (the FP32 action moves half the bytes and
     avoids the FP64-accurate arithmetic)."""
+    if req.solver == "pmg":
+        return req.ndofs * 120.0   # ~15 iterations of a V-cycle costing ~8 operator actions
     its = 4.4 * req.p * max(req.n)
     return req.ndofs * its * (0.25 if req.precision == "mixed" else 1.0)
 
@@ -105,12 +124,18 @@ class Server:
 
     def __init__(self, executor, hbm_budget: float = 150e9, tick_iters: int = 32, max_active: int = 256,
                  keep_results: bool = False, clock: Callable[[], float] = time.perf_counter, policy: str = "fifo",
-                 tick_seconds: Optional[float] = None):
+                 tick_seconds: Optional[float] = None, solver: str = "jacobi", pmg_min_dofs: int = 50000):
         """policy: "fifo" admits waiting requests in arrival order; "sjf" admits the waiting request
         with the least estimated work first (shorter waits for short requests when slots or memory
         are scarce; a request that can never fit is rejected either way).  tick_seconds: if set, a
         request advances by enough iterations per tick for about this much estimated GPU time (at
-        least tick_iters, at most 4096); else by tick_iters."""
+        least tick_iters, at most 4096); else by tick_iters.  solver: "jacobi" solves every request
+        by Jacobi-PCG (or its refined mixed form); "auto" gives diffusion requests of at least
+        pmg_min_dofs DOFs the p-multigrid preconditioner."""
+        if solver not in ("jacobi", "auto"):
+            raise ValueError("solver must be 'jacobi' or 'auto'")
+        self.solver = solver
+        self.pmg_min_dofs = int(pmg_min_dofs)
         self.tick_seconds = tick_seconds
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
@@ -130,6 +155,7 @@ class Server:
         self.ticks = 0
         self.max_concurrent = 0
         self.inflight: dict = {}     # rid -> an advance of the request may still be running
+        self.pmg_count = 0
 
     def _admit(self, now: float):
         if self.policy == "sjf" and len(self.pending) > 1:
@@ -145,14 +171,25 @@ class Server:
                 break                          # wait for memory to free up (queue order kept)
             self.pending.popleft()
             handle = self.ex.start(req)
+            self.pmg_count += req.solver == "pmg"
             self.in_use += need
             self.peak_in_use = max(self.peak_in_use, self.in_use)
             self.active[req.rid] = (req, handle, need, now)
         self.max_concurrent = max(self.max_concurrent, len(self.active))
 
+    def choose_solver(self, req: Request):
+        """The solver policy, applied when a request arrives."""
+        if self.solver == "auto" and req.form == "diffusion" and req.ndofs >= self.pmg_min_dofs:
+            req.solver = "pmg"
+
     def tick_size(self, req: Request) -> int:
         """Iterations per advance: tick_iters, or with tick_seconds enough for about that much GPU
-        time (estimated from the DOFs), so the host's per-tick round trip stays small next to it."""
+        time (estimated from the DOFs), so the host's per-tick round trip stays small next to it.
+        A multigrid-preconditioned request advances by 1 to 4 of its (much costlier) iterations."""
+        if req.solver == "pmg":
+            if self.tick_seconds is None:
+                return 1
+            return int(min(4, max(1, self.tick_seconds / max(req.ndofs / 1.2e8, 1e-12))))
         if self.tick_seconds is None:
             return self.tick_iters
         per_it = req.ndofs / (25e9 if req.precision == "mixed" else 6e9)
@@ -192,7 +229,9 @@ class Server:
         while arrivals or self.pending or self.active:
             now = self.clock() - self.t0
             while arrivals and arrivals[0].arrival <= now:
-                self.pending.append(arrivals.popleft())
+                req = arrivals.popleft()
+                self.choose_solver(req)
+                self.pending.append(req)
             self._admit(now)
             if self.active:
                 self._tick()
@@ -208,7 +247,7 @@ class Server:
         work = sum(o.ndofs * o.iterations for o in self.done)
         mem = getattr(self.ex, "measured", [])
         return {"completed": len(self.done), "rejected": len(self.rejected), "makespan_s": self.makespan,
-                "policy": self.policy,
+                "policy": self.policy, "solver": self.solver, "pmg_requests": self.pmg_count,
                 "device_bytes_check": {"requests": len(mem),
                                        "max_measured_over_estimate": max((m / e for m, e in mem), default=None)},
                 "solves_per_s": len(self.done) / self.makespan if self.makespan > 0 else 0.0,
@@ -270,7 +309,7 @@ class GpuExecutor:
         return True
 
     def _create(self, req: Request):
-        from .fepa import Operator
+        from .fepa import Multigrid, Operator
         torch = self.torch
         if self.pool is not None:
             torch.cuda.set_device(self.device)   # (the current device is per thread)
@@ -285,23 +324,29 @@ class GpuExecutor:
             else:
                 b = op.rhs_sine(1.0)
             x = torch.zeros(op.N, dtype=torch.float64, device="cuda")
-            op.solver_start(b, x, kind="refined" if req.precision == "mixed" else "cg", rtol=req.rtol,
-                            inner_rtol=self.inner_rtol)
+            mg = None
+            if req.solver == "pmg":
+                mg = Multigrid(op, smooth_degree=2, coarse_degree=24,
+                               precision="fp32" if req.precision == "mixed" else "fp64")
+                mg.solver_start(b, x, rtol=req.rtol)
+            else:
+                op.solver_start(b, x, kind="refined" if req.precision == "mixed" else "cg", rtol=req.rtol,
+                                inner_rtol=self.inner_rtol)
         if self.pool is None:   # (other threads' allocations would blur the difference)
             self.measured.append((max(0, free0 - torch.cuda.mem_get_info()[0]), device_bytes(req)))
-        return {"op": op, "stream": stream, "b": b, "x": x}
+        return {"op": op, "mg": mg, "stream": stream, "b": b, "x": x}
 
     def advance(self, h, iters: int):
         if not self._ready(h):
             return
         with self.torch.cuda.stream(h["stream"]):
-            h["op"].solver_advance(iters)
+            (h["mg"] or h["op"]).solver_advance(iters)
 
     def poll(self, h):
         if not self._ready(h):
             return None
         with self.torch.cuda.stream(h["stream"]):
-            return h["op"].solver_poll(blocking=False)
+            return (h["mg"] or h["op"]).solver_poll(blocking=False)
 
     def result(self, h):
         with self.torch.cuda.stream(h["stream"]):
@@ -311,6 +356,8 @@ class GpuExecutor:
         if "future" in h:
             h.update(h.pop("future").result())
         h["stream"].synchronize()
+        if h["mg"] is not None:
+            h["mg"].close()
         h["op"].close()
         h.clear()
 

@@ -109,3 +109,70 @@ def test_server_results_same_alone_and_in_the_mix(async_start):
     chk = rep["device_bytes_check"]
     if not async_start:
         assert chk["requests"] == len(reqs) and chk["max_measured_over_estimate"] <= 1.0, chk
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("step", [1, 3, 40])
+def test_resumable_multigrid_solve_equals_one_shot(precision, step):
+    """fepa_mg_solver_start/advance/poll reach fepa_mg_solve's iterate: the same iteration count
+    and solution, also when an advance enqueues iterations past the stopping test (step 40)."""
+    op, b = make((4, 4, 3), 4, "diffusion", seed=7)
+    mg = F().Multigrid(op, smooth_degree=2, coarse_degree=24, precision=precision)
+    x1, s1 = mg.solve(b, rtol=1e-10)
+    x2 = torch.zeros_like(b)
+    mg.solver_start(b, x2, rtol=1e-10)
+    st = None
+    for _ in range(1000):
+        mg.solver_advance(step)
+        st = mg.solver_poll(blocking=True)
+        if st["done"]:
+            break
+    assert st["done"] and st["status"] == 0 and st["rel_residual"] <= 1e-10
+    assert abs(st["iterations"] - s1["iterations"]) <= (0 if precision == "fp64" else 1)
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
+    # a second solve on the same hierarchy starts from the caller's x again
+    x3 = torch.zeros_like(b)
+    mg.solver_start(b, x3, rtol=1e-10)
+    while not mg.solver_poll(blocking=True)["done"]:
+        mg.solver_advance(2)
+    assert rel(x3.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
+    mg.close()
+
+
+def test_server_with_multigrid_policy_same_alone_and_in_the_mix():
+    """solver="auto": the diffusion requests above the threshold run multigrid-preconditioned CG
+    (FP64 or FP32 V-cycle) beside Jacobi requests; each result equals the same solve run alone
+    and the oracle's, and the admission estimate bounds each request's device memory."""
+    from paper_2402_15940_b300.serve import GpuExecutor, Request, Server, poisson_arrivals
+    specs = [("diffusion", 4, (4, 4, 3), "fp64"), ("mass", 3, (3, 3, 3), "mixed"), ("diffusion", 2, (6, 6, 5), "mixed"),
+             ("diffusion", 1, (3, 3, 3), "fp64"), ("diffusion", 6, (2, 2, 3), "fp64"), ("diffusion", 3, (5, 4, 4), "mixed")]
+    reqs = [Request(rid=i, form=f, p=p, n=n, mesh_seed=70 + i, precision=pr) for i, (f, p, n, pr) in enumerate(specs)]
+    poisson_arrivals(reqs, rate=500.0, seed=2)
+    vf = lambda n, seed: FI.perturbed_cube_vertices(*n, seed=seed)  # noqa: E731
+    make((2, 2, 2), 1, "mass", 0)   # the library's one-time set-up happens before the memory checks
+    srv = Server(GpuExecutor(vf), hbm_budget=4e9, tick_iters=4, keep_results=True, solver="auto", pmg_min_dofs=1000)
+    out = srv.run(reqs)
+    assert len(out) == len(reqs) and all(o.status == 0 for o in out)
+    assert [r.solver for r in reqs] == ["pmg", "jacobi", "pmg", "jacobi", "pmg", "pmg"]
+    for o, r in zip(out, reqs):
+        op, b = make(r.n, r.p, r.form, r.mesh_seed)
+        if r.solver == "pmg":
+            mg = F().Multigrid(op, smooth_degree=2, coarse_degree=24,
+                               precision="fp32" if r.precision == "mixed" else "fp64")
+            xa, sa = mg.solve(b, rtol=1e-10)
+            assert abs(sa["iterations"] - o.iterations) <= 1
+            mg.close()
+        elif r.precision == "fp64":
+            xa, sa = op.solve(b, rtol=1e-10)
+            assert abs(sa["iterations"] - o.iterations) <= 1
+        else:
+            xa, sa = op.solve_refined(b, rtol=1e-10)
+        assert rel(o.result, xa.cpu().numpy()) <= 1e-9, r
+        mesh = O.HexGridMesh(*r.n, FI.perturbed_cube_vertices(*r.n, seed=r.mesh_seed))
+        prob = O.Problem(mesh, r.p, None, r.form, assemble=r.p <= 5)
+        xo, _, _ = prob.solve(prob.sine_rhs(), rtol=1e-13)
+        assert rel(o.result, xo) <= 1e-8
+    rep = srv.report()
+    assert rep["pmg_requests"] == 4
+    chk = rep["device_bytes_check"]
+    assert chk["requests"] == len(reqs) and chk["max_measured_over_estimate"] <= 1.0, chk

@@ -148,3 +148,29 @@ def test_tick_size_scales_with_the_request():
     big = Request(1, "diffusion", 4, (48, 48, 48), 0)
     assert srv.tick_size(small) == 4096 and 16 <= srv.tick_size(big) < 4096
     assert Server(FakeExecutor(lambda r: 1), tick_iters=16).tick_size(big) == 16
+
+
+def test_solver_policy_gives_large_diffusion_requests_multigrid():
+    """solver="auto": diffusion requests of at least pmg_min_dofs DOFs get the p-multigrid
+    preconditioner, smaller ones and mass requests keep Jacobi; the estimates follow the choice
+    (more device memory for the levels, less estimated work) and pmg requests advance by 1 to 4
+    of their iterations per tick."""
+    from paper_2402_15940_b300.serve import estimated_work
+    rs = reqs([("diffusion", 4, 12, 0.0), ("diffusion", 2, 3, 0.0), ("mass", 4, 12, 0.0), ("diffusion", 6, 8, 1.0)])
+    srv = Server(FakeExecutor(lambda r: 30), hbm_budget=1e12, tick_iters=8, clock=FakeClock(), solver="auto",
+                 pmg_min_dofs=20000, tick_seconds=2e-3)
+    out = srv.run(rs)
+    assert len(out) == 4
+    assert [r.solver for r in rs] == ["pmg", "jacobi", "jacobi", "pmg"]
+    assert srv.report()["pmg_requests"] == 2 and srv.report()["solver"] == "auto"
+    assert all(1 <= srv.tick_size(r) <= 4 for r in rs if r.solver == "pmg")
+    j = Request(9, "diffusion", 4, (12, 12, 12), 0)
+    m = Request(9, "diffusion", 4, (12, 12, 12), 0, solver="pmg")
+    assert device_bytes(m) > device_bytes(j)
+    assert estimated_work(m) < estimated_work(j)
+    # with the Jacobi policy nothing changes
+    rs2 = reqs([("diffusion", 4, 12, 0.0)])
+    Server(FakeExecutor(lambda r: 30), hbm_budget=1e12, clock=FakeClock()).run(rs2)
+    assert rs2[0].solver == "jacobi"
+    with pytest.raises(ValueError):
+        Server(FakeExecutor(lambda r: 1), solver="amg")
