@@ -844,7 +844,8 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False, solver=None):
             reqs = [Request(rid=i, form=s["form"], p=s["p"], n=s["n"], mesh_seed=s["mesh_seed"],
                             precision=s["precision"]) for i, s in enumerate(spec)]
             poisson_arrivals(reqs, rate=rate, seed=k)
-            srv = Server(GpuExecutor(vf, priorities=args.serve_priorities, async_start=args.serve_async),
+            srv = Server(GpuExecutor(vf, priorities=args.serve_priorities, async_start=args.serve_async,
+                                     workers=args.serve_workers),
                          hbm_budget=args.hbm_budget, tick_iters=args.tick_iters, policy=args.serve_policy,
                          solver=solver, pmg_min_dofs=args.pmg_min_dofs,
                          tick_seconds=args.tick_seconds if args.tick_seconds > 0 else None)
@@ -866,6 +867,7 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False, solver=None):
                                            "p-multigrid V-cycle (FP32 V-cycle for the mixed ones); others Jacobi-PCG"),
                            "tick_iters": args.tick_iters, "policy": args.serve_policy,
                            "stream_priorities": args.serve_priorities, "async_start": args.serve_async,
+                           "creation_workers": args.serve_workers,
                            "tick_seconds": args.tick_seconds},
                 "per_rate": per_rate, "gpu_launches": launch_count() - l0, "clocks": clk.summary()}
         if quiet:
@@ -928,6 +930,8 @@ def main():
                     help="smallest diffusion request solved with the p-multigrid preconditioner (--serve-solver auto)")
     ap.add_argument("--serve-policy", choices=["fifo", "sjf"], default="fifo",
                     help="admission order of waiting requests (arrival order, or least estimated work first)")
+    ap.add_argument("--serve-workers", type=int, default=2,
+                    help="host threads that build the requests' ops (with asynchronous start)")
     ap.add_argument("--serve-sync-start", dest="serve_async", action="store_false",
                     help="build each request's op on the scheduler thread (default: on a worker thread)")
     ap.add_argument("--no-serve-priorities", dest="serve_priorities", action="store_false",
