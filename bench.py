@@ -728,7 +728,11 @@ def run_batch(args, rank, world, dist, steps=None, warmup=None, quiet=False):
                 "solves_per_s": args.batch_count * world * steps / t,
                 "max_iterations_per_step": maxits, "setup_s": setup_s,
                 "gpu_launches": launches64, "clocks": clk.summary(), "mixed_refined": refined,
-                "mixed_reliable": reliable}
+                "mixed_reliable": reliable,
+                # the autotuner's picks per (p, form) group: FP64 action (0 DFMA, 1 double-float,
+                # 2 double-float in half-size tiles) and the FP32 tile's elements per block
+                "autotune_picks": [{**g, "f64_kernel": F.load_library().fepa_f64_variant_name(g["f64_variant"]).decode()}
+                                   for g in bt.group_info()]}
         if quiet:
             return line
         print(json.dumps(line), flush=True)

@@ -470,6 +470,12 @@ void fepa_batch_destroy(fepa_batch* batch);
 int64_t fepa_batch_ndofs(const fepa_batch* batch);                   /* total DOFs */
 int fepa_batch_offsets(const fepa_batch* batch, int64_t* offsets);   /* host, count + 1 entries */
 int32_t fepa_batch_groups(const fepa_batch* batch);                  /* distinct (p, form) */
+/* The autotuner's picks for group `group` (0 .. groups-1; groups in order of first appearance
+ * of their (p, form)): order, form, elements, FP64 action variant (as fepa_batch_set_f64_variant;
+ * -1 until the first FP64 apply or solve chose it) and the FP32 tile's elements per block (0 until
+ * the first refined or reliable solve chose it).  Outputs may be null. */
+int fepa_batch_group_info(const fepa_batch* batch, int32_t group, int32_t* order, int32_t* form, int64_t* elements,
+                          int32_t* f64_variant, int32_t* f32_elems_per_block);
 int fepa_batch_set_stream(fepa_batch* batch, void* stream);
 
 /* FP64 action variant of every group (as fepa_op_set_f64_variant: 0 DFMA, 1 double-float,

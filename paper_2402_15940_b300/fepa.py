@@ -124,6 +124,7 @@ SIGNATURES = [
     ("fepa_batch_ndofs", _I64, [_P]),
     ("fepa_batch_offsets", ctypes.c_int, [_P, _P]),
     ("fepa_batch_groups", _I32, [_P]),
+    ("fepa_batch_group_info", ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     ("fepa_batch_set_stream", ctypes.c_int, [_P, _P]),
     ("fepa_batch_set_f64_variant", ctypes.c_int, [_P, _I32]),
     ("fepa_batch_apply", ctypes.c_int, [_P, _P, _P]),
@@ -567,6 +568,19 @@ class Batch:
         _check(lib.fepa_batch_offsets(h, off.ctypes.data_as(ctypes.c_void_p)))
         self.offsets = off
         self.groups = int(lib.fepa_batch_groups(h))
+
+    def group_info(self):
+        """Per group: order, form, elements and the autotuner's picks (FP64 variant, FP32 tile
+        elements per block; -1 / 0 until chosen)."""
+        out = []
+        for g in range(self.groups):
+            o, f, v64, ne32 = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+            e = ctypes.c_int64()
+            _check(self._lib.fepa_batch_group_info(self._h, g, ctypes.byref(o), ctypes.byref(f), ctypes.byref(e),
+                                                   ctypes.byref(v64), ctypes.byref(ne32)))
+            out.append({"p": o.value, "form": "diffusion" if f.value == DIFFUSION else "mass", "elements": e.value,
+                        "f64_variant": v64.value, "f32_elements_per_block": ne32.value})
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -308,3 +308,23 @@ def test_batch_reliable_512_problem_mix_sampled():
     for i in rng.choice(512, 6, replace=False):
         sl = slice(bt.offsets[i], bt.offsets[i + 1])
         assert rel(x[sl], x64[sl]) <= 1e-8, i
+
+
+def test_batch_records_the_autotuners_picks_per_group():
+    """After an FP64 solve every group has an FP64 variant picked (0-2), after a refined solve an
+    FP32 tile shape (variant 1 or 2's elements per block); the groups list every (p, form) once."""
+    probs = small_mix(seed=5, count=10)
+    bt = F().Batch(probs)
+    info = bt.group_info()
+    assert len(info) == bt.groups == len({(pr["p"], pr["form"]) for pr in probs})
+    assert {(g["p"], g["form"]) for g in info} == {(pr["p"], pr["form"]) for pr in probs}
+    assert all(g["f64_variant"] == -1 and g["f32_elements_per_block"] == 0 for g in info)
+    b = rhs_for(probs, bt.offsets)
+    bt.solve(torch.from_numpy(b).cuda(), rtol=1e-10)
+    bt.solve_refined(torch.from_numpy(b).cuda(), rtol=1e-10)
+    for g, e in zip(bt.group_info(), info):
+        assert g["elements"] == e["elements"] > 0
+        assert g["f64_variant"] in (0, 1, 2)
+        q = g["p"] + 2
+        ne0 = max(1, 256 // (q * q))
+        assert g["f32_elements_per_block"] in (ne0, max(1, ne0 // 2)), g
