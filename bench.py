@@ -838,7 +838,12 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False, solver=None):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    vf = lambda n, seed: FI.perturbed_cube_vertices(*n, seed=seed)  # noqa: E731
+    # the requests' meshes are their own input data: generated before the timed region (as the
+    # batch's are), so the served time covers building the ops from them, not drawing them
+    spec0 = FI.serve_requests(args.requests, seed=100 * rank)
+    meshes = {(tuple(s["n"]), s["mesh_seed"]): FI.perturbed_cube_vertices(*s["n"], seed=s["mesh_seed"])
+              for s in spec0}
+    vf = lambda n, seed: meshes[(tuple(n), seed)]  # noqa: E731
     rates = [float(r) for r in args.rates.split(",")] if rates is None else rates
     per_rate = []
     l0 = launch_count()
@@ -865,7 +870,8 @@ def run_serve(args, rank, world, dist, rates=None, quiet=False, solver=None):
                 "data": "synthetic",
                 "config": {"workload": f"{args.requests} requests per rate, Poisson arrivals, mass|diffusion, "
                                        "p~U{1..8}, DOFs log-uniform 1e3..5e6, FP64 or mixed+refine (1/2 each) "
-                                       "to 1e-10, continuous batching", "hbm_budget_bytes": args.hbm_budget,
+                                       "to 1e-10, continuous batching; meshes generated before the timed region",
+                           "hbm_budget_bytes": args.hbm_budget,
                            "solver": ("Jacobi-PCG (mixed: FP32 Jacobi-PCG in FP64 refinement)" if solver == "jacobi"
                                       else f"diffusion requests of >= {args.pmg_min_dofs} DOFs: FP64 CG with the "
                                            "p-multigrid V-cycle (FP32 V-cycle for the mixed ones); others Jacobi-PCG"),
