@@ -405,7 +405,7 @@ def bp3_case(args, p, n, rank, world, dist, steps, forms, with_e2e, with_rooflin
             fl = flops_per_elem(p + 1, q, "diffusion") * E
             ach = fl / t_apply / 1e9
             v64, vname = op.f64_variant()
-            if v64 == 1:
+            if v64 in (1, 2):   # double-float (full- or half-size blocks)
                 traffic = args.traffic_fp64
                 if traffic is None and (p, n) == (4, 64):
                     traffic = NCU_TRAFFIC_P4_N64["df"]
@@ -428,7 +428,7 @@ def bp3_case(args, p, n, rank, world, dist, steps, forms, with_e2e, with_rooflin
             r["dfma_kernel"] = {"kernel": f"pa_apply<double,{p},{q},diffusion>", "apply_ms": 1e3 * t_dfma,
                                 "achieved": fl / t_dfma / 1e9, "unit": "GFLOP/s",
                                 "frac_of_fp64_pipe": fl / t_dfma / 1e9 / FP64_PEAK_GFLOPS}
-            r["arithmetic"] = ("FP64-accurate double-float on the FP32 pipe (autotuned)" if v64 == 1 else
+            r["arithmetic"] = ("FP64-accurate double-float on the FP32 pipe (autotuned)" if v64 in (1, 2) else
                                "native binary64 (DFMA, autotuned)")
         else:
             by = bytes_per_elem(p + 1, q, "diffusion", p, n, word=4) * E
@@ -782,7 +782,7 @@ def run_sweep(args, rank, world, dist, targets=(1e5, 1e6, 3e7), quiet=False):
                 fl = flops_per_elem(p + 1, q, form) * E
                 by64 = bytes_per_elem(p + 1, q, form, p, n, word=8) * E
                 by32 = bytes_per_elem(p + 1, q, form, p, n, word=4) * E
-                alu_peak = DF_PEAK_GFLOPS if v64 == 1 else FP64_PEAK_GFLOPS
+                alu_peak = DF_PEAK_GFLOPS if v64 in (1, 2) else FP64_PEAK_GFLOPS
                 # roofline of the FP64-accurate action: the slower of its ALU ceiling and HBM
                 roof64 = min(alu_peak * 1e9 / (fl / E), hbm_peak * 1e9 / (by64 / E)) * N / E
                 if form == "diffusion":
