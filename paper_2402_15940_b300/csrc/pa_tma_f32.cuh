@@ -186,8 +186,18 @@ constexpr SmemPick smem_pick(int P, int Q, bool DIFF) {
          : (P == 4 && Q == 5 && !DIFF) ? SmemPick{5, 0, 7, 37, 0, 37, 0}
          : (P == 4 && Q == 6 && DIFF) ? SmemPick{5, 0, 7, 38, 2, 38, 4}
          : (P == 4 && Q == 6 && !DIFF) ? SmemPick{5, 0, 9, 45, 0, 38, 0}
-         // p >= 5: the plain odd strides (the search's picks measured no faster there,
-         // p = 8 diffusion 2-4 % slower)
+         // p = 6, 8 and mass p = 7 (q = p + 2): S1 strides from a search over the two S1 access
+         // patterns alone (stage 1's lines (b, c) and stage 2's lines (i, c), one element): with the
+         // plain strides stage 2's reads and 2^T's writes took up to 3.7x the wavefronts of a
+         // conflict-free access (ncu at p = 8: 32 % of the shared wavefronts were bank conflicts);
+         // these cut that to 1.5-1.7x for 18-67 % more S1.  Measured on B300 (best variant, ~3e7
+         // DOFs): mass p = 6, 7, 8 -2.7, -2.2, -4.9 %, diffusion p = 6, 8 -3.0, -1.4 %; diffusion
+         // p = 7 +4.6 % (kept plain), 1e5-DOF meshes within 2 %.
+         : (P == 6 && Q == 8) ? SmemPick{7, 0, 15, 105, 0, 72, 0}
+         : (P == 7 && Q == 9 && !DIFF) ? SmemPick{9, 0, 12, 105, 0, 105, 0}
+         : (P == 8 && Q == 10) ? SmemPick{9, 0, 13, 117, 0, 106, 0}
+         // other p >= 5: the plain odd strides (the model-search picks of p <= 4's kind measured no
+         // faster there, p = 8 diffusion 2-4 % slower)
          : SmemPick{(P + 1) | 1, 0, Q | 1, (P + 1) * (Q | 1), 0,
                     Q * Q + (((Q - (Q * Q) % 32) % 32) + 32) % 32, 0};
 }

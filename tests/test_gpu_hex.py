@@ -176,3 +176,47 @@ def test_hex_grid_equals_structured_at_benchmark_size(form):
     assert float(torch.linalg.norm((y32h - y32s).double()) / torch.linalg.norm(y32s.double())) <= 1e-6
     d_s, d_h = st.diagonal(), hx.diagonal()[pi]
     assert float(torch.linalg.norm(d_h - d_s) / torch.linalg.norm(d_s)) <= 1e-14
+
+
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_hex_every_action_variant_matches_oracle(p):
+    """Every compiled FP64 action (DFMA, double-float in full- and half-size blocks) and every
+    FP32 launch shape on the unstructured mesh, diffusion with the boundary fixed."""
+    op, mesh, pi, bd = setup("unstructured", p, "diffusion", seed=60 + p)
+    op.set_essential(op.boundary_dofs())
+    prob = O.Problem(mesh, p, None, O.DIFFUSION, assemble=p <= 5)
+    x = FI.uniform_vector(op.N, seed=61)
+    xl = np.empty_like(x)
+    xl[pi] = x
+    ref = prob.apply(x, constrained=True)
+    for v in (0, 1, 2):
+        op.set_f64_variant(v)
+        y = op.apply(torch.from_numpy(xl).cuda()).cpu().numpy()[pi]
+        assert rel(y, ref) <= TOL64, v
+    ref32 = prob.apply(x.astype(np.float32).astype(np.float64), constrained=True)
+    for v in range(4):
+        op.set_f32_variant(v)
+        y32 = op.apply_f32(torch.from_numpy(xl.astype(np.float32)).cuda()).cpu().numpy()[pi]
+        assert rel(y32, ref32) <= TOL32, v
+
+
+def test_hex_resumable_multigrid_solve_matches_oracle():
+    """The resumable multigrid-preconditioned CG on the unstructured mesh: the blocking solve's
+    iterations and solution, and the oracle's tightly solved solution."""
+    op, mesh, pi, bd = setup("unstructured", 4, "diffusion", seed=64)
+    op.set_essential(op.boundary_dofs())
+    b = op.rhs_sine(3 * math.pi ** 2)
+    mg = F().Multigrid(op, precision="fp64")
+    x1, s1 = mg.solve(b, rtol=1e-11)
+    x2 = torch.zeros_like(b)
+    mg.solver_start(b, x2, rtol=1e-11)
+    st = mg.solver_poll(blocking=True)
+    while not st["done"]:
+        mg.solver_advance(3)
+        st = mg.solver_poll(blocking=True)
+    assert st["status"] == 0 and st["iterations"] == s1["iterations"]
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-12
+    prob = O.Problem(mesh, 4, None, O.DIFFUSION)
+    xt, _, _ = prob.solve(prob.sine_rhs(), rtol=1e-14)
+    assert rel(x2.cpu().numpy()[pi], xt) <= 1e-9
+    mg.close()
