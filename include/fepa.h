@@ -564,7 +564,8 @@ typedef struct fepa_mg fepa_mg;
 
 int fepa_mg_create(fepa_op* fine, int32_t smooth_degree, int32_t coarse_degree, int32_t precision, fepa_mg** out);
 /* After fepa_op_set_vertices on the fine op: move every level's mesh and rebuild its
- * diagonal and lambda_max (no allocation). */
+ * diagonal and lambda_max (no allocation).  FEPA_ERR_ARG while a resumable solve
+ * (fepa_mg_solver_start) has not finished. */
 int fepa_mg_update(fepa_mg* mg);
 void fepa_mg_destroy(fepa_mg* mg);
 int32_t fepa_mg_levels(const fepa_mg* mg);

@@ -513,11 +513,11 @@ class Operator:
     def solver_start(self, b, x, kind="cg", rtol=1e-10, maxit=20000, max_outer=50, inner_rtol=1e-4,
                      precond="jacobi"):
         torch = _torch()
-        self._sv_keep = (b, x)   # the buffers must outlive the solve
         k = {"cg": SOLVER_CG, "refined": SOLVER_REFINED}.get(kind, kind)
         _check(self._lib.fepa_solver_start(self._h, int(k), _dev_ptr(b, torch.float64, self.N, "b"),
                                            _dev_ptr(x, torch.float64, self.N, "x"), float(rtol), int(maxit),
                                            int(max_outer), float(inner_rtol), _PRECONDS[precond]))
+        self._sv_keep = (b, x)   # the buffers must outlive the solve (kept once it has started)
 
     def solver_advance(self, iterations):
         _check(self._lib.fepa_solver_advance(self._h, int(iterations)))
@@ -757,10 +757,10 @@ class Multigrid:
     def solver_start(self, b, x, rtol=1e-10, maxit=1000):
         torch = _torch()
         n = self.levels[0]["ndofs"]
-        self._sv_keep = (b, x)   # the buffers must outlive the solve
         self.op._sync_stream()
         _check(self._lib.fepa_mg_solver_start(self._h, _dev_ptr(b, torch.float64, n, "b"),
                                               _dev_ptr(x, torch.float64, n, "x"), float(rtol), int(maxit)))
+        self._sv_keep = (b, x)   # the buffers must outlive the solve
 
     def solver_advance(self, iterations):
         _check(self._lib.fepa_mg_solver_advance(self._h, int(iterations)))

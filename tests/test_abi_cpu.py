@@ -62,6 +62,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.fepa_cg_solve(None, None, None, 1e-10, 10, 1, None) == fepa.ERR_ARG
     assert lib.fepa_op_set_fused_dot(None, 1) == fepa.ERR_ARG
     assert lib.fepa_op_apply_f32_dot(None, None, None, None) == fepa.ERR_ARG
+    st = fepa.SolverState()
+    assert lib.fepa_mg_solver_start(None, None, None, 1e-10, 10) == fepa.ERR_ARG
+    assert lib.fepa_mg_solver_advance(None, 1) == fepa.ERR_ARG
+    assert lib.fepa_mg_solver_poll(None, 0, ctypes.byref(st)) == fepa.ERR_ARG
+    assert lib.fepa_batch_group_info(None, 0, None, None, None, None, None) == fepa.ERR_ARG
 
 
 def test_product_code_never_imports_oracle():

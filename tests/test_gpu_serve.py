@@ -130,9 +130,14 @@ def test_resumable_multigrid_solve_equals_one_shot(precision, step):
     assert st["done"] and st["status"] == 0 and st["rel_residual"] <= 1e-10
     assert abs(st["iterations"] - s1["iterations"]) <= (0 if precision == "fp64" else 1)
     assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
-    # a second solve on the same hierarchy starts from the caller's x again
+    # a second solve on the same hierarchy starts from the caller's x again; while it runs the
+    # hierarchy cannot be moved nor a second solve started
     x3 = torch.zeros_like(b)
     mg.solver_start(b, x3, rtol=1e-10)
+    with pytest.raises(F().FepaError):
+        mg.update()
+    with pytest.raises(F().FepaError):
+        mg.solver_start(b, torch.zeros_like(b), rtol=1e-10)
     while not mg.solver_poll(blocking=True)["done"]:
         mg.solver_advance(2)
     assert rel(x3.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
