@@ -401,3 +401,67 @@ def test_l2_convergence_rate_two_sided(p):
         errs.append(O.l2_error(mesh, p, x, O.sine_solution))
     rate = math.log(errs[-2] / errs[-1]) / math.log(ns[-1] / ns[-2])
     assert p + 1 - 0.35 < rate < p + 1 + 0.35, (errs, rate)
+
+
+def _cheb_smoother_matrix(A, lmin, lmax, k):
+    """Closed form of k Chebyshev-Jacobi steps from x0 = 0: the error is R_k(D^-1 A) times the
+    initial error, R_k(t) = T_k((theta - t) / delta) / T_k(theta / delta), so x_k = S b with
+    S = (I - R_k(D^-1 A)) A^-1.  R_k(D^-1 A) is evaluated through the eigendecomposition of the
+    symmetric D^-1/2 A D^-1/2, T_k by numpy's Chebyshev-series routine."""
+    d = np.diag(A)
+    Ds, Dis = np.diag(np.sqrt(d)), np.diag(1.0 / np.sqrt(d))
+    lam, Q = np.linalg.eigh(Dis @ A @ Dis)
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    Tk = lambda x: np.polynomial.chebyshev.chebval(x, [0.0] * k + [1.0])  # noqa: E731
+    R = Dis @ (Q * (Tk((theta - lam) / delta) / Tk(theta / delta))) @ Q.T @ Ds
+    return (np.eye(len(d)) - R) @ np.linalg.inv(A)
+
+
+def test_chebyshev_smoother_and_vcycle_equal_their_closed_forms():
+    """The oracle's smoother recurrence equals the closed-form Chebyshev polynomial of D^-1 A,
+    and its V-cycle (levels p = 4, 2, 1) equals the symmetric V-cycle built from dense matrices:
+    M_l = (I - S A)[(I - C A) S + C] + S with C = P M_{l+1} Z_{l+1} P^T Z_l (Z_l zeroes the
+    essential rows of level l) and M_L the coarsest level's smoother, so its error operator is
+    (I - S A)(I - C A)(I - S A).  A dropped smoothing pass, a missing mask, P in place of P^T or a
+    wrong recurrence coefficient each change the matrix."""
+    mesh = perturbed(2, 2, 2, seed=12)
+    ps = [4, 2, 1]
+    probs = [O.Problem(mesh, p, None, O.DIFFUSION) for p in ps]
+    As = [pr.Ac for pr in probs]
+    Ad = [A.toarray() for A in As]
+    Ps = [O.order_prolongation(mesh, ps[l + 1], ps[l]) for l in range(len(ps) - 1)]
+    ess = [pr.ess for pr in probs]
+    lam = [np.linalg.eigvals(A / np.diag(A)[:, None]).real.max() for A in Ad]
+    smooth, coarse, deg, cdeg = (0.25, 1.1), (0.003, 1.2), 2, 24
+    # the smoother alone, on unit vectors
+    S0 = _cheb_smoother_matrix(Ad[0], smooth[0] * lam[0], smooth[1] * lam[0], deg)
+    Sor = np.stack([O.chebyshev_smoother(lambda v: Ad[0] @ v, np.diag(Ad[0]), e, smooth[0] * lam[0],
+                                         smooth[1] * lam[0], deg) for e in np.eye(probs[0].N)], axis=1)
+    np.testing.assert_allclose(Sor, S0, rtol=0, atol=1e-11 * np.abs(S0).max())
+
+    def mask(l):
+        z = np.ones(probs[l].N)
+        z[ess[l]] = 0.0
+        return np.diag(z)
+
+    def vcycle_matrix(l):
+        A = Ad[l]
+        if l == len(ps) - 1:
+            return _cheb_smoother_matrix(A, coarse[0] * lam[l], coarse[1] * lam[l], cdeg)
+        S = _cheb_smoother_matrix(A, smooth[0] * lam[l], smooth[1] * lam[l], deg)
+        P = Ps[l].toarray()
+        C = P @ vcycle_matrix(l + 1) @ mask(l + 1) @ P.T @ mask(l)
+        I = np.eye(len(A))
+        return (I - S @ A) @ ((I - C @ A) @ S + C) + S
+
+    M = vcycle_matrix(0)
+    Mor = np.stack([O.pmg_vcycle(As, [A.diagonal() for A in As], Ps, lam, deg, cdeg, e, smooth=smooth,
+                                 coarse=coarse, ess=ess) for e in np.eye(probs[0].N)], axis=1)
+    np.testing.assert_allclose(Mor, M, rtol=0, atol=1e-9 * np.abs(M).max())
+    # and the error operator factorises as stated
+    S = _cheb_smoother_matrix(Ad[0], smooth[0] * lam[0], smooth[1] * lam[0], deg)
+    P = Ps[0].toarray()
+    C = P @ vcycle_matrix(1) @ mask(1) @ P.T @ mask(0)
+    I = np.eye(probs[0].N)
+    E = (I - S @ Ad[0]) @ (I - C @ Ad[0]) @ (I - S @ Ad[0])
+    np.testing.assert_allclose(I - Mor @ Ad[0], E, rtol=0, atol=1e-8)
