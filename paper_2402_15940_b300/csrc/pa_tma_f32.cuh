@@ -193,6 +193,14 @@ constexpr SmemPick smem_pick(int P, int Q, bool DIFF) {
          // these cut that to 1.5-1.7x for 18-67 % more S1.  Measured on B300 (best variant, ~3e7
          // DOFs): mass p = 6, 7, 8 -2.7, -2.2, -4.9 %, diffusion p = 6, 8 -3.0, -1.4 %; diffusion
          // p = 7 +4.6 % (kept plain), 1e5-DOF meshes within 2 %.
+         // p = 5, q = 7: the plain strides with element pads for S1 and S2 from a model of stages
+         // 1, 2, 3, 2^T, 1^T and the gather / scatter with the block's 5 (variant 1) or 2 (variant 2)
+         // elements, whose 49-thread columns make every warp straddle two elements: the S2 pad moves
+         // the second element's stage-3 columns onto the banks the first leaves free (modelled shared
+         // wavefronts of a 5-element diffusion block 1,666 -> 1,414).  Measured on B300 (~3e7 DOFs,
+         // two runs): diffusion -1.9 % (best plain), -2.4 % (the CG loop's fused build); mass -0.5..-1.1 %.
+         : (P == 5 && Q == 7 && DIFF) ? SmemPick{7, 0, 7, 42, 3, 71, 19}
+         : (P == 5 && Q == 7 && !DIFF) ? SmemPick{7, 0, 7, 42, 31, 71, 7}
          : (P == 6 && Q == 8) ? SmemPick{7, 0, 15, 105, 0, 72, 0}
          : (P == 7 && Q == 9 && !DIFF) ? SmemPick{9, 0, 12, 105, 0, 105, 0}
          : (P == 8 && Q == 10) ? SmemPick{9, 0, 13, 117, 0, 106, 0}
