@@ -183,6 +183,75 @@ cg_update(int64_t N, double* __restrict__ x, double* __restrict__ r, const doubl
   }
 }
 
+// The FP64 loop's balanced pair (the graph and stream loops of fepa_cg_solve and the resumable
+// solve): cg_update_r leaves x to cg_direction_x, which reads d anyway, so the update kernel makes
+// four FP64 operations per DOF instead of five and moves 32 bytes instead of 56 -- B300's FP64
+// pipe (about 0.6 T multiply-adds/s) and HBM bound cg_update about equally at large N.  The last
+// step's x update is cg_flush64's.  Each value is computed as by cg_update / cg_direction (the same
+// alpha, old d and operations), only one kernel later.
+__global__ void __launch_bounds__(RED_THREADS)
+cg_update_r(int64_t N, double* __restrict__ r, const double* __restrict__ h, const double* __restrict__ inv_diag,
+            CgState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i] - alpha * h[i];
+    r[i] = ri;
+    const double zi = inv_diag ? ri * inv_diag[i] : ri;
+    v[0] += zi * ri;
+    v[1] += ri * ri;
+  }
+  double blk[2];
+  block_sum<2>(v, blk);
+  if (publish_partials<2>(blk, partials, &st->ticket)) {
+    double tot[2];
+    final_sums<2>(partials, tot);
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      st->rr = tot[1];
+      if (tot[1] <= st->tol2) {
+        st->converged = 1;
+        st->done = 1;
+      } else if (st->iter >= st->maxit || !isfinite(st->rr)) {
+        st->done = 1;
+      }
+      st->beta = tot[0] / st->rho;
+      st->rho = tot[0];
+      st->ticket = 0;
+    }
+  }
+}
+
+// x += alpha d (this iteration's step, d still the old direction); d = z + beta d; h = 0.  Block 0
+// sets the graph's while-condition.  Once the loop is done nothing is written (cg_flush64).
+__global__ void __launch_bounds__(RED_THREADS)
+cg_direction_x(int64_t N, const double* __restrict__ r, double* __restrict__ d, double* __restrict__ h,
+               const double* __restrict__ inv_diag, double* __restrict__ x, const CgState* st,
+               cudaGraphConditionalHandle cond, int use_cond) {
+  const int done = st->done;
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(cond, (done || st->iter >= st->tick_limit) ? 0u : 1u);
+  if (done) return;
+  const double alpha = st->alpha, beta = st->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = d[i];
+    x[i] += alpha * di;
+    const double zi = inv_diag ? r[i] * inv_diag[i] : r[i];
+    d[i] = zi + beta * di;
+    h[i] = 0.0;
+  }
+}
+
+// x += alpha d for the final step of a finished FP64 loop (done and at least one step): its
+// direction kernel returned before advancing x
+__global__ void cg_flush64(int64_t N, double* __restrict__ x, const double* __restrict__ d, const CgState* st) {
+  if (!(st->done && st->iter > 0)) return;
+  const double alpha = st->alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += alpha * d[i];
+}
+
 // d = z + beta d; h = 0.  Block 0 sets the graph's while-condition to !done.
 __global__ void __launch_bounds__(RED_THREADS)
 cg_direction(int64_t N, const double* __restrict__ r, double* __restrict__ d, double* __restrict__ h,

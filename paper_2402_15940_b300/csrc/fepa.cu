@@ -835,10 +835,17 @@ int body64(fepa_op* op, CgLoop& L, const double* invd, cudaStream_t s, cudaGraph
   TRY(launch_apply_nocount(op, d, h, &L.st->done, s));
   cg_dot_dh<<<rb, RED_THREADS, 0, s>>>(op->N, d, h, L.st, L.partials);
   BODY_CHECK();
-  cg_update<<<rb, RED_THREADS, 0, s>>>(op->N, x, r, d, h, invd, L.st, L.partials);
+  cg_update_r<<<rb, RED_THREADS, 0, s>>>(op->N, r, h, invd, L.st, L.partials);
   BODY_CHECK();
-  cg_direction<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, L.st, cond, use_cond);
+  cg_direction_x<<<rb, RED_THREADS, 0, s>>>(op->N, r, d, h, invd, x, L.st, cond, use_cond);
   BODY_CHECK();
+  return FEPA_OK;
+}
+
+// the final step's x update of a finished FP64 loop (body64 advances x in its direction kernel)
+int flush64(fepa_op* op, CgLoop& L, cudaStream_t s) {
+  cg_flush64<<<grid_for(op->N, 256, 148 * 16), 256, 0, s>>>(op->N, op->xw, (const double*)L.d, L.st);
+  LAUNCH_CHECK();
   return FEPA_OK;
 }
 
@@ -960,6 +967,7 @@ int run_cg(fepa_op* op, const double* b, double* x, double rtol, int maxit, int 
     return body64(op, L, invd, bs, cond, use_cond);
   };
   TRY(run_loop(op, L, precond, body, op->st_host));
+  TRY(flush64(op, L, s));
   CUDA_TRY(cudaMemcpyAsync(x, op->xw, op->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   const CgState h = *op->st_host;
